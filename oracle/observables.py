@@ -1,0 +1,165 @@
+"""Block observables and structure factor in plain FP64 (test infrastructure).
+
+Sec. II B (Eqs. 46-50): the lattice of side S is divided into blocks of side
+L = S/2^i (i = 0, 1, ...; the paper allows powers of two, footnote there) and
+  m_L^(b) = L^-d sum_{i in b} phi_i                      (Eq. 46)
+  M_L = <|m_L|>                                          (Eq. 47)
+  chi_L = L^d/kT (<m_L^2> - <m_L>^2)        (theta > 0)  (Eq. 48)
+  chi_L = L^d/kT (<m_L^2> - <|m_L|>^2)      (theta < 0)  (Eq. 49)
+  c_H,L = L^d/kT (<E_L^2> - <E_L>^2),  E_L^(b) = (2 L^d)^-1 sum phi_i^2  (Eq. 50)
+averaged over all blocks of a level and over samples in time.  phi is the
+order parameter of Eq. 1 with rho_0 the global mean density.  U_L =
+1 - <m^4>/(3 <m^2>^2) is Binder's cumulant (the paper does not use it; it is
+reported as a numerical-accuracy figure).
+
+Levels: block dims (nx/2^i, ny/2^i[, nz/2^i]) for i = 0, 1, ... while every
+division is exact, then the single-site level (1, 1, 1) if not yet reached.
+For a 2-D lattice the z extent of a block is 1.  Level i = 0 is the whole
+system, where m = 0 by mass conservation (kept as a check).
+
+Structure factor (Eq. 80): C(k) = N^-1 |sum_r phi(r) exp(-i k.r)|^2, with the
+discrete Fourier transform taken by numpy's FFT (a library primitive).  Shell
+binning (a convention of this project): on an S^d lattice, k = 2 pi n / S with
+n_a wrapped to [-S/2, S/2), and the point goes to shell j with
+j (j - 1) < |n|^2 <= j (j + 1), i.e. the integer nearest to |n|.  Shell 0
+(k = 0, where C = 0 by mass conservation) is not reported.
+"""
+
+import numpy as np
+
+from . import lbm
+
+ACC_FIELDS = ("n", "sum_m", "sum_m2", "sum_abs_m", "sum_m4", "sum_e", "sum_e2")
+
+
+def levels(p):
+    dims = [p.nx, p.ny] + ([p.nz] if p.nz > 1 or p.lattice == "D3Q19" else [])
+    out = []
+    i = 0
+    while all(n % (1 << i) == 0 and (n >> i) >= 1 for n in dims):
+        blk = [n >> i for n in dims]
+        if p.nz == 1 and len(blk) == 2:
+            blk.append(1)
+        out.append(tuple(blk))
+        if all(b == 1 for b in blk):
+            break
+        i += 1
+    if out[-1] != (1, 1, 1):
+        out.append((1, 1, 1))
+    return out
+
+
+def order_parameter(f):
+    """phi = (rho - rho_bar)/rho_bar with rho_bar the global mean (Eq. 1)."""
+    rho = lbm.density(f)
+    rbar = rho.mean()
+    return (rho - rbar) / rbar
+
+
+def block_means(x, blk):
+    """Mean of ``x`` (shape (nz, ny, nx)) over blocks of dims (bx, by, bz)."""
+    bx, by, bz = blk
+    nz, ny, nx = x.shape
+    return x.reshape(nz // bz, bz, ny // by, by, nx // bx, bx).mean(axis=(1, 3, 5))
+
+
+def sample(phi, lv):
+    """Per-level increments of the accumulators for one snapshot of phi."""
+    rows = []
+    for blk in lv:
+        m = block_means(phi, blk).ravel()
+        e = 0.5 * block_means(phi * phi, blk).ravel()
+        rows.append([m.size, m.sum(), (m * m).sum(), np.abs(m).sum(), (m ** 4).sum(),
+                     e.sum(), (e * e).sum()])
+    return np.asarray(rows, dtype=np.float64)
+
+
+def derived(acc, lv, kT):
+    """M_L, chi_L (Eqs. 48 and 49), c_H,L (Eq. 50), U_L from accumulated sums."""
+    out = []
+    for row, blk in zip(acc, lv):
+        n = row[0]
+        vol = float(blk[0] * blk[1] * blk[2])
+        mean_m, m2, am, m4, e, e2 = (row[1:] / n) if n > 0 else (np.nan,) * 6
+        out.append({
+            "block": blk,
+            "M_L": am,
+            "m2": m2,
+            "m4": m4,
+            "chi_L": vol / kT * (m2 - mean_m ** 2),
+            "chi_L_lowT": vol / kT * (m2 - am ** 2),
+            "c_HL": vol / kT * (e2 - e ** 2),
+            "U_L": 1.0 - m4 / (3.0 * m2 * m2) if m2 > 0 else np.nan,
+        })
+    return out
+
+
+def structure_factor(phi):
+    """C(k) = |sum_r phi(r) e^{-i k.r}|^2 / N over the full k grid (Eq. 80)."""
+    F = np.fft.fftn(phi)
+    return (F.real ** 2 + F.imag ** 2) / phi.size
+
+
+def shell_index(shape):
+    """Shell j of every k point of a cubic / square lattice (see module docstring)."""
+    nz, ny, nx = shape
+    sides = [n for n in (nx, ny, nz) if n > 1]
+    if len(set(sides)) != 1:
+        raise ValueError("shell binning needs equal sides")
+    n2 = np.zeros(shape, dtype=np.int64)
+    for ax, n in zip((0, 1, 2), (nz, ny, nx)):
+        if n == 1:
+            continue
+        idx = np.arange(n)
+        idx = np.where(2 * idx < n, idx, idx - n)             # wrap to [-S/2, S/2)
+        shp = [1, 1, 1]
+        shp[ax] = n
+        n2 = n2 + (idx.reshape(shp) ** 2)
+    j = np.floor(np.sqrt(n2.astype(np.float64))).astype(np.int64)
+    # exact integer rule j(j-1) < n2 <= j(j+1)
+    j = np.where(j * (j + 1) < n2, j + 1, j)
+    j = np.where(j * (j - 1) >= n2, j - 1, j)
+    j = np.where(n2 == 0, 0, j)
+    return j
+
+
+def bin_shells(ck_sum, shape, nbins):
+    """(sum of C over each shell j = 1..nbins, number of k points per shell)."""
+    j = shell_index(shape).ravel()
+    vals = np.asarray(ck_sum).ravel()
+    sums = np.zeros(nbins)
+    counts = np.zeros(nbins, dtype=np.int64)
+    for b in range(1, nbins + 1):
+        sel = j == b
+        sums[b - 1] = vals[sel].sum()
+        counts[b - 1] = sel.sum()
+    return sums, counts
+
+
+class Recorder:
+    """Accumulates block observables (and optionally C(k)) every ``every`` steps.
+
+    A sample is taken at times t > 0 with t % every == 0, from the state f(., t).
+    Also records the FP64 mass sum rho and momentum sum j at each sample.
+    """
+
+    def __init__(self, p, every, sk_every=0):
+        self.p = p
+        self.lv = levels(p)
+        self.every = every
+        self.sk_every = sk_every
+        self.acc = np.zeros((len(self.lv), len(ACC_FIELDS)))
+        self.ck = np.zeros(p.shape)
+        self.n_sk = 0
+        self.mass = []
+        self.mom = []
+
+    def __call__(self, f, t):
+        if self.every > 0 and t > 0 and t % self.every == 0:
+            phi = order_parameter(f)
+            self.acc += sample(phi, self.lv)
+            self.mass.append(lbm.density(f).sum())
+            self.mom.append(lbm.momentum(f, self.p.lat).reshape(3, -1).sum(axis=1))
+        if self.sk_every > 0 and t > 0 and t % self.sk_every == 0:
+            self.ck += structure_factor(order_parameter(f))
+            self.n_sk += 1
