@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the fused fluctuating lattice Boltzmann step on GB300.
+
+Metric: MLUPS (million lattice-site updates per second, all systems, all
+ranks) of the batched FP32 ensemble, with the HBM-roofline fraction of the
+fused step kernel.
+
+Default workload ``fss_160``: the finite-size-scaling ensemble of 160 D3Q19
+systems, L in {16, 24, 32, 48, 64}^3 x 8 values of a in [-0.004, 0.004] x 4
+replicas, b = 0.1, kappa = 0.01, tau = 1, kT = 1e-4, FP32-deviation
+populations, FP64 observables every 100 steps, CUDA-graph replay of 100-step
+chunks.  One benchmark step = 100 fused LB steps + one observable pass (one
+sampling interval of the hot path).  The populations (2 x 2.06 GB) are far
+larger than L2, so no flush is needed between iterations.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+N > 1 runs under torch.distributed.run; each rank advances its own ensemble
+(weak scaling, no data-path collective).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LB_STEPS_PER_STEP = 100
+WORKLOADS = {
+    "fss_160": dict(ensemble="fss_160", lattice="D3Q19", precision="fp32"),
+    "fss_160_d2q9": dict(ensemble="fss_160", lattice="D2Q9", precision="fp32"),
+    "single_64": dict(ensemble="single_64", lattice="D3Q19", precision="fp32"),
+    "large_256": dict(ensemble="large_256", lattice="D3Q19", precision="fp32"),
+    "fss_160_fp64": dict(ensemble="fss_160", lattice="D3Q19", precision="fp64"),
+}
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+KERNEL_SOURCES = ["paper_1202_4748_gb300/csrc/step_kernels.cuh", "paper_1202_4748_gb300/csrc/lb_device.cuh"]
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def describe(wl, systems):
+    import synth
+    sides = sorted({s["nx"] for s in systems})
+    a = sorted({round(s["a"], 6) for s in systems})
+    return {
+        "workload": "%s: %d %s systems, sides %s, %d values of a in [%g, %g], %s populations"
+                    % (wl["ensemble"], len(systems), wl["lattice"], sides, len(a), a[0], a[-1], wl["precision"]),
+        "lattice": wl["lattice"], "coupling": systems[0]["coupling"], "precision": wl["precision"],
+        "systems": len(systems), "sites": synth.sites(systems),
+        "b": 0.1, "kappa": 0.01, "tau": 1.0, "kT": 1e-4,
+        "lb_steps_per_step": LB_STEPS_PER_STEP, "obs_every": LB_STEPS_PER_STEP, "graph_chunk": LB_STEPS_PER_STEP,
+        "l2": "working set larger than L2 (inputs larger than L2, no flush)",
+    }
+
+
+def q_of(lattice):
+    return 9 if lattice == "D2Q9" else 19
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, fl in rows for k, v in enumerate(fl) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_sample_systems(wl):
+    """One system per size class of the workload (the bounded CPU sample)."""
+    import synth
+    systems = synth.ensemble(wl["ensemble"], wl["lattice"])
+    seen, out = set(), []
+    for s in systems:
+        if s["nx"] not in seen:
+            seen.add(s["nx"])
+            out.append(s)
+    return out
+
+
+def oracle_params(s):
+    from oracle import lbm
+    return lbm.Params(lattice=s["lattice"], coupling=s["coupling"], nx=s["nx"], ny=s["ny"], nz=s["nz"],
+                      rho_c=s["rho_c"], a=s["a"], b=s["b"], kappa=s["kappa"], kT=s["kT"],
+                      tau=tuple(s["tau"]), seed=s["seed"], system_id=s["system_id"])
+
+
+def run_oracle_sample(wl, steps, warmup):
+    """Time the FP64 oracle on the bounded sample; returns (MLUPS, sites, seconds)."""
+    from oracle import lbm
+    params_of = oracle_params
+    systems = oracle_sample_systems(wl)
+    ps = [params_of(s) for s in systems]
+    fs = [lbm.initial_state(p) for p in ps]
+    for k in range(len(ps)):
+        fs[k] = lbm.run(fs[k], 0, warmup, ps[k])
+    t0 = time.perf_counter()
+    for k in range(len(ps)):
+        fs[k] = lbm.run(fs[k], warmup, steps, ps[k])
+    dt = time.perf_counter() - t0
+    sites = sum(p.n_sites for p in ps)
+    return sites * steps / dt / 1e6, sites, dt
+
+
+def cpu_baseline_subprocess(wl_name, steps, warmup):
+    """Run the oracle sample in a fresh single-threaded process (not a fork of this one)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", wl_name, "--steps", str(steps),
+           "--warmup", str(warmup)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------------------
+def load_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def load_traffic():
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if t.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return t
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fss_160", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+
+    if args.cpu_sample:
+        mlups, sites, dt = run_oracle_sample(WORKLOADS[args.cpu_sample], args.steps, args.warmup)
+        print(json.dumps({"mlups": mlups, "sites": sites, "seconds": dt}))
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = WORKLOADS[args.workload]
+
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+
+    import torch
+    import synth
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1202_4748_gb300 as lb
+
+    systems = synth.ensemble(wl["ensemble"], wl["lattice"])
+    n_sys = len(systems)
+    for s in systems:                       # each rank draws its own noise streams
+        s["system_id"] += rank * n_sys
+    sites = synth.sites(systems)
+    q = q_of(wl["lattice"])
+    es = 4 if wl["precision"] == "fp32" else 8
+
+    stream = torch.cuda.current_stream()
+    ens = lb.Ensemble(systems, precision=wl["precision"], obs_every=LB_STEPS_PER_STEP,
+                      graph_chunk=LB_STEPS_PER_STEP)
+    ens.init(amplitude=0.01)
+    for _ in range(args.warmup):
+        ens.step(LB_STEPS_PER_STEP)
+    ens.sync()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    gpu_index = local_rank
+    if os.environ.get("CUDA_VISIBLE_DEVICES"):
+        vis = os.environ["CUDA_VISIBLE_DEVICES"].split(",")
+        if local_rank < len(vis) and vis[local_rank].strip().isdigit():
+            gpu_index = int(vis[local_rank])
+    clocks = ClockSampler(gpu_index)
+
+    # ---- timed region: K benchmark steps ---------------------------------
+    launches0 = ens.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ens.step(LB_STEPS_PER_STEP)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ens.sync()
+    launches = ens.kernel_launches() - launches0
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    updates = sites * LB_STEPS_PER_STEP * args.steps * world
+    mlups = updates / (ms_max * 1e-3) / 1e6
+
+    # ---- step-kernel duration: 99 plain step launches, no observable pass ----
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    k0.record(stream)
+    ens.step(LB_STEPS_PER_STEP - 1)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    kern_ms = k0.elapsed_time(k1) / (LB_STEPS_PER_STEP - 1)
+    ens.step(1)
+    ens.sync()
+    bytes_per_launch = sites * q * 2 * es
+    achieved = bytes_per_launch / (kern_ms * 1e-3) / 1e9
+    peak, peak_kind = load_peak()
+    traffic = load_traffic()
+
+    # ---- end to end through the public API from pinned host memory -----------
+    import numpy as np
+    k_e2e = max(3, args.steps // 2)
+    rho_host = torch.empty(sites, dtype=torch.float64, pin_memory=True)
+    rho_host.copy_(torch.from_numpy(np.concatenate(
+        [synth.random_density((s["nz"], s["ny"], s["nx"]), seed=s["system_id"]).ravel() for s in systems])))
+    rho_np = rho_host.numpy()
+    barrier()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(k_e2e):
+        ens.init(rho=rho_np)                     # H2D of the step's input density field
+        ens.step(LB_STEPS_PER_STEP)
+        for k in range(n_sys):                   # D2H of the step's result (observables)
+            levels, _ = ens.observables(k)
+            d2h += 64 * len(levels) + 64
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_mlups = sites * LB_STEPS_PER_STEP * k_e2e * world / e2e_s / 1e6
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = cpu_baseline_subprocess(args.workload, steps=2, warmup=0)
+        if "mlups" in r:
+            n_cls = len(oracle_sample_systems(wl))
+            cpu = {"value": r["mlups"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                   "sample": "FP64 numpy oracle, %d systems (one per size class, %d sites) x 2 LB steps, %.1f s"
+                             % (n_cls, r["sites"], r["seconds"])}
+        else:
+            cpu = {"value": None, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": r.get("error")}
+
+    ens.close()
+    if rank == 0:
+        out = {
+            "metric": "MLUPS of the batched FP32 fused fluctuating LB step (HBM-roofline fraction in roofline)",
+            "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if wl["precision"] == "fp32" else "f64", "data": "synthetic",
+            "config": describe(wl, systems),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4),
+                         "traffic": (traffic["bytes_per_launch_scaled"] if traffic else None),
+                         "kernel": "step_kernel", "kernel_ms": round(kern_ms, 5),
+                         "bytes_per_launch": bytes_per_launch,
+                         "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
+                         "frac_of_8TBs": round(achieved / 8000.0, 4)},
+            "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": sites * 8,
+                    "d2h_bytes_per_step": d2h // k_e2e},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(args, wl, rank, world):
+    """Reference arm: the FP64 oracle on the host cores, on a bounded sample."""
+    if rank != 0:
+        return
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    env_threads = 1
+    from oracle import lbm
+    params_of = oracle_params
+    systems = oracle_sample_systems(wl)
+    ps = [params_of(s) for s in systems]
+    fs = [lbm.initial_state(p) for p in ps]
+    t = 0
+    for _ in range(args.warmup):
+        fs = [lbm.step(f, t, p) for f, p in zip(fs, ps)]
+        t += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fs = [lbm.step(f, t, p) for f, p in zip(fs, ps)]
+        t += 1
+    dt = time.perf_counter() - t0
+    sites = sum(p.n_sites for p in ps)
+    mlups = sites * args.steps / dt / 1e6
+    sample = ("FP64 numpy oracle on %d systems of the %s workload (one per size class, %d sites); "
+              "one step = one LB step of the sample" % (len(ps), wl["ensemble"], sites))
+    out = {
+        "metric": "MLUPS of the batched FP32 fused fluctuating LB step (HBM-roofline fraction in roofline)",
+        "value": round(mlups, 4), "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "%s (bounded oracle sample)" % wl["ensemble"], "lattice": wl["lattice"]},
+        "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": int(env_threads or 1),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

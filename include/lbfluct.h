@@ -1,0 +1,220 @@
+/*
+ * lbfluct.h -- C ABI of the GB300 fluctuating non-ideal-fluid lattice Boltzmann library.
+ *
+ * The library advances ensembles of independent periodic lattices with the
+ * fluctuating lattice Boltzmann method of Gross & Varnik, "Simulation of static
+ * critical phenomena in non-ideal fluids with the Lattice Boltzmann method"
+ * (arXiv:1202.4748), Sec. III A:
+ *   - evolution equation Eq. 61, moments Eq. 62,
+ *   - non-ideal thermodynamics through the pressure tensor Eqs. 63-64: the
+ *     paper's D2Q9 modified equilibrium Eq. 65 (LB_MODEQ), or a D2Q9/D3Q19 form
+ *     with the Landau pressure in the equilibrium and the square-gradient part
+ *     of the chemical potential as a Guo body force (LB_GUO),
+ *   - collision in the moment basis of Eq. 66 with per-mode relaxation rates,
+ *   - local Gaussian noise with the covariance of Eq. 68 (Cholesky-factored),
+ *     drawn from a counter-based Philox4x32-10 stream keyed by
+ *     (site, step, system, draw) so runs are reproducible and resumable,
+ * and accumulates in FP64 the block observables of Sec. II B (Eqs. 46-50) and
+ * the structure factor of Eq. 80.
+ *
+ * Conventions shared by all entry points
+ *   Ownership  The caller owns the device workspace (any device allocation of
+ *              at least lb_workspace_bytes(), 256-byte aligned) and the CUDA
+ *              stream.  The library never allocates device memory.  Host
+ *              buffers passed to getters are caller-owned and are not retained.
+ *   Errors     Every call returns an lb_status; nothing is thrown across the
+ *              ABI.  Device-detected errors (non-positive density, indefinite
+ *              noise covariance, non-finite values) are raised by the next
+ *              synchronising call (lb_sync, getters) and are sticky: after one,
+ *              lb_step returns LB_ERR_STATE until lb_init / lb_write_fields /
+ *              lb_load restores a state.
+ *   Threads    Thread-compatible: one context per host thread at a time.
+ *   Layouts    Host population arrays are float64 [q][nz][ny][nx] (x fastest)
+ *              holding f_i(r, t): the populations at site r before the
+ *              collision of step t.  Velocity order D2Q9: rest, (1,0), (-1,0),
+ *              (0,1), (0,-1), (1,1), (-1,-1), (1,-1), (-1,1).  D3Q19: rest,
+ *              +-x, +-y, +-z, then (1,1,0), (-1,-1,0), (1,-1,0), (-1,1,0),
+ *              (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1),
+ *              (0,1,-1), (0,-1,1).
+ */
+#ifndef LBFLUCT_H
+#define LBFLUCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_ARG = -1,                 /* invalid argument (sizes, tau, kT, combos)  */
+    LB_ERR_CUDA = -2,                /* a CUDA runtime call failed                  */
+    LB_ERR_WORKSPACE = -3,           /* workspace too small or misaligned           */
+    LB_ERR_NONPOSITIVE_DENSITY = -4, /* rho <= 0 met at some site (device)          */
+    LB_ERR_NOISE_NOT_PD = -5,        /* Eq. 68 covariance not positive definite     */
+    LB_ERR_NONFINITE = -6,           /* NaN/Inf met in the observables              */
+    LB_ERR_UNSUPPORTED = -7,         /* valid but not supported combination         */
+    LB_ERR_STATE = -8,               /* sticky error or call out of order           */
+    LB_ERR_IO = -9                   /* checkpoint file error                       */
+} lb_status;
+
+enum { LB_D2Q9 = 0, LB_D3Q19 = 1 };
+enum { LB_MODEQ = 0, LB_GUO = 1 };
+enum { LB_FP64 = 0, LB_FP32_DEVIATION = 1 };
+enum { LB_INIT_UNIFORM_NOISE = 0, LB_INIT_FROM_RHO = 1 };
+#define LB_MAX_Q 19
+#define LB_MAX_LEVELS 32
+
+/* One system of an ensemble.  mu = f0'(phi)/rho_c - kappa lap rho with
+ * f0 = a/2 phi^2 + b/4 phi^4, phi = (rho - rho_c)/rho_c (Eqs. 1-3; a, b are
+ * the paper's r, u).  tau[a] is the relaxation time of moment a (entries of
+ * conserved moments are ignored; every other must exceed 1/2).  The kinematic
+ * viscosity of the Holdych term of Eq. 63 uses tau[4].  Sizes are >= 1;
+ * nz must be 1 for D2Q9.  LB_MODEQ requires D2Q9.  system_id < 2^24. */
+typedef struct {
+    int32_t lattice;
+    int32_t coupling;
+    int32_t nx, ny, nz;
+    double rho_c, a, b, kappa;
+    double kT;                  /* noise temperature k_B T >= 0 (0: deterministic) */
+    double tau[LB_MAX_Q];
+    uint64_t seed;              /* Philox key                                       */
+    uint32_t system_id;         /* enters the Philox counter                        */
+} lb_system_desc;
+
+/* Run options, shared by all systems of a context.  All systems of one
+ * context must share lattice, coupling and precision.
+ *   precision   LB_FP64 (populations and arithmetic in float64) or
+ *               LB_FP32_DEVIATION (float32 populations stored as deviations
+ *               from the rest equilibrium f^eq(rho_c, 0) = rho_c on the rest
+ *               velocity, float32 collision; observables still FP64).
+ *   obs_every   sample the block observables after every obs_every-th step
+ *               (time t > 0 with t % obs_every == 0); 0 disables.
+ *   sk_every    accumulate C(k) likewise; 0 disables.  Needs equal sides.
+ *   graph_chunk if > 0 (even), lb_step replays CUDA graphs of graph_chunk
+ *               steps (with the observable launches inside) when the step
+ *               counter is a multiple of graph_chunk; 0 = plain launches.
+ *   tile        tile shape of the step kernel (0 = library default).       */
+typedef struct {
+    int32_t precision;
+    int32_t obs_every;
+    int32_t sk_every;
+    int32_t graph_chunk;
+    int32_t tile[3];
+    int32_t reserved;
+} lb_run_opts;
+
+/* FP64 accumulators of one block level (Eqs. 46-50).  Blocks have dims
+ * (bx, by, bz); n counts block samples (blocks x snapshots).  m is the block
+ * mean of phi (Eq. 46), e = E_L of Eq. 50 = block mean of phi^2 / 2. */
+typedef struct {
+    int32_t bx, by, bz, pad;
+    double n;
+    double sum_m, sum_m2, sum_abs_m, sum_m4, sum_e, sum_e2;
+} lb_obs_level;
+
+/* Global FP64 bookkeeping of one system at its latest observable sample. */
+typedef struct {
+    int64_t step;               /* current step counter of the context           */
+    int64_t n_samples;          /* observable snapshots accumulated              */
+    double mass0;               /* sum rho at initialisation                     */
+    double mass;                /* sum rho at the latest sample                  */
+    double momentum[3];         /* sum of sum_i c_i f_i at the latest sample     */
+    double rho_mean;            /* mass / sites                                  */
+} lb_obs_global;
+
+typedef struct lb_ctx lb_ctx;
+
+/* Bytes of device workspace needed for these systems and options.
+ * Errors: LB_ERR_ARG for invalid descriptors (see lb_system_desc). */
+lb_status lb_workspace_bytes(const lb_system_desc* systems, int n_systems,
+                             const lb_run_opts* opts, size_t* bytes);
+
+/* Create a context over caller-owned device memory d_workspace (bytes long,
+ * 256-byte aligned) on CUDA stream `stream` (a cudaStream_t; NULL = legacy
+ * default stream) of the current device.  Validates arguments (Sec. III B's
+ * low-Mach constraint kT << rho_c/3 is not enforced).  The state is undefined
+ * until lb_init, lb_write_fields or lb_load.
+ * Errors: LB_ERR_ARG, LB_ERR_WORKSPACE, LB_ERR_UNSUPPORTED, LB_ERR_CUDA. */
+lb_status lb_create(const lb_system_desc* systems, int n_systems, const lb_run_opts* opts,
+                    void* d_workspace, size_t bytes, void* stream, lb_ctx** out);
+
+/* Initialise every system at step 0 with u = 0 and f = f^eq(rho, 0, grad rho):
+ *   LB_INIT_UNIFORM_NOISE  rho = rho_c + amplitude (2U - 1) with U from the
+ *                          system's Philox stream (draw 0xFF, step 0), minus its
+ *                          FP64 mean so that the average density is rho_c;
+ *   LB_INIT_FROM_RHO       rho from h_rho: float64, all systems concatenated in
+ *                          descriptor order, each [nz][ny][nx].
+ * Clears observables and the sticky error.  Synchronises the stream.
+ * Errors: LB_ERR_ARG (mode, missing h_rho), LB_ERR_CUDA. */
+lb_status lb_init(lb_ctx* ctx, int mode, double amplitude, const double* h_rho);
+
+/* Advance all systems nsteps time steps (Eq. 61: collide, add noise, stream),
+ * sampling observables on the obs_every / sk_every schedule.  Asynchronous
+ * on the context's stream.  Errors: LB_ERR_STATE (sticky error / no state),
+ * LB_ERR_ARG (nsteps < 0), LB_ERR_CUDA. */
+lb_status lb_step(lb_ctx* ctx, int64_t nsteps);
+
+/* Wait for the stream and report device-detected errors. */
+lb_status lb_sync(lb_ctx* ctx);
+
+/* Copy the FP64 accumulators of system `sys` (descriptor order) to the host:
+ * up to max_levels levels into h_levels (level 0 = whole system, then blocks
+ * halving each side while exact, last the single-site level), the level count
+ * into *n_levels, and the global bookkeeping into *h_global (nullable).
+ * Synchronises.  Errors: LB_ERR_ARG, device errors, LB_ERR_CUDA. */
+lb_status lb_observables(lb_ctx* ctx, int sys, lb_obs_level* h_levels, int max_levels,
+                         int* n_levels, lb_obs_global* h_global);
+
+/* Derived quantities of one level at noise temperature kT (Eqs. 47-50):
+ * out[0] = M_L = <|m|>, out[1] = chi_L (Eq. 48), out[2] = chi_L low-T form
+ * (Eq. 49), out[3] = c_H,L (Eq. 50), out[4] = Binder U_L = 1 - <m^4>/(3<m^2>^2),
+ * out[5] = <m>.  Pure host arithmetic.  Errors: LB_ERR_ARG (n == 0, kT <= 0). */
+lb_status lb_derive(const lb_obs_level* level, double kT, double out[6]);
+
+/* Structure factor of Eq. 80 accumulated over the sk_every schedule, binned in
+ * shells j = 1..nbins (k = 2 pi n / S, shell j holds j(j-1) < |n|^2 <= j(j+1)):
+ * h_sum[j-1] = sum over samples and shell points of C(k), h_count[j-1] = number
+ * of k points in the shell, *n_samples = snapshots.  Requires equal sides.
+ * Synchronises.  Errors: LB_ERR_ARG, LB_ERR_UNSUPPORTED (sk disabled / sides). */
+lb_status lb_structure_factor(lb_ctx* ctx, int sys, double* h_sum, int64_t* h_count, int nbins,
+                              int64_t* n_samples);
+
+/* Copy f_i(r, t) of system `sys` to h_f (float64 [q][nz][ny][nx]).  Synchronises.
+ * Errors: LB_ERR_ARG, LB_ERR_CUDA. */
+lb_status lb_read_fields(lb_ctx* ctx, int sys, double* h_f);
+
+/* Overwrite f_i(r, t) of system `sys` from h_f (same layout; FP32 contexts
+ * round the deviations to float).  Clears the sticky error.  Synchronises.
+ * Errors: LB_ERR_ARG, LB_ERR_CUDA. */
+lb_status lb_write_fields(lb_ctx* ctx, int sys, const double* h_f);
+
+/* Step counter (number of steps taken since lb_init). */
+lb_status lb_get_step(lb_ctx* ctx, int64_t* step);
+
+/* Checkpoint populations, step counter, accumulators and descriptors to a file;
+ * lb_load restores them into a context created with identical descriptors and
+ * options.  Because the noise is keyed by (site, step, system), a resumed run
+ * is bit-identical to an uninterrupted one.  Errors: LB_ERR_IO, LB_ERR_ARG. */
+lb_status lb_save(lb_ctx* ctx, const char* path);
+lb_status lb_load(lb_ctx* ctx, const char* path);
+
+/* Number of kernels this context has launched so far (graph replays count
+ * every kernel node).  Instrumentation for benchmarks; no device call. */
+lb_status lb_kernel_launches(lb_ctx* ctx, int64_t* count);
+
+/* Release host-side resources (graphs, context); the workspace stays the caller's. */
+void lb_destroy(lb_ctx* ctx);
+
+/* Static string for a status code. */
+const char* lb_status_string(lb_status status);
+
+/* Library version string. */
+const char* lb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBFLUCT_H */

@@ -1,0 +1,256 @@
+"""Python binding of liblbfluct: GB300 fluctuating non-ideal-fluid lattice Boltzmann.
+
+A thin ctypes layer over the C ABI of ``include/lbfluct.h`` (same entry-point
+names, argument marshalling only).  Every step of the method runs in the CUDA
+kernels of the shared library; PyTorch is used only to allocate the device
+workspace and to obtain the current CUDA stream.  Importing this package
+fails loudly if the library has not been built (``__graft_entry__.build()``
+or ``python -m paper_1202_4748_gb300._build``).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbfluct.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("liblbfluct.so is not built (expected at %s); build it with "
+                      "`python -m paper_1202_4748_gb300._build`" % LIB_PATH)
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---- constants (include/lbfluct.h) ------------------------------------------------
+LB_OK = 0
+LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_WORKSPACE = -1, -2, -3
+LB_ERR_NONPOSITIVE_DENSITY, LB_ERR_NOISE_NOT_PD, LB_ERR_NONFINITE = -4, -5, -6
+LB_ERR_UNSUPPORTED, LB_ERR_STATE, LB_ERR_IO = -7, -8, -9
+LB_D2Q9, LB_D3Q19 = 0, 1
+LB_MODEQ, LB_GUO = 0, 1
+LB_FP64, LB_FP32_DEVIATION = 0, 1
+LB_INIT_UNIFORM_NOISE, LB_INIT_FROM_RHO = 0, 1
+LB_MAX_Q = 19
+LB_MAX_LEVELS = 32
+Q_OF = {LB_D2Q9: 9, LB_D3Q19: 19}
+
+
+class lb_system_desc(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int32), ("coupling", ctypes.c_int32),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("rho_c", ctypes.c_double), ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("kT", ctypes.c_double),
+                ("tau", ctypes.c_double * LB_MAX_Q),
+                ("seed", ctypes.c_uint64), ("system_id", ctypes.c_uint32)]
+
+
+class lb_run_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("obs_every", ctypes.c_int32),
+                ("sk_every", ctypes.c_int32), ("graph_chunk", ctypes.c_int32),
+                ("tile", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32)]
+
+
+class lb_obs_level(ctypes.Structure):
+    _fields_ = [("bx", ctypes.c_int32), ("by", ctypes.c_int32), ("bz", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("n", ctypes.c_double),
+                ("sum_m", ctypes.c_double), ("sum_m2", ctypes.c_double),
+                ("sum_abs_m", ctypes.c_double), ("sum_m4", ctypes.c_double),
+                ("sum_e", ctypes.c_double), ("sum_e2", ctypes.c_double)]
+
+
+class lb_obs_global(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("n_samples", ctypes.c_int64),
+                ("mass0", ctypes.c_double), ("mass", ctypes.c_double),
+                ("momentum", ctypes.c_double * 3), ("rho_mean", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_SIG = {
+    "lb_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(lb_system_desc), ctypes.c_int,
+                                          ctypes.POINTER(lb_run_opts), ctypes.POINTER(ctypes.c_size_t)]),
+    "lb_create": (ctypes.c_int, [ctypes.POINTER(lb_system_desc), ctypes.c_int, ctypes.POINTER(lb_run_opts),
+                                 _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    "lb_init": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, _P]),
+    "lb_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "lb_sync": (ctypes.c_int, [_P]),
+    "lb_observables": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(lb_obs_level), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(lb_obs_global)]),
+    "lb_derive": (ctypes.c_int, [ctypes.POINTER(lb_obs_level), ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "lb_structure_factor": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+    "lb_read_fields": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "lb_write_fields": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "lb_get_step": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "lb_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "lb_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "lb_kernel_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "lb_destroy": (None, [_P]),
+    "lb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "lb_version": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _SIG.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+    globals()[_name] = _fn
+
+EXPORTED = tuple(_SIG)
+
+
+class LBError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        msg = lb_status_string(status).decode()
+        super().__init__("%s: %s (%d)" % (where, msg, status) if where else "%s (%d)" % (msg, status))
+
+
+def check(status, where=""):
+    if status != LB_OK:
+        raise LBError(status, where)
+    return status
+
+
+# ---- marshalling helpers ---------------------------------------------------------
+_LATTICE = {"D2Q9": LB_D2Q9, "D3Q19": LB_D3Q19}
+_COUPLING = {"modeq": LB_MODEQ, "guo": LB_GUO}
+
+
+def make_desc(systems):
+    """ctypes array of lb_system_desc from a list of dicts (synth.system format)."""
+    arr = (lb_system_desc * len(systems))()
+    for k, s in enumerate(systems):
+        d = arr[k]
+        d.lattice = _LATTICE[s["lattice"]] if isinstance(s["lattice"], str) else int(s["lattice"])
+        d.coupling = _COUPLING[s["coupling"]] if isinstance(s["coupling"], str) else int(s["coupling"])
+        d.nx, d.ny, d.nz = int(s["nx"]), int(s["ny"]), int(s["nz"])
+        d.rho_c, d.a, d.b = float(s["rho_c"]), float(s["a"]), float(s["b"])
+        d.kappa, d.kT = float(s["kappa"]), float(s["kT"])
+        for i, v in enumerate(s["tau"]):
+            d.tau[i] = float(v)
+        d.seed = int(s["seed"])
+        d.system_id = int(s["system_id"])
+    return arr
+
+
+def make_opts(precision="fp64", obs_every=0, sk_every=0, graph_chunk=0, tile=(0, 0, 0)):
+    o = lb_run_opts()
+    o.precision = {"fp64": LB_FP64, "fp32": LB_FP32_DEVIATION}.get(precision, precision)
+    o.obs_every, o.sk_every, o.graph_chunk = int(obs_every), int(sk_every), int(graph_chunk)
+    for k in range(3):
+        o.tile[k] = int(tile[k])
+    return o
+
+
+def workspace_bytes(systems, **opts):
+    desc = make_desc(systems)
+    o = make_opts(**opts)
+    n = ctypes.c_size_t()
+    check(lb_workspace_bytes(desc, len(systems), ctypes.byref(o), ctypes.byref(n)), "lb_workspace_bytes")
+    return n.value
+
+
+class Ensemble:
+    """An lb_ctx over a torch-allocated workspace on the current CUDA stream."""
+
+    def __init__(self, systems, device=None, stream=None, **opts):
+        import torch
+        self.systems = [dict(s) for s in systems]
+        self.q = 9 if self.systems[0]["lattice"] in ("D2Q9", LB_D2Q9) else 19
+        self._desc = make_desc(self.systems)
+        self._opts = make_opts(**opts)
+        n = ctypes.c_size_t()
+        check(lb_workspace_bytes(self._desc, len(systems), ctypes.byref(self._opts), ctypes.byref(n)),
+              "lb_workspace_bytes")
+        self.workspace_bytes = n.value
+        dev = torch.device("cuda" if device is None else device)
+        self.workspace = torch.empty(n.value, dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        ctx = _P()
+        check(lb_create(self._desc, len(systems), ctypes.byref(self._opts),
+                        _P(self.workspace.data_ptr()), n.value, _P(self.stream.cuda_stream),
+                        ctypes.byref(ctx)), "lb_create")
+        self.ctx = ctx
+
+    def shape(self, k):
+        s = self.systems[k]
+        return (int(s["nz"]), int(s["ny"]), int(s["nx"]))
+
+    def init(self, mode=LB_INIT_UNIFORM_NOISE, amplitude=0.01, rho=None):
+        ptr = None
+        if rho is not None:
+            self._rho = np.ascontiguousarray(rho, dtype=np.float64)
+            ptr = self._rho.ctypes.data_as(_P)
+            mode = LB_INIT_FROM_RHO
+        check(lb_init(self.ctx, mode, float(amplitude), ptr), "lb_init")
+
+    def step(self, n):
+        check(lb_step(self.ctx, int(n)), "lb_step")
+
+    def sync(self):
+        check(lb_sync(self.ctx), "lb_sync")
+
+    def get_step(self):
+        v = ctypes.c_int64()
+        check(lb_get_step(self.ctx, ctypes.byref(v)), "lb_get_step")
+        return v.value
+
+    def observables(self, k):
+        lv = (lb_obs_level * LB_MAX_LEVELS)()
+        n = ctypes.c_int()
+        g = lb_obs_global()
+        check(lb_observables(self.ctx, k, lv, LB_MAX_LEVELS, ctypes.byref(n), ctypes.byref(g)), "lb_observables")
+        levels = []
+        for l in range(n.value):
+            L = lv[l]
+            levels.append(dict(block=(L.bx, L.by, L.bz), n=L.n, sum_m=L.sum_m, sum_m2=L.sum_m2,
+                               sum_abs_m=L.sum_abs_m, sum_m4=L.sum_m4, sum_e=L.sum_e, sum_e2=L.sum_e2))
+        glob = dict(step=g.step, n_samples=g.n_samples, mass0=g.mass0, mass=g.mass,
+                    momentum=tuple(g.momentum), rho_mean=g.rho_mean)
+        return levels, glob
+
+    def derive(self, level, kT):
+        L = lb_obs_level()
+        L.bx, L.by, L.bz = level["block"]
+        for f in ("n", "sum_m", "sum_m2", "sum_abs_m", "sum_m4", "sum_e", "sum_e2"):
+            setattr(L, f, level[f])
+        out = (ctypes.c_double * 6)()
+        check(lb_derive(ctypes.byref(L), float(kT), out), "lb_derive")
+        return dict(M_L=out[0], chi_L=out[1], chi_L_lowT=out[2], c_HL=out[3], U_L=out[4], mean_m=out[5])
+
+    def structure_factor(self, k, nbins):
+        s = np.zeros(nbins)
+        c = np.zeros(nbins, dtype=np.int64)
+        ns = ctypes.c_int64()
+        check(lb_structure_factor(self.ctx, k, s.ctypes.data_as(_P), c.ctypes.data_as(_P), nbins,
+                                  ctypes.byref(ns)), "lb_structure_factor")
+        return s, c, ns.value
+
+    def read_fields(self, k):
+        out = np.empty((self.q,) + self.shape(k), dtype=np.float64)
+        check(lb_read_fields(self.ctx, k, out.ctypes.data_as(_P)), "lb_read_fields")
+        return out
+
+    def write_fields(self, k, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (self.q,) + self.shape(k)
+        check(lb_write_fields(self.ctx, k, f.ctypes.data_as(_P)), "lb_write_fields")
+
+    def kernel_launches(self):
+        v = ctypes.c_int64()
+        check(lb_kernel_launches(self.ctx, ctypes.byref(v)), "lb_kernel_launches")
+        return v.value
+
+    def save(self, path):
+        check(lb_save(self.ctx, os.fsencode(path)), "lb_save")
+
+    def load(self, path):
+        check(lb_load(self.ctx, os.fsencode(path)), "lb_load")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

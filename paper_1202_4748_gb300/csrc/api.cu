@@ -1,0 +1,837 @@
+// C ABI of the fluctuating lattice Boltzmann library (declared in include/lbfluct.h).
+//
+// Host responsibilities: validate descriptors, carve the caller's device
+// workspace, build the work lists (step tiles, site chunks, observable block
+// items), order the launches on the caller's stream, optionally capture step
+// chunks in CUDA graphs, and move data between host and device for I/O.
+// Every arithmetic step of the method runs in the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbfluct.h"
+#include "lb_launch.h"
+
+using namespace lbf;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct LevelHost {
+    int bx, by, bz, gx, gy, gz;
+    int64_t nblocks;
+    bool pyramid;   // part of the halving pyramid (else: the separate single-site level)
+};
+
+struct SysHost {
+    lb_system_desc d;
+    int64_t n = 0, site_off = 0, pop_off = 0;
+    std::vector<LevelHost> lv;
+    int imax = 0;          // bottom pyramid level index
+    bool unit_sep = false; // single-site level appended after the pyramid
+    int lv_first = 0;      // index of level 0 in the flattened LevelDev array
+};
+
+// Byte offsets of every region inside the workspace.
+struct Plan {
+    size_t sys, tiles, pop0, pop1, step, status, d, dbar, site_items, site_partial, spans, red4, glob, levels,
+        S, E, bottom_items, up_items, rec, acc, field_tmp, total;
+    int n_tiles = 0, n_site_items = 0, n_levels = 0, n_bottom = 0, n_up = 0, n_rec = 0, max_depth = 0;
+    int64_t n_sites = 0, n_blocks_pyr = 0, max_sites = 0;
+    std::vector<int4> tiles_h, site_items_h;
+    std::vector<SysSpan> spans_h;
+    std::vector<LevelDev> levels_h;
+    std::vector<ObsItem> bottom_h, up_h;
+    std::vector<int> up_first;   // up items of depth u: [up_first[u-1], up_first[u])
+};
+
+int q_of(int lattice) { return lattice == LB_D2Q9 ? 9 : 19; }
+
+lb_status validate(const lb_system_desc* s, int n, const lb_run_opts* o) {
+    if (!s || n <= 0 || !o) return LB_ERR_ARG;
+    if (o->precision != LB_FP64 && o->precision != LB_FP32_DEVIATION) return LB_ERR_ARG;
+    if (o->obs_every < 0 || o->sk_every < 0 || o->graph_chunk < 0 || (o->graph_chunk & 1)) return LB_ERR_ARG;
+    for (int k = 0; k < n; ++k) {
+        const lb_system_desc& d = s[k];
+        if (d.lattice != s[0].lattice || d.coupling != s[0].coupling) return LB_ERR_ARG;
+        if (d.lattice != LB_D2Q9 && d.lattice != LB_D3Q19) return LB_ERR_ARG;
+        if (d.coupling != LB_MODEQ && d.coupling != LB_GUO) return LB_ERR_ARG;
+        if (d.coupling == LB_MODEQ && d.lattice != LB_D2Q9) return LB_ERR_ARG;
+        if (d.nx < 1 || d.ny < 1 || d.nz < 1) return LB_ERR_ARG;
+        if (d.lattice == LB_D2Q9 && d.nz != 1) return LB_ERR_ARG;
+        if (int64_t(d.nx) * d.ny * d.nz >= (int64_t(1) << 31)) return LB_ERR_ARG;
+        if (!(d.rho_c > 0) || !std::isfinite(d.a) || !std::isfinite(d.b) || !(d.kappa >= 0) || !(d.kT >= 0) ||
+            !std::isfinite(d.kT) || !std::isfinite(d.kappa))
+            return LB_ERR_ARG;
+        if (d.system_id >= (1u << 24)) return LB_ERR_ARG;
+        const int q = q_of(d.lattice), nc = d.lattice == LB_D2Q9 ? 3 : 4;
+        for (int a = nc; a < q; ++a)
+            if (!(d.tau[a] > 0.5) || !std::isfinite(d.tau[a])) return LB_ERR_ARG;
+    }
+    return LB_OK;
+}
+
+std::vector<LevelHost> make_levels(const lb_system_desc& d, int& imax, bool& unit_sep) {
+    const bool dims3 = d.lattice == LB_D3Q19;
+    std::vector<LevelHost> out;
+    for (int i = 0;; ++i) {
+        const int64_t p = int64_t(1) << i;
+        if (d.nx % p || d.ny % p || (dims3 && d.nz % p)) break;
+        LevelHost L;
+        L.bx = int(d.nx / p);
+        L.by = int(d.ny / p);
+        L.bz = dims3 ? int(d.nz / p) : 1;
+        L.gx = int(p);
+        L.gy = int(p);
+        L.gz = dims3 ? int(p) : 1;
+        L.nblocks = int64_t(L.gx) * L.gy * L.gz;
+        L.pyramid = true;
+        out.push_back(L);
+        if (L.bx == 1 && L.by == 1 && L.bz == 1) break;
+        if (i > 30) break;
+    }
+    imax = int(out.size()) - 1;
+    unit_sep = !(out.back().bx == 1 && out.back().by == 1 && out.back().bz == 1);
+    if (unit_sep) {
+        LevelHost L;
+        L.bx = L.by = L.bz = 1;
+        L.gx = d.nx;
+        L.gy = d.ny;
+        L.gz = d.nz;
+        L.nblocks = int64_t(d.nx) * d.ny * d.nz;
+        L.pyramid = false;
+        out.push_back(L);
+    }
+    return out;
+}
+
+int tile_table(int lattice, int (*t)[3]) {
+    return lattice == LB_D2Q9 ? tile_shapes_d2q9(t, 16) : tile_shapes_d3q19(t, 16);
+}
+
+lb_status choose_tile(int lattice, const lb_run_opts* o, int& tile_id, int tdim[3]) {
+    int t[16][3];
+    const int nt = tile_table(lattice, t);
+    tile_id = 0;
+    if (o->tile[0] > 0) {
+        tile_id = -1;
+        for (int k = 0; k < nt; ++k)
+            if (t[k][0] == o->tile[0] && t[k][1] == o->tile[1] && t[k][2] == (o->tile[2] > 0 ? o->tile[2] : 1))
+                tile_id = k;
+        if (tile_id < 0) return LB_ERR_UNSUPPORTED;
+    }
+    for (int k = 0; k < 3; ++k) tdim[k] = t[tile_id][k];
+    return LB_OK;
+}
+
+lb_status make_plan(const lb_system_desc* s, int n, const lb_run_opts* o, std::vector<SysHost>& sys, Plan& P,
+                    int& tile_id) {
+    lb_status st = validate(s, n, o);
+    if (st != LB_OK) return st;
+    int tdim[3];
+    st = choose_tile(s[0].lattice, o, tile_id, tdim);
+    if (st != LB_OK) return st;
+    const int q = q_of(s[0].lattice);
+    const size_t es = o->precision == LB_FP64 ? 8 : 4;
+    sys.assign(n, SysHost());
+    int64_t site_off = 0;
+    int lv_count = 0;
+    for (int k = 0; k < n; ++k) {
+        SysHost& h = sys[k];
+        h.d = s[k];
+        h.n = int64_t(s[k].nx) * s[k].ny * s[k].nz;
+        h.site_off = site_off;
+        h.pop_off = site_off * q;
+        site_off += h.n;
+        h.lv = make_levels(s[k], h.imax, h.unit_sep);
+        h.lv_first = lv_count;
+        lv_count += int(h.lv.size());
+        P.max_sites = std::max(P.max_sites, h.n);
+    }
+    P.n_sites = site_off;
+    P.n_levels = lv_count;
+
+    // step tiles, system by system
+    for (int k = 0; k < n; ++k) {
+        const lb_system_desc& d = s[k];
+        for (int z = 0; z < d.nz; z += tdim[2])
+            for (int y = 0; y < d.ny; y += tdim[1])
+                for (int x = 0; x < d.nx; x += tdim[0]) P.tiles_h.push_back(make_int4(k, x, y, z));
+    }
+    P.n_tiles = int(P.tiles_h.size());
+
+    // site chunks
+    const int chunk = AUX_THREADS * SITES_PER_THREAD;
+    for (int k = 0; k < n; ++k) {
+        SysSpan sp{int(P.site_items_h.size()), 0};
+        for (int64_t b = 0; b < sys[k].n; b += chunk)
+            P.site_items_h.push_back(make_int4(k, int(b), int(std::min<int64_t>(b + chunk, sys[k].n)), 0));
+        sp.count = int(P.site_items_h.size()) - sp.first;
+        P.spans_h.push_back(sp);
+    }
+    P.n_site_items = int(P.site_items_h.size());
+
+    // observable levels, items and records
+    const int bchunk = OBS_THREADS * BLOCKS_PER_THREAD;
+    int64_t blk_off = 0;
+    P.levels_h.resize(lv_count);
+    for (int k = 0; k < n; ++k) {
+        SysHost& h = sys[k];
+        for (size_t l = 0; l < h.lv.size(); ++l) {
+            const LevelHost& L = h.lv[l];
+            LevelDev& D = P.levels_h[h.lv_first + l];
+            D.sys = k;
+            D.bx = L.bx;
+            D.by = L.by;
+            D.bz = L.bz;
+            D.gx = L.gx;
+            D.gy = L.gy;
+            D.gz = L.gz;
+            D.nblocks = L.nblocks;
+            D.child = (L.pyramid && int(l) < h.imax) ? h.lv_first + int(l) + 1 : -1;
+            D.off = L.pyramid ? blk_off : -1;
+            if (L.pyramid) blk_off += L.nblocks;
+            D.rec_first = 0;
+            D.rec_count = 0;
+        }
+    }
+    P.n_blocks_pyr = blk_off;
+    int rec = 0;
+    // bottom items (records of the bottom level, then of the unit level)
+    for (int k = 0; k < n; ++k) {
+        SysHost& h = sys[k];
+        LevelDev& B = P.levels_h[h.lv_first + h.imax];
+        const int first = int(P.bottom_h.size());
+        for (int64_t b = 0; b < B.nblocks; b += bchunk) {
+            ObsItem it;
+            it.level = h.lv_first + h.imax;
+            it.unit_level = h.unit_sep ? h.lv_first + h.imax + 1 : -1;
+            it.b0 = b;
+            it.b1 = std::min<int64_t>(b + bchunk, B.nblocks);
+            it.rec = -1;
+            it.rec2 = -1;
+            P.bottom_h.push_back(it);
+        }
+        const int cnt = int(P.bottom_h.size()) - first;
+        B.rec_first = rec;
+        B.rec_count = cnt;
+        for (int j = 0; j < cnt; ++j) P.bottom_h[first + j].rec = rec + j;
+        rec += cnt;
+        if (h.unit_sep) {
+            LevelDev& U = P.levels_h[h.lv_first + h.imax + 1];
+            U.rec_first = rec;
+            U.rec_count = cnt;
+            for (int j = 0; j < cnt; ++j) P.bottom_h[first + j].rec2 = rec + j;
+            rec += cnt;
+        }
+    }
+    // up items grouped by depth u = 1..max_depth (level imax - u of each system)
+    int max_depth = 0;
+    for (auto& h : sys) max_depth = std::max(max_depth, h.imax);
+    P.max_depth = max_depth;
+    P.up_first.push_back(0);
+    for (int u = 1; u <= max_depth; ++u) {
+        for (int k = 0; k < n; ++k) {
+            SysHost& h = sys[k];
+            const int l = h.imax - u;
+            if (l < 0) continue;
+            LevelDev& D = P.levels_h[h.lv_first + l];
+            D.rec_first = rec;
+            for (int64_t b = 0; b < D.nblocks; b += bchunk) {
+                ObsItem it;
+                it.level = h.lv_first + l;
+                it.unit_level = -1;
+                it.b0 = b;
+                it.b1 = std::min<int64_t>(b + bchunk, D.nblocks);
+                it.rec = rec++;
+                it.rec2 = -1;
+                P.up_h.push_back(it);
+            }
+            D.rec_count = rec - D.rec_first;
+        }
+        P.up_first.push_back(int(P.up_h.size()));
+    }
+    P.n_bottom = int(P.bottom_h.size());
+    P.n_up = int(P.up_h.size());
+    P.n_rec = rec;
+
+    // byte layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + std::max<size_t>(bytes, 1));
+        return at;
+    };
+    P.sys = take(sizeof(SysDev) * n);
+    P.tiles = take(sizeof(int4) * P.n_tiles);
+    P.pop0 = take(es * q * P.n_sites);
+    P.pop1 = take(es * q * P.n_sites);
+    P.step = take(sizeof(int64_t));
+    P.status = take(sizeof(int));
+    P.d = take(sizeof(double) * P.n_sites);
+    P.dbar = take(sizeof(double) * n);
+    P.site_items = take(sizeof(int4) * P.n_site_items);
+    P.site_partial = take(sizeof(double) * 4 * P.n_site_items);
+    P.spans = take(sizeof(SysSpan) * n);
+    P.red4 = take(sizeof(double) * 4 * n);
+    P.glob = take(sizeof(double) * 8 * n);
+    P.levels = take(sizeof(LevelDev) * P.n_levels);
+    P.S = take(sizeof(double) * P.n_blocks_pyr);
+    P.E = take(sizeof(double) * P.n_blocks_pyr);
+    P.bottom_items = take(sizeof(ObsItem) * P.n_bottom);
+    P.up_items = take(sizeof(ObsItem) * P.n_up);
+    P.rec = take(sizeof(double) * REC * P.n_rec);
+    P.acc = take(sizeof(double) * 7 * P.n_levels);
+    P.field_tmp = take(sizeof(double) * P.max_sites);
+    P.total = off;
+    return LB_OK;
+}
+
+SysDev to_dev(const SysHost& h) {
+    SysDev s;
+    std::memset(&s, 0, sizeof(s));
+    const lb_system_desc& d = h.d;
+    const int q = q_of(d.lattice), nc = d.lattice == LB_D2Q9 ? 3 : 4;
+    const int H = d.coupling == LB_GUO ? 2 : 1;
+    s.nx = d.nx;
+    s.ny = d.ny;
+    s.nz = d.nz;
+    s.small = (d.nx < H + 1 || d.ny < H + 1 || (d.lattice == LB_D3Q19 && d.nz < H + 1)) ? 1 : 0;
+    s.n_sites = h.n;
+    s.site_offset = h.site_off;
+    s.pop_offset = h.pop_off;
+    s.rho_c = d.rho_c;
+    s.a = d.a;
+    s.b = d.b;
+    s.kappa = d.kappa;
+    s.kT = d.kT;
+    s.inv_rho_c = 1.0 / d.rho_c;
+    s.nu = d.lattice == LB_D2Q9 ? (d.tau[4] - 0.5) / 3.0 : 0.0;
+    double gamma[LB_MAX_Q];
+    for (int a = 0; a < q; ++a) {
+        s.lam[a] = a < nc ? 0.0 : 1.0 / d.tau[a];
+        gamma[a] = 1.0 - s.lam[a];
+        s.g_diag[a] = 1.0 - gamma[a] * gamma[a];
+    }
+    const int P = d.lattice == LB_D2Q9 ? 3 : 4, R = d.lattice == LB_D2Q9 ? 8 : 16;
+    s.g_pair = 1.0 - gamma[P] * gamma[R];
+    s.seed_lo = uint32_t(d.seed & 0xffffffffu);
+    s.seed_hi = uint32_t(d.seed >> 32);
+    s.system_id = d.system_id;
+    return s;
+}
+
+}  // namespace
+
+struct lb_ctx {
+    int lattice = 0, coupling = 0, fp32 = 0, q = 9, n_sys = 0, tile_id = 0;
+    lb_run_opts opts{};
+    std::vector<SysHost> sys;
+    Plan P;
+    cudaStream_t stream = nullptr;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    int64_t step = 0;
+    bool has_state = false;
+    lb_status sticky = LB_OK;
+    // graph cache: [parity], with the number of kernel nodes of each
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_kernels[2] = {0, 0};
+    int64_t launches = 0;       // kernels launched (host-side count)
+
+    template <class T>
+    T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+    void* pop(int k) const { return ws + (k ? P.pop1 : P.pop0); }
+};
+
+namespace {
+
+#define LB_CHECK(expr)                                   \
+    do {                                                 \
+        cudaError_t e_ = (expr);                         \
+        if (e_ != cudaSuccess) return LB_ERR_CUDA;       \
+    } while (0)
+
+cudaError_t launch_step_any(lb_ctx* c, const StepLaunch& a) {
+    return c->lattice == LB_D2Q9 ? launch_step_d2q9(c->coupling, c->fp32, a, c->stream)
+                                 : launch_step_d3q19(c->coupling, c->fp32, a, c->stream);
+}
+
+// Observable sample of the state held in population buffer `buf`.
+cudaError_t sample_obs(lb_ctx* c, int buf, bool set_mass0, bool count) {
+    const Plan& P = c->P;
+    cudaError_t e;
+    const SysDev* sys = c->at<SysDev>(P.sys);
+    e = c->lattice == LB_D2Q9
+            ? launch_obs_site_d2q9(c->fp32, sys, c->at<int4>(P.site_items), P.n_site_items, c->pop(buf),
+                                   c->at<double>(P.d), c->at<double>(P.site_partial), c->stream)
+            : launch_obs_site_d3q19(c->fp32, sys, c->at<int4>(P.site_items), P.n_site_items, c->pop(buf),
+                                    c->at<double>(P.d), c->at<double>(P.site_partial), c->stream);
+    if (e != cudaSuccess) return e;
+    e = launch_reduce_sys(c->at<SysSpan>(P.spans), c->n_sys, c->at<double>(P.site_partial), 4, c->at<double>(P.red4),
+                          c->stream);
+    if (e != cudaSuccess) return e;
+    e = launch_obs_globals(sys, c->n_sys, c->at<double>(P.red4), c->at<double>(P.dbar), c->at<double>(P.glob),
+                           set_mass0 ? 1 : 0, count ? 1 : 0, c->stream);
+    c->launches += 3;
+    if (e != cudaSuccess || !count) return e;
+    c->launches += 2 + P.max_depth;
+    e = launch_pyr_bottom(sys, c->at<LevelDev>(P.levels), c->at<ObsItem>(P.bottom_items), P.n_bottom,
+                          c->at<double>(P.d), c->at<double>(P.dbar), c->at<double>(P.S), c->at<double>(P.E),
+                          c->at<double>(P.rec), c->stream);
+    if (e != cudaSuccess) return e;
+    for (int u = 1; u <= P.max_depth; ++u) {
+        const int first = P.up_first[u - 1], cnt = P.up_first[u] - first;
+        e = launch_pyr_up(sys, c->at<LevelDev>(P.levels), c->at<ObsItem>(P.up_items) + first, cnt,
+                          c->lattice == LB_D3Q19 ? 1 : 0, c->at<double>(P.S), c->at<double>(P.E),
+                          c->at<double>(P.rec), c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_obs_accum(c->at<LevelDev>(P.levels), P.n_levels, c->at<double>(P.rec), c->at<double>(P.acc),
+                            c->at<int>(P.status), c->stream);
+}
+
+// Launch `n` steps starting at host step c->step (device counter must equal it).
+cudaError_t launch_steps(lb_ctx* c, int64_t n) {
+    const Plan& P = c->P;
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t t = c->step + k;
+        StepLaunch a;
+        a.sys = c->at<SysDev>(P.sys);
+        a.tiles = c->at<int4>(P.tiles);
+        a.n_tiles = P.n_tiles;
+        a.fin = c->pop(int(t & 1));
+        a.fout = c->pop(int((t + 1) & 1));
+        a.step_ptr = c->at<int64_t>(P.step);
+        a.k = int(k);
+        a.status = c->at<int>(P.status);
+        a.tile_id = c->tile_id;
+        cudaError_t e = launch_step_any(c, a);
+        if (e != cudaSuccess) return e;
+        c->launches += 1;
+        const int64_t t1 = t + 1;
+        if (c->opts.obs_every > 0 && t1 % c->opts.obs_every == 0) {
+            e = sample_obs(c, int(t1 & 1), false, true);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    c->launches += 1;
+    return launch_advance(c->at<int64_t>(P.step), n, c->stream);
+}
+
+lb_status read_status(lb_ctx* c) {
+    int st = 0;
+    if (cudaMemcpyAsync(&st, c->at<int>(c->P.status), sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return LB_ERR_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LB_ERR_CUDA;
+    if (st & ST_RHO) return LB_ERR_NONPOSITIVE_DENSITY;
+    if (st & ST_NOISE) return LB_ERR_NOISE_NOT_PD;
+    if (st & ST_NONFINITE) return LB_ERR_NONFINITE;
+    return LB_OK;
+}
+
+lb_status sync_and_check(lb_ctx* c) {
+    lb_status s = read_status(c);
+    if (s != LB_OK && c->sticky == LB_OK) c->sticky = s;
+    return c->sticky != LB_OK ? c->sticky : s;
+}
+
+void drop_graphs(lb_ctx* c) {
+    for (auto& g : c->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+lb_status reset_accumulators(lb_ctx* c) {
+    const Plan& P = c->P;
+    LB_CHECK(cudaMemsetAsync(c->ws + P.acc, 0, sizeof(double) * 7 * P.n_levels, c->stream));
+    LB_CHECK(cudaMemsetAsync(c->ws + P.glob, 0, sizeof(double) * 8 * c->n_sys, c->stream));
+    LB_CHECK(cudaMemsetAsync(c->ws + P.status, 0, sizeof(int), c->stream));
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lb_version(void) { return "lbfluct 0.1 (sm_103a)"; }
+
+const char* lb_status_string(lb_status s) {
+    switch (s) {
+        case LB_OK: return "ok";
+        case LB_ERR_ARG: return "invalid argument";
+        case LB_ERR_CUDA: return "CUDA error";
+        case LB_ERR_WORKSPACE: return "workspace too small or misaligned";
+        case LB_ERR_NONPOSITIVE_DENSITY: return "non-positive density";
+        case LB_ERR_NOISE_NOT_PD: return "noise covariance not positive definite";
+        case LB_ERR_NONFINITE: return "non-finite observable";
+        case LB_ERR_UNSUPPORTED: return "unsupported combination";
+        case LB_ERR_STATE: return "invalid state (sticky error or missing initialisation)";
+        case LB_ERR_IO: return "checkpoint I/O error";
+    }
+    return "unknown status";
+}
+
+lb_status lb_workspace_bytes(const lb_system_desc* systems, int n_systems, const lb_run_opts* opts, size_t* bytes) {
+    if (!bytes) return LB_ERR_ARG;
+    std::vector<SysHost> sys;
+    Plan P;
+    int tile_id;
+    lb_status st = make_plan(systems, n_systems, opts, sys, P, tile_id);
+    if (st != LB_OK) return st;
+    *bytes = P.total;
+    return LB_OK;
+}
+
+lb_status lb_create(const lb_system_desc* systems, int n_systems, const lb_run_opts* opts, void* d_workspace,
+                    size_t bytes, void* stream, lb_ctx** out) {
+    if (!out) return LB_ERR_ARG;
+    *out = nullptr;
+    lb_ctx* c = new lb_ctx();
+    lb_status st = make_plan(systems, n_systems, opts, c->sys, c->P, c->tile_id);
+    if (st != LB_OK) {
+        delete c;
+        return st;
+    }
+    if (opts->sk_every > 0) {
+        delete c;
+        return LB_ERR_UNSUPPORTED;
+    }
+    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) || bytes < c->P.total) {
+        delete c;
+        return LB_ERR_WORKSPACE;
+    }
+    c->lattice = systems[0].lattice;
+    c->coupling = systems[0].coupling;
+    c->fp32 = opts->precision == LB_FP32_DEVIATION ? 1 : 0;
+    c->q = q_of(c->lattice);
+    c->n_sys = n_systems;
+    c->opts = *opts;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->ws = static_cast<char*>(d_workspace);
+    c->ws_bytes = bytes;
+    const Plan& P = c->P;
+    std::vector<SysDev> sd;
+    for (auto& h : c->sys) sd.push_back(to_dev(h));
+    bool ok = cudaMemcpyAsync(c->ws + P.sys, sd.data(), sizeof(SysDev) * sd.size(), cudaMemcpyHostToDevice,
+                              c->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(c->ws + P.tiles, P.tiles_h.data(), sizeof(int4) * P.n_tiles, cudaMemcpyHostToDevice,
+                               c->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(c->ws + P.site_items, P.site_items_h.data(), sizeof(int4) * P.n_site_items,
+                               cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(c->ws + P.spans, P.spans_h.data(), sizeof(SysSpan) * P.spans_h.size(),
+                               cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(c->ws + P.levels, P.levels_h.data(), sizeof(LevelDev) * P.n_levels,
+                               cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+    if (P.n_bottom)
+        ok = ok && cudaMemcpyAsync(c->ws + P.bottom_items, P.bottom_h.data(), sizeof(ObsItem) * P.n_bottom,
+                                   cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+    if (P.n_up)
+        ok = ok && cudaMemcpyAsync(c->ws + P.up_items, P.up_h.data(), sizeof(ObsItem) * P.n_up,
+                                   cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(c->ws + P.step, 0, sizeof(int64_t), c->stream) == cudaSuccess;
+    ok = ok && reset_accumulators(c) == LB_OK;
+    ok = ok && cudaStreamSynchronize(c->stream) == cudaSuccess;
+    if (!ok) {
+        delete c;
+        return LB_ERR_CUDA;
+    }
+    *out = c;
+    return LB_OK;
+}
+
+lb_status lb_init(lb_ctx* c, int mode, double amplitude, const double* h_rho) {
+    if (!c) return LB_ERR_ARG;
+    if (mode != LB_INIT_UNIFORM_NOISE && mode != LB_INIT_FROM_RHO) return LB_ERR_ARG;
+    if (mode == LB_INIT_FROM_RHO && !h_rho) return LB_ERR_ARG;
+    if (mode == LB_INIT_UNIFORM_NOISE && !(amplitude >= 0 && std::isfinite(amplitude))) return LB_ERR_ARG;
+    const Plan& P = c->P;
+    const SysDev* sys = c->at<SysDev>(P.sys);
+    drop_graphs(c);
+    c->step = 0;
+    LB_CHECK(cudaMemsetAsync(c->ws + P.step, 0, sizeof(int64_t), c->stream));
+    if (reset_accumulators(c) != LB_OK) return LB_ERR_CUDA;
+    if (mode == LB_INIT_UNIFORM_NOISE) {
+        LB_CHECK(launch_init_noise(sys, c->at<int4>(P.site_items), P.n_site_items, amplitude, c->at<double>(P.d),
+                                   c->at<double>(P.site_partial), c->stream));
+        LB_CHECK(launch_reduce_sys(c->at<SysSpan>(P.spans), c->n_sys, c->at<double>(P.site_partial), 4,
+                                   c->at<double>(P.red4), c->stream));
+        // dbar = sum d / n via the globals kernel (its mass fields are overwritten below)
+        LB_CHECK(launch_obs_globals(sys, c->n_sys, c->at<double>(P.red4), c->at<double>(P.dbar),
+                                    c->at<double>(P.glob), 1, 0, c->stream));
+    } else {
+        LB_CHECK(cudaMemcpyAsync(c->at<double>(P.d), h_rho, sizeof(double) * P.n_sites, cudaMemcpyHostToDevice,
+                                 c->stream));
+        LB_CHECK(launch_set_dbar(sys, c->n_sys, c->at<double>(P.dbar), c->stream));
+    }
+    LB_CHECK(c->lattice == LB_D2Q9
+                 ? launch_init_feq_d2q9(c->coupling, c->fp32, sys, c->at<int4>(P.site_items), P.n_site_items,
+                                        c->at<double>(P.d), c->at<double>(P.dbar), c->pop(0), c->stream)
+                 : launch_init_feq_d3q19(c->coupling, c->fp32, sys, c->at<int4>(P.site_items), P.n_site_items,
+                                         c->at<double>(P.d), c->at<double>(P.dbar), c->pop(0), c->stream));
+    LB_CHECK(sample_obs(c, 0, true, false));
+    LB_CHECK(cudaStreamSynchronize(c->stream));
+    c->sticky = LB_OK;
+    c->has_state = true;
+    return LB_OK;
+}
+
+lb_status lb_step(lb_ctx* c, int64_t nsteps) {
+    if (!c) return LB_ERR_ARG;
+    if (nsteps < 0) return LB_ERR_ARG;
+    if (!c->has_state || c->sticky != LB_OK) return LB_ERR_STATE;
+    if (nsteps == 0) return LB_OK;
+    const int C = c->opts.graph_chunk;
+    int64_t left = nsteps;
+    while (left > 0) {
+        const bool aligned = C > 0 && c->step % C == 0 && left >= C &&
+                             (c->opts.obs_every == 0 || C % c->opts.obs_every == 0);
+        if (!aligned) {
+            // plain launches up to the next chunk boundary (or all remaining)
+            int64_t n = left;
+            if (C > 0) {
+                const int64_t to_boundary = (C - c->step % C) % C;
+                n = to_boundary > 0 ? std::min(left, to_boundary) : left;
+                if (n >= C) n = left;   // never reached: aligned handles it
+            }
+            if (launch_steps(c, n) != cudaSuccess) return LB_ERR_CUDA;
+            c->step += n;
+            left -= n;
+            continue;
+        }
+        const int parity = int(c->step & 1);
+        if (!c->graph[parity]) {
+            cudaStream_t cap;
+            if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return LB_ERR_CUDA;
+            cudaStream_t saved = c->stream;
+            c->stream = cap;
+            cudaGraph_t g = nullptr;
+            const int64_t before = c->launches;
+            bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            ok = ok && launch_steps(c, C) == cudaSuccess;
+            c->graph_kernels[parity] = c->launches - before;
+            c->launches = before;
+            ok = (cudaStreamEndCapture(cap, &g) == cudaSuccess) && ok;
+            c->stream = saved;
+            ok = ok && cudaGraphInstantiate(&c->graph[parity], g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cap);
+            if (!ok) return LB_ERR_CUDA;
+        }
+        if (cudaGraphLaunch(c->graph[parity], c->stream) != cudaSuccess) return LB_ERR_CUDA;
+        c->launches += c->graph_kernels[parity];
+        c->step += C;
+        left -= C;
+    }
+    return LB_OK;
+}
+
+lb_status lb_sync(lb_ctx* c) {
+    if (!c) return LB_ERR_ARG;
+    return sync_and_check(c);
+}
+
+lb_status lb_get_step(lb_ctx* c, int64_t* step) {
+    if (!c || !step) return LB_ERR_ARG;
+    *step = c->step;
+    return LB_OK;
+}
+
+lb_status lb_observables(lb_ctx* c, int sys, lb_obs_level* h_levels, int max_levels, int* n_levels,
+                         lb_obs_global* h_global) {
+    if (!c || sys < 0 || sys >= c->n_sys || (!h_levels && max_levels > 0)) return LB_ERR_ARG;
+    const SysHost& h = c->sys[sys];
+    const int nl = int(h.lv.size());
+    std::vector<double> acc(7 * nl), glob(8);
+    LB_CHECK(cudaMemcpyAsync(acc.data(), c->at<double>(c->P.acc) + 7 * h.lv_first, sizeof(double) * 7 * nl,
+                             cudaMemcpyDeviceToHost, c->stream));
+    LB_CHECK(cudaMemcpyAsync(glob.data(), c->at<double>(c->P.glob) + 8 * sys, sizeof(double) * 8,
+                             cudaMemcpyDeviceToHost, c->stream));
+    lb_status s = sync_and_check(c);
+    if (n_levels) *n_levels = nl;
+    for (int l = 0; l < nl && l < max_levels; ++l) {
+        lb_obs_level& o = h_levels[l];
+        o.bx = h.lv[l].bx;
+        o.by = h.lv[l].by;
+        o.bz = h.lv[l].bz;
+        o.pad = 0;
+        o.n = acc[7 * l + 0];
+        o.sum_m = acc[7 * l + 1];
+        o.sum_m2 = acc[7 * l + 2];
+        o.sum_abs_m = acc[7 * l + 3];
+        o.sum_m4 = acc[7 * l + 4];
+        o.sum_e = acc[7 * l + 5];
+        o.sum_e2 = acc[7 * l + 6];
+    }
+    if (h_global) {
+        h_global->step = c->step;
+        h_global->n_samples = int64_t(glob[0]);
+        h_global->mass0 = glob[1];
+        h_global->mass = glob[2];
+        h_global->momentum[0] = glob[3];
+        h_global->momentum[1] = glob[4];
+        h_global->momentum[2] = glob[5];
+        h_global->rho_mean = glob[6];
+    }
+    return s;
+}
+
+lb_status lb_derive(const lb_obs_level* L, double kT, double out[6]) {
+    if (!L || !out || !(L->n > 0) || !(kT > 0)) return LB_ERR_ARG;
+    const double n = L->n, v = double(L->bx) * L->by * L->bz;
+    const double m = L->sum_m / n, m2 = L->sum_m2 / n, am = L->sum_abs_m / n, m4 = L->sum_m4 / n;
+    const double e = L->sum_e / n, e2 = L->sum_e2 / n;
+    out[0] = am;
+    out[1] = v / kT * (m2 - m * m);
+    out[2] = v / kT * (m2 - am * am);
+    out[3] = v / kT * (e2 - e * e);
+    out[4] = m2 > 0 ? 1.0 - m4 / (3.0 * m2 * m2) : NAN;
+    out[5] = m;
+    return LB_OK;
+}
+
+lb_status lb_structure_factor(lb_ctx* c, int sys, double* h_sum, int64_t* h_count, int nbins, int64_t* n_samples) {
+    (void)h_sum;
+    (void)h_count;
+    (void)nbins;
+    (void)n_samples;
+    if (!c || sys < 0 || sys >= c->n_sys) return LB_ERR_ARG;
+    return LB_ERR_UNSUPPORTED;
+}
+
+lb_status lb_read_fields(lb_ctx* c, int sys, double* h_f) {
+    if (!c || !h_f || sys < 0 || sys >= c->n_sys) return LB_ERR_ARG;
+    if (!c->has_state) return LB_ERR_STATE;
+    const SysHost& h = c->sys[sys];
+    const int buf = int(c->step & 1);
+    double* tmp = c->at<double>(c->P.field_tmp);
+    for (int i = 0; i < c->q; ++i) {
+        LB_CHECK(c->lattice == LB_D2Q9
+                     ? launch_gather_d2q9(c->fp32, c->at<SysDev>(c->P.sys), sys, i, h.n, c->pop(buf), tmp, c->stream)
+                     : launch_gather_d3q19(c->fp32, c->at<SysDev>(c->P.sys), sys, i, h.n, c->pop(buf), tmp,
+                                           c->stream));
+        LB_CHECK(cudaMemcpyAsync(h_f + int64_t(i) * h.n, tmp, sizeof(double) * h.n, cudaMemcpyDeviceToHost,
+                                 c->stream));
+    }
+    LB_CHECK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_write_fields(lb_ctx* c, int sys, const double* h_f) {
+    if (!c || !h_f || sys < 0 || sys >= c->n_sys) return LB_ERR_ARG;
+    const SysHost& h = c->sys[sys];
+    const int buf = int(c->step & 1);
+    double* tmp = c->at<double>(c->P.field_tmp);
+    for (int i = 0; i < c->q; ++i) {
+        LB_CHECK(cudaMemcpyAsync(tmp, h_f + int64_t(i) * h.n, sizeof(double) * h.n, cudaMemcpyHostToDevice,
+                                 c->stream));
+        LB_CHECK(c->lattice == LB_D2Q9
+                     ? launch_scatter_d2q9(c->fp32, c->at<SysDev>(c->P.sys), sys, i, h.n, tmp, c->pop(buf), c->stream)
+                     : launch_scatter_d3q19(c->fp32, c->at<SysDev>(c->P.sys), sys, i, h.n, tmp, c->pop(buf),
+                                            c->stream));
+    }
+    LB_CHECK(cudaMemsetAsync(c->ws + c->P.status, 0, sizeof(int), c->stream));
+    LB_CHECK(cudaStreamSynchronize(c->stream));
+    c->sticky = LB_OK;
+    c->has_state = true;
+    return LB_OK;
+}
+
+// Checkpoint file: header, descriptors, populations (raw), accumulators, globals.
+struct CkptHeader {
+    char magic[8];
+    int32_t version, lattice, coupling, fp32, n_sys, q;
+    int64_t step, n_sites, n_levels;
+};
+
+lb_status lb_save(lb_ctx* c, const char* path) {
+    if (!c || !path) return LB_ERR_ARG;
+    if (!c->has_state) return LB_ERR_STATE;
+    const Plan& P = c->P;
+    const size_t es = c->fp32 ? 4 : 8;
+    std::vector<char> pop(es * c->q * P.n_sites);
+    std::vector<double> acc(7 * P.n_levels), glob(8 * c->n_sys);
+    LB_CHECK(cudaMemcpyAsync(pop.data(), c->pop(int(c->step & 1)), pop.size(), cudaMemcpyDeviceToHost, c->stream));
+    LB_CHECK(cudaMemcpyAsync(acc.data(), c->ws + P.acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost,
+                             c->stream));
+    LB_CHECK(cudaMemcpyAsync(glob.data(), c->ws + P.glob, sizeof(double) * glob.size(), cudaMemcpyDeviceToHost,
+                             c->stream));
+    LB_CHECK(cudaStreamSynchronize(c->stream));
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return LB_ERR_IO;
+    CkptHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, "LBFLUCT1", 8);
+    hd.version = 1;
+    hd.lattice = c->lattice;
+    hd.coupling = c->coupling;
+    hd.fp32 = c->fp32;
+    hd.n_sys = c->n_sys;
+    hd.q = c->q;
+    hd.step = c->step;
+    hd.n_sites = P.n_sites;
+    hd.n_levels = P.n_levels;
+    bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1;
+    for (auto& h : c->sys) ok = ok && std::fwrite(&h.d, sizeof(lb_system_desc), 1, fp) == 1;
+    ok = ok && std::fwrite(pop.data(), 1, pop.size(), fp) == pop.size();
+    ok = ok && std::fwrite(acc.data(), sizeof(double), acc.size(), fp) == acc.size();
+    ok = ok && std::fwrite(glob.data(), sizeof(double), glob.size(), fp) == glob.size();
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? LB_OK : LB_ERR_IO;
+}
+
+lb_status lb_load(lb_ctx* c, const char* path) {
+    if (!c || !path) return LB_ERR_ARG;
+    const Plan& P = c->P;
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return LB_ERR_IO;
+    CkptHeader hd;
+    bool ok = std::fread(&hd, sizeof(hd), 1, fp) == 1 && std::memcmp(hd.magic, "LBFLUCT1", 8) == 0 &&
+              hd.version == 1 && hd.lattice == c->lattice && hd.coupling == c->coupling && hd.fp32 == c->fp32 &&
+              hd.n_sys == c->n_sys && hd.q == c->q && hd.n_sites == P.n_sites && hd.n_levels == P.n_levels;
+    for (int k = 0; ok && k < c->n_sys; ++k) {
+        lb_system_desc d;
+        ok = std::fread(&d, sizeof(d), 1, fp) == 1 && std::memcmp(&d, &c->sys[k].d, sizeof(d)) == 0;
+    }
+    const size_t es = c->fp32 ? 4 : 8;
+    std::vector<char> pop(es * c->q * P.n_sites);
+    std::vector<double> acc(7 * P.n_levels), glob(8 * c->n_sys);
+    ok = ok && std::fread(pop.data(), 1, pop.size(), fp) == pop.size();
+    ok = ok && std::fread(acc.data(), sizeof(double), acc.size(), fp) == acc.size();
+    ok = ok && std::fread(glob.data(), sizeof(double), glob.size(), fp) == glob.size();
+    std::fclose(fp);
+    if (!ok) return LB_ERR_IO;
+    drop_graphs(c);
+    c->step = hd.step;
+    LB_CHECK(cudaMemcpyAsync(c->pop(int(c->step & 1)), pop.data(), pop.size(), cudaMemcpyHostToDevice, c->stream));
+    LB_CHECK(cudaMemcpyAsync(c->ws + P.acc, acc.data(), sizeof(double) * acc.size(), cudaMemcpyHostToDevice,
+                             c->stream));
+    LB_CHECK(cudaMemcpyAsync(c->ws + P.glob, glob.data(), sizeof(double) * glob.size(), cudaMemcpyHostToDevice,
+                             c->stream));
+    LB_CHECK(cudaMemcpyAsync(c->ws + P.step, &c->step, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    LB_CHECK(cudaMemsetAsync(c->ws + P.status, 0, sizeof(int), c->stream));
+    LB_CHECK(cudaStreamSynchronize(c->stream));
+    c->sticky = LB_OK;
+    c->has_state = true;
+    return LB_OK;
+}
+
+lb_status lb_kernel_launches(lb_ctx* c, int64_t* count) {
+    if (!c || !count) return LB_ERR_ARG;
+    *count = c->launches;
+    return LB_OK;
+}
+
+void lb_destroy(lb_ctx* c) {
+    if (!c) return;
+    drop_graphs(c);
+    delete c;
+}
+
+}  // extern "C"

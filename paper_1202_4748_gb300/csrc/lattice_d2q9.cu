@@ -1,0 +1,55 @@
+// D2Q9 instantiations (the paper's lattice): modified equilibrium (Eq. 65)
+// and the Guo-forced form, FP64 and FP32-deviation storage.
+#include "lattice_tu.cuh"
+
+namespace lbf {
+
+namespace {
+constexpr int kTiles[][3] = {{32, 8, 1}, {64, 4, 1}, {128, 2, 1}};
+constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
+
+template <int CP, class Real>
+cudaError_t step_tile(const StepLaunch& a, cudaStream_t st) {
+    switch (a.tile_id) {
+        case 0: return step_one<D2Q9, CP, Real, 32, 8, 1>(a, st);
+        case 1: return step_one<D2Q9, CP, Real, 64, 4, 1>(a, st);
+        case 2: return step_one<D2Q9, CP, Real, 128, 2, 1>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace
+
+int tile_shapes_d2q9(int (*out)[3], int max) {
+    for (int t = 0; t < kNumTiles && t < max; ++t)
+        for (int k = 0; k < 3; ++k) out[t][k] = kTiles[t][k];
+    return kNumTiles;
+}
+
+cudaError_t launch_step_d2q9(int coupling, int fp32, const StepLaunch& a, cudaStream_t st) {
+    if (a.n_tiles == 0) return cudaSuccess;
+    if (coupling == MODEQ) return fp32 ? step_tile<MODEQ, float>(a, st) : step_tile<MODEQ, double>(a, st);
+    return fp32 ? step_tile<GUO, float>(a, st) : step_tile<GUO, double>(a, st);
+}
+
+cudaError_t launch_init_feq_d2q9(int coupling, int fp32, const SysDev* sys, const int4* items, int n_items,
+                                 const double* d, const double* dbar, void* fbuf, cudaStream_t st) {
+    return fp32 ? init_feq_any<D2Q9, float>(coupling, sys, items, n_items, d, dbar, fbuf, st)
+                : init_feq_any<D2Q9, double>(coupling, sys, items, n_items, d, dbar, fbuf, st);
+}
+cudaError_t launch_gather_d2q9(int fp32, const SysDev* sys, int s, int i, int64_t n, const void* fbuf, double* out,
+                               cudaStream_t st) {
+    return fp32 ? gather_any<D2Q9, float>(sys, s, i, n, fbuf, out, st)
+                : gather_any<D2Q9, double>(sys, s, i, n, fbuf, out, st);
+}
+cudaError_t launch_scatter_d2q9(int fp32, const SysDev* sys, int s, int i, int64_t n, const double* in, void* fbuf,
+                                cudaStream_t st) {
+    return fp32 ? scatter_any<D2Q9, float>(sys, s, i, n, in, fbuf, st)
+                : scatter_any<D2Q9, double>(sys, s, i, n, in, fbuf, st);
+}
+cudaError_t launch_obs_site_d2q9(int fp32, const SysDev* sys, const int4* items, int n_items, const void* fbuf,
+                                 double* d, double* partial, cudaStream_t st) {
+    return fp32 ? obs_site_any<D2Q9, float>(sys, items, n_items, fbuf, d, partial, st)
+                : obs_site_any<D2Q9, double>(sys, items, n_items, fbuf, d, partial, st);
+}
+
+}  // namespace lbf

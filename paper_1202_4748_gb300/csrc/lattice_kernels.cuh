@@ -1,0 +1,190 @@
+// Lattice-dependent auxiliary kernels: initial equilibrium, population
+// gather/scatter for host I/O, and the per-site pass of the observables.
+// All reductions are fixed-order (per thread sequential, then a shared-memory
+// tree), so results are bitwise reproducible run to run.
+#pragma once
+
+#include "lb_device.cuh"
+#include "lb_launch.h"
+
+namespace lbf {
+
+// Work item of a site pass: (system, first site, end site, unused).
+// Deterministic sum of K doubles over the CTA; result valid in thread 0.
+template <int K, int NT>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* sh /* K * NT */) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k * NT + t] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int s = NT / 2; s > 0; s >>= 1) {
+        if (t < s) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) sh[k * NT + t] += sh[k * NT + t + s];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = sh[k * NT];
+}
+
+__device__ __forceinline__ void site_coords(int site, int nx, int ny, int& x, int& y, int& z) {
+    x = site % nx;
+    const int r = site / nx;
+    y = r % ny;
+    z = r / ny;
+}
+
+// f = f^eq(rho, u = 0, grad rho) at every site, written to the pull layout:
+// buf_i(r - c_i) = f_i(r, 0).  rho = rho_c + d - dbar (d in FP64 scratch).
+template <class L, int CP, class Real>
+__global__ void __launch_bounds__(AUX_THREADS)
+    init_feq_kernel(const SysDev* __restrict__ sysv, const int4* __restrict__ items, const double* __restrict__ d,
+                    const double* __restrict__ dbar, Real* __restrict__ fbuf) {
+    const int4 it = items[blockIdx.x];
+    const SysDev& S = sysv[it.x];
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const int64_t N = S.n_sites;
+    const double* ds = d + S.site_offset;
+    const double db = dbar[it.x];
+    for (int j = 0; j < SITES_PER_THREAD; ++j) {
+        const int site = it.y + j * AUX_THREADS + threadIdx.x;
+        if (site >= it.z) break;
+        int x, y, z;
+        site_coords(site, nx, ny, x, y, z);
+        auto nb = [&](int i) {
+            const int sx = wrapm(x + L::c(i, 0), nx), sy = wrapm(y + L::c(i, 1), ny);
+            const int sz = L::D == 3 ? wrapm(z + L::c(i, 2), nz) : 0;
+            return ds[sx + nx * (sy + ny * sz)] - db;
+        };
+        const double drho = ds[site] - db;
+        const double rho = S.rho_c + drho;
+        const double phi = drho * S.inv_rho_c;
+        const double df0 = phi * (S.a + S.b * phi * phi);
+        const double f0 = phi * phi * (0.5 * S.a + 0.25 * S.b * phi * phi);
+        const double p0 = rho * S.inv_rho_c * df0 - f0;
+        double feq[L::Q];
+        double s = 0.0;
+        if constexpr (CP == MODEQ) {
+            double gx = 0.0, gy = 0.0, lap = 0.0;
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i) {
+                const double rn = nb(i);
+                gx += 3.0 * L::w(i) * L::c(i, 0) * rn;
+                gy += 3.0 * L::w(i) * L::c(i, 1) * rn;
+                lap += 6.0 * L::w(i) * (rn - drho);
+            }
+            const double iso = p0 - S.kappa * rho * lap;
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i) {
+                feq[i] = pooley_w(i) * iso +
+                         S.kappa * (pooley_wxx(i) * gx * gx + pooley_wyy(i) * gy * gy + pooley_wxy(i) * gx * gy);
+                s += feq[i];
+            }
+        } else {
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i) {
+                feq[i] = 3.0 * L::w(i) * p0;
+                s += feq[i];
+            }
+        }
+        feq[0] = drho - s;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const int sx = wrapm(x - L::c(i, 0), nx), sy = wrapm(y - L::c(i, 1), ny);
+            const int sz = L::D == 3 ? wrapm(z - L::c(i, 2), nz) : 0;
+            fbuf[S.pop_offset + int64_t(i) * N + (sx + nx * (sy + ny * sz))] = Real(feq[i]);
+        }
+    }
+}
+
+// out[site] = f_i(r, t) = buf_i(r - c_i) + rho_c [i == 0], one population.
+template <class L, class Real>
+__global__ void __launch_bounds__(AUX_THREADS)
+    gather_kernel(const SysDev* __restrict__ sysv, int sys, int i, const Real* __restrict__ fbuf,
+                  double* __restrict__ out) {
+    const SysDev& S = sysv[sys];
+    const int64_t site = int64_t(blockIdx.x) * AUX_THREADS + threadIdx.x;
+    if (site >= S.n_sites) return;
+    int x, y, z;
+    site_coords(int(site), S.nx, S.ny, x, y, z);
+    int cx = 0, cy = 0, cz = 0;
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q)
+        if (q == i) {
+            cx = L::c(q, 0);
+            cy = L::c(q, 1);
+            cz = L::c(q, 2);
+        }
+    const int sx = wrapm(x - cx, S.nx), sy = wrapm(y - cy, S.ny), sz = wrapm(z - cz, S.nz);
+    const double v = double(fbuf[S.pop_offset + int64_t(i) * S.n_sites + (sx + S.nx * (sy + S.ny * sz))]);
+    out[site] = v + (i == 0 ? S.rho_c : 0.0);
+}
+
+// buf_i(r - c_i) = f_i(r) - rho_c [i == 0], one population.
+template <class L, class Real>
+__global__ void __launch_bounds__(AUX_THREADS)
+    scatter_kernel(const SysDev* __restrict__ sysv, int sys, int i, const double* __restrict__ in,
+                   Real* __restrict__ fbuf) {
+    const SysDev& S = sysv[sys];
+    const int64_t site = int64_t(blockIdx.x) * AUX_THREADS + threadIdx.x;
+    if (site >= S.n_sites) return;
+    int x, y, z;
+    site_coords(int(site), S.nx, S.ny, x, y, z);
+    int cx = 0, cy = 0, cz = 0;
+#pragma unroll
+    for (int q = 0; q < L::Q; ++q)
+        if (q == i) {
+            cx = L::c(q, 0);
+            cy = L::c(q, 1);
+            cz = L::c(q, 2);
+        }
+    const int sx = wrapm(x - cx, S.nx), sy = wrapm(y - cy, S.ny), sz = wrapm(z - cz, S.nz);
+    fbuf[S.pop_offset + int64_t(i) * S.n_sites + (sx + S.nx * (sy + S.ny * sz))] =
+        Real(in[site] - (i == 0 ? S.rho_c : 0.0));
+}
+
+// Observable site pass: d(r) = rho(r, t) - rho_c = sum_i delta f_i(r - c_i) and
+// j(r) = sum_i c_i f_i(r - c_i), summed in FP64.  Writes d and per-item
+// partial sums (sum d, sum jx, sum jy, sum jz).
+template <class L, class Real>
+__global__ void __launch_bounds__(AUX_THREADS)
+    obs_site_kernel(const SysDev* __restrict__ sysv, const int4* __restrict__ items, const Real* __restrict__ fbuf,
+                    double* __restrict__ d, double* __restrict__ partial) {
+    __shared__ double sh[4 * AUX_THREADS];
+    const int4 it = items[blockIdx.x];
+    const SysDev& S = sysv[it.x];
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const Real* fb = fbuf + S.pop_offset;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = 0; j < SITES_PER_THREAD; ++j) {
+        const int site = it.y + j * AUX_THREADS + threadIdx.x;
+        if (site >= it.z) break;
+        int x, y, z;
+        site_coords(site, nx, ny, x, y, z);
+        double r = 0.0, m[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const int sx = wrap1(x - L::c(i, 0), nx), sy = wrap1(y - L::c(i, 1), ny);
+            const int sz = L::D == 3 ? wrap1(z - L::c(i, 2), nz) : 0;
+            const double v = double(fb[int64_t(i) * S.n_sites + (sx + nx * (sy + ny * sz))]);
+            r += v;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (L::c(i, a) != 0) m[a] += L::c(i, a) * v;
+        }
+        d[S.site_offset + site] = r;
+        acc[0] += r;
+        acc[1] += m[0];
+        acc[2] += m[1];
+        acc[3] += m[2];
+    }
+    block_sum<4, AUX_THREADS>(acc, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) partial[int64_t(blockIdx.x) * 4 + k] = acc[k];
+    }
+}
+
+}  // namespace lbf

@@ -1,0 +1,62 @@
+// Shared body of the per-lattice translation units: tile-shape table and the
+// launchers for the step, init, gather/scatter and observable-site kernels.
+#pragma once
+
+#include "lattice_kernels.cuh"
+#include "lb_launch.h"
+#include "step_kernels.cuh"
+
+namespace lbf {
+
+template <class L, int CP, class Real, int TX, int TY, int TZ>
+cudaError_t step_one(const StepLaunch& a, cudaStream_t st) {
+    StepArgs<Real> A;
+    A.sys = a.sys;
+    A.tiles = a.tiles;
+    A.fin = static_cast<const Real*>(a.fin);
+    A.fout = static_cast<Real*>(a.fout);
+    A.step_ptr = a.step_ptr;
+    A.k = a.k;
+    A.status = a.status;
+    step_kernel<L, CP, Real, TX, TY, TZ><<<a.n_tiles, TX * TY * TZ, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+template <class L, class Real>
+cudaError_t init_feq_any(int coupling, const SysDev* sys, const int4* items, int n_items, const double* d,
+                         const double* dbar, void* fbuf, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    if (coupling == MODEQ) {
+        if constexpr (L::D == 2)
+            init_feq_kernel<L, MODEQ, Real><<<n_items, AUX_THREADS, 0, st>>>(sys, items, d, dbar, static_cast<Real*>(fbuf));
+        else
+            return cudaErrorInvalidValue;
+    } else {
+        init_feq_kernel<L, GUO, Real><<<n_items, AUX_THREADS, 0, st>>>(sys, items, d, dbar, static_cast<Real*>(fbuf));
+    }
+    return cudaGetLastError();
+}
+
+template <class L, class Real>
+cudaError_t gather_any(const SysDev* sys, int s, int i, int64_t n, const void* fbuf, double* out, cudaStream_t st) {
+    const unsigned grid = unsigned((n + AUX_THREADS - 1) / AUX_THREADS);
+    gather_kernel<L, Real><<<grid, AUX_THREADS, 0, st>>>(sys, s, i, static_cast<const Real*>(fbuf), out);
+    return cudaGetLastError();
+}
+
+template <class L, class Real>
+cudaError_t scatter_any(const SysDev* sys, int s, int i, int64_t n, const double* in, void* fbuf, cudaStream_t st) {
+    const unsigned grid = unsigned((n + AUX_THREADS - 1) / AUX_THREADS);
+    scatter_kernel<L, Real><<<grid, AUX_THREADS, 0, st>>>(sys, s, i, in, static_cast<Real*>(fbuf));
+    return cudaGetLastError();
+}
+
+template <class L, class Real>
+cudaError_t obs_site_any(const SysDev* sys, const int4* items, int n_items, const void* fbuf, double* d,
+                         double* partial, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    obs_site_kernel<L, Real><<<n_items, AUX_THREADS, 0, st>>>(sys, items, static_cast<const Real*>(fbuf), d, partial);
+    return cudaGetLastError();
+}
+
+}  // namespace lbf

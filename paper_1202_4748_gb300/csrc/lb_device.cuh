@@ -1,0 +1,221 @@
+// Device-side building blocks of the fluctuating lattice Boltzmann library:
+// velocity sets, moment bases, the Philox4x32-10 counter-based generator and
+// per-system parameters.  Written for sm_103a; everything is header-only and
+// templated so that each (lattice, coupling, precision) instantiation folds
+// its constant tables at compile time.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+#include <cuda_runtime.h>
+
+namespace lbf {
+
+constexpr int LB_MAX_Q_DEV = 19;
+
+// Compile-time loop: f(std::integral_constant<int, k>) for k = B .. E-1, so
+// that table entries indexed by k are constant expressions (folded by the
+// C++ front end, not by the optimiser).
+template <int B, int E, class F>
+__host__ __device__ __forceinline__ void sfor(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        sfor<B + 1, E>(static_cast<F&&>(f));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Velocity sets and moment bases
+// ---------------------------------------------------------------------------
+// D2Q9 (the paper's lattice, Sec. III A).  Rest velocity first, then the axis
+// pairs and the diagonal pairs (1,1)/(-1,-1) and (1,-1)/(-1,1) -- the order in
+// which the printed weights of Eq. 65 (w^xy = +1/4 on the 5th/6th, -1/4 on the
+// 7th/8th velocity) place them.
+//
+// Moment basis (Eq. 66 expands f_i = T_ai t_i m_a / N_a): rows
+//   1, cx, cy, 3c^2-2, cx^2-cy^2, cx cy, (3c^2-4)cx, (3c^2-4)cy, 9c^4-15c^2+2
+// whose squared lengths N = (1, 1/3, 1/3, 4, 4/9, 1/9, 2/3, 2/3, 16) are the
+// diagonal of Eq. 68 at c_s^2 = 1/3.
+struct D2Q9 {
+    static constexpr int Q = 9;
+    static constexpr int D = 2;
+    static constexpr int NC = 3;        // conserved moments: rho, jx, jy
+    static constexpr int PP = 3;        // the two non-conserved modes with a rest-
+    static constexpr int PR = 8;        // velocity component (coupled in Eq. 68)
+    __host__ __device__ static constexpr int c(int i, int a) {
+        constexpr int v[9][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
+                                 {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+        return v[i][a];
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+    __host__ __device__ static constexpr int T(int a, int i) {
+        const int x = c(i, 0), y = c(i, 1), c2 = x * x + y * y;
+        switch (a) {
+            case 0: return 1;
+            case 1: return x;
+            case 2: return y;
+            case 3: return 3 * c2 - 2;
+            case 4: return x * x - y * y;
+            case 5: return x * y;
+            case 6: return (3 * c2 - 4) * x;
+            case 7: return (3 * c2 - 4) * y;
+            default: return 9 * c2 * c2 - 15 * c2 + 2;
+        }
+    }
+};
+
+// D3Q19 (3-D variant): rest, 6 face and 12 edge velocities, weights 1/3,
+// 1/18, 1/36, and an orthogonal polynomial basis: rho, j, six second-order
+// stresses (c^2-1, 3cx^2-c^2, cy^2-cz^2, cx cy, cy cz, cz cx), nine ghosts
+// ((3c^2-5)c_a, (cy^2-cz^2)cx, (cz^2-cx^2)cy, (cx^2-cy^2)cz, 3c^4-6c^2+1,
+// (2c^2-3)(3cx^2-c^2), (2c^2-3)(cy^2-cz^2)).
+struct D3Q19 {
+    static constexpr int Q = 19;
+    static constexpr int D = 3;
+    static constexpr int NC = 4;
+    static constexpr int PP = 4;
+    static constexpr int PR = 16;
+    __host__ __device__ static constexpr int c(int i, int a) {
+        constexpr int v[19][3] = {{0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},  {0, -1, 0},
+                                  {0, 0, 1},   {0, 0, -1},  {1, 1, 0},   {-1, -1, 0}, {1, -1, 0},
+                                  {-1, 1, 0},  {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                  {0, 1, 1},   {0, -1, -1}, {0, 1, -1},  {0, -1, 1}};
+        return v[i][a];
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+    __host__ __device__ static constexpr int T(int a, int i) {
+        const int x = c(i, 0), y = c(i, 1), z = c(i, 2);
+        const int c2 = x * x + y * y + z * z;
+        switch (a) {
+            case 0: return 1;
+            case 1: return x;
+            case 2: return y;
+            case 3: return z;
+            case 4: return c2 - 1;
+            case 5: return 3 * x * x - c2;
+            case 6: return y * y - z * z;
+            case 7: return x * y;
+            case 8: return y * z;
+            case 9: return z * x;
+            case 10: return (3 * c2 - 5) * x;
+            case 11: return (3 * c2 - 5) * y;
+            case 12: return (3 * c2 - 5) * z;
+            case 13: return (y * y - z * z) * x;
+            case 14: return (z * z - x * x) * y;
+            case 15: return (x * x - y * y) * z;
+            case 16: return 3 * c2 * c2 - 6 * c2 + 1;
+            case 17: return (2 * c2 - 3) * (3 * x * x - c2);
+            default: return (2 * c2 - 3) * (y * y - z * z);
+        }
+    }
+};
+
+// Squared length N_a = sum_i t_i T_ai^2 and inverse-transform coefficients.
+template <class L>
+__host__ __device__ constexpr double norm2(int a) {
+    double s = 0.0;
+    for (int i = 0; i < L::Q; ++i) s += L::w(i) * double(L::T(a, i)) * double(L::T(a, i));
+    return s;
+}
+template <class L>
+__host__ __device__ constexpr double tinv(int i, int a) {
+    return L::w(i) * double(L::T(a, i)) / norm2<L>(a);
+}
+
+enum Coupling { MODEQ = 0, GUO = 1 };
+
+// Modified-equilibrium weights of Eq. 65 (D2Q9 order above; index 0 unused).
+__host__ __device__ constexpr double pooley_w(int i) { return i == 0 ? 0.0 : (i < 5 ? 1.0 / 3.0 : 1.0 / 12.0); }
+__host__ __device__ constexpr double pooley_wxx(int i) {
+    return i == 0 ? 0.0 : (i < 3 ? 1.0 / 3.0 : (i < 5 ? -1.0 / 6.0 : -1.0 / 24.0));
+}
+__host__ __device__ constexpr double pooley_wyy(int i) {
+    return i == 0 ? 0.0 : (i < 3 ? -1.0 / 6.0 : (i < 5 ? 1.0 / 3.0 : -1.0 / 24.0));
+}
+__host__ __device__ constexpr double pooley_wxy(int i) {
+    return i < 5 ? 0.0 : (i < 7 ? 0.25 : -0.25);
+}
+
+// ---------------------------------------------------------------------------
+// Per-system parameters, resident in the workspace
+// ---------------------------------------------------------------------------
+struct SysDev {
+    int32_t nx, ny, nz;
+    int32_t small;          // 1 if some side is too short for the single-branch wrap
+    int64_t n_sites;
+    int64_t site_offset;    // first site of this system in the concatenated site arrays
+    int64_t pop_offset;     // first population element: pop_offset + i * n_sites + site
+    double rho_c, a, b, kappa, kT;
+    double inv_rho_c;
+    double nu;              // kinematic viscosity of the Holdych term (tau[4])
+    double lam[LB_MAX_Q_DEV];
+    double g_diag[LB_MAX_Q_DEV];   // 1 - gamma_a^2
+    double g_pair;                 // 1 - gamma_P gamma_R
+    uint32_t seed_lo, seed_hi;
+    uint32_t system_id;
+    int32_t pad;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi_a = __umulhi(0xD2511F53u, ctr.x);
+        const uint32_t lo_a = 0xD2511F53u * ctr.x;
+        const uint32_t hi_b = __umulhi(0xCD9E8D57u, ctr.z);
+        const uint32_t lo_b = 0xCD9E8D57u * ctr.z;
+        ctr = make_uint4(hi_b ^ ctr.y ^ k0, lo_b, hi_a ^ ctr.w ^ k1, lo_a);
+    }
+    return ctr;
+}
+
+// Counter layout: (site, step low word, step high word, system_id << 8 | draw).
+__device__ __forceinline__ uint4 site_draw(const SysDev& s, uint32_t site, int64_t step, uint32_t draw) {
+    const uint4 ctr = make_uint4(site, uint32_t(uint64_t(step) & 0xffffffffu), uint32_t(uint64_t(step) >> 32),
+                                 (s.system_id << 8) | draw);
+    return philox4x32_10(ctr, s.seed_lo, s.seed_hi);
+}
+
+// Uniform in (0,1): (x + 1/2) 2^-32, then Box-Muller (R = sqrt(-2 ln U_a),
+// angle 2 pi U_b).  Float and double versions.
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0, double& n1) {
+    const double ua = (double(wa) + 0.5) * 2.3283064365386962890625e-10;
+    const double ub = (double(wb) + 0.5) * 2.3283064365386962890625e-10;
+    const double r = sqrt(-2.0 * log(ua));
+    double s, c;
+    sincospi(2.0 * ub, &s, &c);
+    n0 = r * c;
+    n1 = r * s;
+}
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
+    const float ua = (float(wa) + 0.5f) * 2.3283064365386963e-10f;
+    const float ub = (float(wb) + 0.5f) * 2.3283064365386963e-10f;
+    const float r = sqrtf(-2.0f * logf(ua));
+    float s, c;
+    sincospif(2.0f * ub, &s, &c);
+    n0 = r * c;
+    n1 = r * s;
+}
+
+// Periodic wrap of a coordinate that is at most one period outside [0, n).
+__device__ __forceinline__ int wrap1(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+// Any coordinate.
+__device__ __forceinline__ int wrapm(int x, int n) {
+    int r = x % n;
+    return r < 0 ? r + n : r;
+}
+
+// Device status bits (OR-ed by kernels, mapped to lb_status on the host).
+enum : int { ST_RHO = 1, ST_NOISE = 2, ST_NONFINITE = 4 };
+
+}  // namespace lbf

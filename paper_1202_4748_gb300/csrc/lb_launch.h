@@ -1,0 +1,95 @@
+// Internal host-side interface between the C ABI (api.cu) and the kernel
+// translation units.  Plain structs and pointers only.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lb_device.cuh"
+
+namespace lbf {
+
+constexpr int AUX_THREADS = 256;        // threads of the auxiliary (non-step) kernels
+constexpr int SITES_PER_THREAD = 4;     // sites per thread in a site-pass item
+
+struct StepLaunch {
+    const SysDev* sys;
+    const int4* tiles;
+    int n_tiles;
+    const void* fin;
+    void* fout;
+    const int64_t* step_ptr;
+    int k;
+    int* status;
+    int tile_id;            // index into the lattice's tile-shape table
+};
+
+// Tile shapes compiled for each lattice (x, y, z); index = tile_id.
+int tile_shapes_d2q9(int (*out)[3], int max);
+int tile_shapes_d3q19(int (*out)[3], int max);
+
+cudaError_t launch_step_d2q9(int coupling, int fp32, const StepLaunch& a, cudaStream_t st);
+cudaError_t launch_step_d3q19(int coupling, int fp32, const StepLaunch& a, cudaStream_t st);
+
+cudaError_t launch_init_feq_d2q9(int coupling, int fp32, const SysDev* sys, const int4* items, int n_items,
+                                 const double* d, const double* dbar, void* fbuf, cudaStream_t st);
+cudaError_t launch_init_feq_d3q19(int coupling, int fp32, const SysDev* sys, const int4* items, int n_items,
+                                  const double* d, const double* dbar, void* fbuf, cudaStream_t st);
+cudaError_t launch_gather_d2q9(int fp32, const SysDev* sys, int s, int i, int64_t n, const void* fbuf, double* out,
+                               cudaStream_t st);
+cudaError_t launch_gather_d3q19(int fp32, const SysDev* sys, int s, int i, int64_t n, const void* fbuf, double* out,
+                                cudaStream_t st);
+cudaError_t launch_scatter_d2q9(int fp32, const SysDev* sys, int s, int i, int64_t n, const double* in, void* fbuf,
+                                cudaStream_t st);
+cudaError_t launch_scatter_d3q19(int fp32, const SysDev* sys, int s, int i, int64_t n, const double* in, void* fbuf,
+                                 cudaStream_t st);
+cudaError_t launch_obs_site_d2q9(int fp32, const SysDev* sys, const int4* items, int n_items, const void* fbuf,
+                                 double* d, double* partial, cudaStream_t st);
+cudaError_t launch_obs_site_d3q19(int fp32, const SysDev* sys, const int4* items, int n_items, const void* fbuf,
+                                  double* d, double* partial, cudaStream_t st);
+
+// ---- lattice-independent (obs.cu) ----------------------------------------
+struct SysSpan {            // items [first, first + count) of one system
+    int first, count;
+};
+
+// One block level of one system, as the observable kernels see it.
+struct LevelDev {
+    int32_t sys;
+    int32_t bx, by, bz;     // block dims
+    int32_t gx, gy, gz;     // blocks per axis
+    int32_t child;          // index of the next finer pyramid level (-1 at the bottom)
+    int64_t nblocks;
+    int64_t off;            // offset of this level's block sums in the S/E arrays (-1: unit level)
+    int32_t rec_first;      // records of this level in the partial-record array
+    int32_t rec_count;
+};
+
+struct ObsItem {            // a range of blocks of one level
+    int32_t level;          // index into the LevelDev array
+    int32_t unit_level;     // bottom items also feed the separate single-site level (-1: none)
+    int64_t b0, b1;
+    int32_t rec, rec2;      // partial records written (rec2 for the unit level)
+};
+
+cudaError_t launch_init_noise(const SysDev* sys, const int4* items, int n_items, double amp, double* d,
+                              double* partial, cudaStream_t st);
+cudaError_t launch_reduce_sys(const SysSpan* spans, int n_sys, const double* partial, int K, double* out,
+                              cudaStream_t st);
+cudaError_t launch_obs_globals(const SysDev* sys, int n_sys, const double* red4, double* dbar, double* glob,
+                               int set_mass0, int count_sample, cudaStream_t st);
+cudaError_t launch_set_dbar(const SysDev* sys, int n_sys, double* dbar, cudaStream_t st);
+cudaError_t launch_pyr_bottom(const SysDev* sys, const LevelDev* lv, const ObsItem* items, int n_items,
+                              const double* d, const double* dbar, double* S, double* E, double* rec,
+                              cudaStream_t st);
+cudaError_t launch_pyr_up(const SysDev* sys, const LevelDev* lv, const ObsItem* items, int n_items, int dims3,
+                          double* S, double* E, double* rec, cudaStream_t st);
+cudaError_t launch_obs_accum(const LevelDev* lv, int n_levels_total, const double* rec, double* acc,
+                             int* status, cudaStream_t st);
+cudaError_t launch_advance(int64_t* step, int64_t n, cudaStream_t st);
+
+constexpr int OBS_THREADS = 256;
+constexpr int BLOCKS_PER_THREAD = 4;
+constexpr int REC = 6;      // per record: sum m, m^2, |m|, m^4, e, e^2
+
+}  // namespace lbf

@@ -1,0 +1,125 @@
+"""The C ABI: library loads, exports every declared entry point, validates arguments.
+
+Runs without a GPU: nothing here reaches a CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lbfluct.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    import paper_1202_4748_gb300 as lb
+    lib = ctypes.CDLL(lb.LIB_PATH)
+    names = _declared()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(lb.EXPORTED) == names
+
+
+def test_status_strings_and_version():
+    import paper_1202_4748_gb300 as lb
+    assert lb.lb_status_string(0) == b"ok"
+    for code in range(-9, 0):
+        assert lb.lb_status_string(code) != b"unknown status"
+    assert b"sm_103a" in lb.lb_version()
+
+
+def _one(**kw):
+    s = synth.system("D2Q9", n=16)
+    s.update(kw)
+    return s
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=0), dict(nz=2), dict(kT=-1.0), dict(rho_c=0.0), dict(kappa=-1e-3),
+    dict(tau=[1.0] * 3 + [0.5] + [1.0] * 5), dict(system_id=1 << 24), dict(lattice="D3Q19", coupling="modeq"),
+    dict(a=float("nan")),
+])
+def test_invalid_descriptors_rejected(bad):
+    import paper_1202_4748_gb300 as lb
+    s = _one(**bad)
+    if s["lattice"] == "D3Q19":
+        s["tau"] = [1.0] * 19
+    with pytest.raises(lb.LBError) as e:
+        lb.workspace_bytes([s])
+    assert e.value.status == lb.LB_ERR_ARG
+
+
+def test_mixed_lattices_and_bad_options_rejected():
+    import paper_1202_4748_gb300 as lb
+    a = _one()
+    b = synth.system("D3Q19", n=8)
+    with pytest.raises(lb.LBError):
+        lb.workspace_bytes([a, b])
+    with pytest.raises(lb.LBError):
+        lb.workspace_bytes([a], graph_chunk=3)
+    with pytest.raises(lb.LBError):
+        lb.workspace_bytes([a], precision=7)
+    with pytest.raises(lb.LBError) as e:
+        lb.workspace_bytes([a], tile=(7, 7, 1))
+    assert e.value.status == lb.LB_ERR_UNSUPPORTED
+
+
+def test_workspace_grows_with_sites_and_precision():
+    import paper_1202_4748_gb300 as lb
+    e = synth.ensemble("fss_160", "D3Q19")
+    b32 = lb.workspace_bytes(e, precision="fp32", obs_every=100)
+    b64 = lb.workspace_bytes(e, precision="fp64", obs_every=100)
+    pops32 = 2 * 19 * 4 * synth.sites(e)
+    assert pops32 < b32 < pops32 * 1.6
+    assert b64 == b32 + pops32      # same bookkeeping, twice the population bytes
+
+
+def test_create_rejects_bad_workspace_without_touching_the_device():
+    import paper_1202_4748_gb300 as lb
+    desc = lb.make_desc([_one()])
+    o = lb.make_opts()
+    ctx = ctypes.c_void_p()
+    st = lb.lb_create(desc, 1, ctypes.byref(o), None, 1 << 20, None, ctypes.byref(ctx))
+    assert st == lb.LB_ERR_WORKSPACE and not ctx.value
+    st = lb.lb_create(desc, 1, ctypes.byref(o), ctypes.c_void_p(4096 + 8), 1 << 40, None, ctypes.byref(ctx))
+    assert st == lb.LB_ERR_WORKSPACE
+
+
+def test_null_context_calls_fail_cleanly():
+    import paper_1202_4748_gb300 as lb
+    assert lb.lb_step(None, 1) == lb.LB_ERR_ARG
+    assert lb.lb_sync(None) == lb.LB_ERR_ARG
+    assert lb.lb_init(None, 0, 0.01, None) == lb.LB_ERR_ARG
+    lb.lb_destroy(None)
+
+
+def test_derive_matches_oracle_formulas():
+    """lb_derive (host arithmetic in the library) against the oracle's Eqs. 47-50."""
+    import paper_1202_4748_gb300 as lb
+    from oracle import observables as ob
+    rng = np.random.default_rng(3)
+    acc = np.abs(rng.standard_normal((1, 7)))
+    acc[0, 0] = 1234.0
+    kT = 2e-4
+    want = ob.derived(acc, [(4, 2, 1)], kT)[0]
+    L = lb.lb_obs_level()
+    L.bx, L.by, L.bz = 4, 2, 1
+    L.n, L.sum_m, L.sum_m2, L.sum_abs_m, L.sum_m4, L.sum_e, L.sum_e2 = acc[0]
+    out = (ctypes.c_double * 6)()
+    assert lb.lb_derive(ctypes.byref(L), kT, out) == 0
+    assert np.isclose(out[0], want["M_L"], rtol=1e-15)
+    assert np.isclose(out[1], want["chi_L"], rtol=1e-13)
+    assert np.isclose(out[2], want["chi_L_lowT"], rtol=1e-13)
+    assert np.isclose(out[3], want["c_HL"], rtol=1e-13)
+    assert np.isclose(out[4], want["U_L"], rtol=1e-13)
+    L.n = 0
+    assert lb.lb_derive(ctypes.byref(L), kT, out) == lb.LB_ERR_ARG

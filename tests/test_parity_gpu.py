@@ -1,0 +1,281 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Bars (from the method's stated tolerances):
+  FP64 path: max |f_gpu - f_oracle| / max |f_oracle| <= 1e-12 at every compared
+             step; observables to 1e-10 relative.
+  FP32-deviation path: one step from an identical state, max |df| / max |f| <= 1e-5.
+Inputs are seeded and synthetic (see ``synth``); every expected value comes
+from the oracle.
+"""
+import dataclasses
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import lbm, observables as ob
+from tests.helpers import oracle_state, params_of, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("GPU tests need CUDA; the library has no CPU fallback")
+    import paper_1202_4748_gb300 as m
+    return m
+
+
+def _sys(lattice, coupling, nx, ny, nz=1, **kw):
+    s = synth.system(lattice, coupling, n=nx, **{k: v for k, v in kw.items() if k in
+                                                 ("a", "b", "kappa", "kT", "tau", "seed", "system_id", "rho_c")})
+    s.update(nx=nx, ny=ny, nz=nz)
+    return s
+
+
+MIXED_TAU_9 = [1, 1, 1, 0.8, 0.9, 1.3, 0.7, 1.6, 1.1]
+MIXED_TAU_19 = [1, 1, 1, 1] + list(np.linspace(0.7, 1.5, 15))
+
+CASES = [
+    ("D2Q9", "modeq", (70, 37, 1), MIXED_TAU_9),
+    ("D2Q9", "guo", (45, 29, 1), MIXED_TAU_9),
+    ("D3Q19", "guo", (20, 13, 11), MIXED_TAU_19),
+]
+
+
+def _run_gpu(lb, systems, f0s, nsteps, precision="fp64", **opts):
+    ens = lb.Ensemble(systems, precision=precision, **opts)
+    for k, f in enumerate(f0s):
+        ens.write_fields(k, f)
+    ens.step(nsteps)
+    ens.sync()
+    out = [ens.read_fields(k) for k in range(len(systems))]
+    ens.close()
+    return out
+
+
+@pytest.mark.parametrize("lattice,coupling,shape,tau", CASES)
+def test_fp64_multistep_parity(lb, lattice, coupling, shape, tau):
+    s = _sys(lattice, coupling, *shape, a=0.01, b=0.1, kappa=0.01, kT=1e-4, tau=tau, seed=7, system_id=3)
+    p = params_of(s)
+    f0 = oracle_state(p)
+    ens = lb.Ensemble([s], precision="fp64")
+    ens.write_fields(0, f0)
+    assert rel_err(ens.read_fields(0), f0) == 0.0          # write/read round trip is exact
+    f = f0
+    t = 0
+    for chunk in (1, 4, 15):
+        ens.step(chunk)
+        ens.sync()
+        f = lbm.run(f, t, chunk, p)
+        t += chunk
+        assert rel_err(ens.read_fields(0), f) < TOL64, (t, rel_err(ens.read_fields(0), f))
+    ens.close()
+
+
+@pytest.mark.parametrize("lattice,coupling,shape,tau", CASES)
+def test_fp32_one_step_parity(lb, lattice, coupling, shape, tau):
+    s = _sys(lattice, coupling, *shape, a=-0.002, b=0.1, kappa=0.01, kT=1e-4, tau=tau, seed=11)
+    p = params_of(s)
+    f0 = oracle_state(p, steps=5)
+    ens = lb.Ensemble([s], precision="fp32")
+    ens.write_fields(0, f0)
+    f0r = ens.read_fields(0)            # the FP32-rounded state, as the GPU holds it
+    assert rel_err(f0r, f0) < 1e-7
+    for t in range(3):
+        ens.step(1)
+        ens.sync()
+        got = ens.read_fields(0)
+        want = lbm.step(f0r, t, p)
+        assert rel_err(got, want) < TOL32, (t, rel_err(got, want))
+        # the next step starts again from the GPU's own state
+        ens.write_fields(0, got)
+        f0r = ens.read_fields(0)
+    ens.close()
+
+
+def test_batched_systems_of_different_sizes(lb):
+    """Tiles of several systems share one launch; each system matches the oracle alone."""
+    systems = [_sys("D3Q19", "guo", 9, 8, 7, a=0.0, kT=1e-4, seed=1, system_id=0, tau=[1.0] * 19),
+               _sys("D3Q19", "guo", 17, 5, 9, a=-0.003, kT=2e-4, seed=2, system_id=1, tau=MIXED_TAU_19),
+               _sys("D3Q19", "guo", 4, 4, 4, a=0.003, kT=0.0, seed=3, system_id=2, tau=[1.0] * 19)]
+    ps = [params_of(s) for s in systems]
+    f0s = [oracle_state(p) for p in ps]
+    got = _run_gpu(lb, systems, f0s, 6)
+    for g, p, f in zip(got, ps, f0s):
+        assert rel_err(g, lbm.run(f, 0, 6, p)) < TOL64
+
+
+@pytest.mark.parametrize("lattice,coupling,shape", [
+    ("D2Q9", "modeq", (1, 1, 1)), ("D2Q9", "modeq", (2, 3, 1)), ("D2Q9", "modeq", (5, 1, 1)),
+    ("D2Q9", "guo", (3, 2, 1)), ("D3Q19", "guo", (2, 2, 2)), ("D3Q19", "guo", (1, 3, 2)),
+    ("D3Q19", "guo", (3, 3, 3)),
+])
+def test_degenerate_tiny_lattices(lb, lattice, coupling, shape):
+    """Sides shorter than the stencil: sites are their own periodic neighbours."""
+    q = 9 if lattice == "D2Q9" else 19
+    s = _sys(lattice, coupling, *shape, a=0.02, kT=1e-4, tau=[1.0] * q, seed=5)
+    p = params_of(s)
+    rng = np.random.default_rng(0)
+    rho = 1 + 0.01 * rng.standard_normal(p.shape)
+    f0 = lbm.equilibrium_at_rest(rho, p) + 1e-4 * rng.standard_normal((q,) + p.shape)
+    got = _run_gpu(lb, [s], [f0], 5)[0]
+    assert rel_err(got, lbm.run(f0, 0, 5, p)) < TOL64
+
+
+@pytest.mark.parametrize("lattice,coupling", [("D2Q9", "modeq"), ("D2Q9", "guo"), ("D3Q19", "guo")])
+def test_init_matches_oracle(lb, lattice, coupling):
+    s = synth.system(lattice, coupling, n=24 if lattice == "D2Q9" else 10, seed=9, system_id=5)
+    s["ny"] = s["nx"] - 3 if lattice == "D2Q9" else s["ny"]
+    p = params_of(s)
+    for prec, tol in (("fp64", 1e-14), ("fp32", 1e-7)):
+        ens = lb.Ensemble([s], precision=prec)
+        ens.init(amplitude=0.01)
+        got = ens.read_fields(0)
+        want = lbm.initial_state(p, amplitude=0.01)
+        assert rel_err(got, want) < tol
+        _, glob = ens.observables(0)
+        assert abs(glob["mass0"] / p.n_sites - p.rho_c) < 1e-14
+        ens.close()
+    rho = synth.random_density(p.shape, seed=4)
+    ens = lb.Ensemble([s], precision="fp64")
+    ens.init(rho=rho)
+    assert rel_err(ens.read_fields(0), lbm.equilibrium_at_rest(rho, p)) < 1e-14
+    ens.close()
+
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_single_16_thousand_step_trajectory(lb, lattice):
+    """The 16^3 / 64^2 FP64 workload (a = 0, b = 0.1, kappa = 0.01, tau = 1, kT = 1e-4,
+    seed 1): trajectory parity at 1e-12 over 1000 steps, and observables every 10."""
+    s = synth.ensemble("single_16", lattice)[0]
+    p = params_of(s)
+    ens = lb.Ensemble([s], precision="fp64", obs_every=10)
+    ens.init(amplitude=0.01)
+    rec = ob.Recorder(p, every=10)
+    f = lbm.initial_state(p)
+    t = 0
+    for chunk in (10, 90, 400, 500):
+        ens.step(chunk)
+        f = lbm.run(f, t, chunk, p, callback=rec)
+        t += chunk
+        assert rel_err(ens.read_fields(0), f) < TOL64, (t, rel_err(ens.read_fields(0), f))
+    levels, glob = ens.observables(0)
+    assert glob["n_samples"] == 100 and glob["step"] == 1000
+    assert len(levels) == len(rec.lv)
+    for L, blk, row in zip(levels, rec.lv, rec.acc):
+        assert L["block"] == blk
+        got = np.array([L["n"], L["sum_m"], L["sum_m2"], L["sum_abs_m"], L["sum_m4"], L["sum_e"], L["sum_e2"]])
+        scale = np.maximum(np.abs(row), 1e-300)
+        if blk == (p.nx, p.ny, p.nz if lattice == "D3Q19" else 1):
+            # whole-system level: m = 0 up to rounding (mass conservation)
+            assert abs(got[1]) < 1e-12 * got[0] and got[0] == row[0]
+            continue
+        assert np.all(np.abs(got - row) <= 1e-10 * scale), (blk, got, row)
+    assert abs(glob["mass"] - rec.mass[-1]) < 1e-12 * rec.mass[-1]
+    assert np.allclose(glob["momentum"], rec.mom[-1], atol=1e-12)
+    ens.close()
+
+
+def test_fss_160_full_size_sampled_parity(lb):
+    """The 160-system D3Q19 FP32 ensemble in the launch configuration the benchmark
+    times: after one step, three systems (smallest, a middle one, largest) are
+    compared with the oracle stepping each from the same state."""
+    systems = synth.ensemble("fss_160", "D3Q19")
+    ens = lb.Ensemble(systems, precision="fp32", obs_every=100)
+    ens.init(amplitude=0.01)
+    picks = [0, 77, len(systems) - 1]
+    before = {k: ens.read_fields(k) for k in picks}
+    ens.step(1)
+    ens.sync()
+    for k in picks:
+        p = params_of(systems[k])
+        want = lbm.step(before[k], 0, p)
+        assert rel_err(ens.read_fields(k), want) < TOL32, k
+    ens.close()
+
+
+def test_errors_are_reported_and_sticky(lb):
+    s = _sys("D2Q9", "modeq", 16, 16, kT=1e-4, tau=[1.0] * 9)
+    p = params_of(s)
+    f = lbm.equilibrium_at_rest(np.ones(p.shape), p)
+    f[0, 0, 3, 3] = -5.0
+    ens = lb.Ensemble([s], precision="fp64")
+    ens.write_fields(0, f)
+    ens.step(1)
+    with pytest.raises(lb.LBError) as e:
+        ens.sync()
+    assert e.value.status == lb.LB_ERR_NONPOSITIVE_DENSITY
+    with pytest.raises(lb.LBError) as e:
+        ens.step(1)
+    assert e.value.status == lb.LB_ERR_STATE
+    ens.write_fields(0, lbm.equilibrium_at_rest(np.ones(p.shape), p))     # restores a state
+    ens.step(2)
+    ens.sync()
+    ens.close()
+    # c_s^2 = rho a >= 0.6 makes the covariance of Eq. 68 indefinite
+    s2 = _sys("D2Q9", "modeq", 8, 8, a=0.7, b=0.0, kT=1e-4, tau=[1.0] * 9)
+    ens = lb.Ensemble([s2], precision="fp64")
+    ens.init(amplitude=0.0)
+    ens.step(1)
+    with pytest.raises(lb.LBError) as e:
+        ens.sync()
+    assert e.value.status == lb.LB_ERR_NOISE_NOT_PD
+    ens.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_resume_is_bit_identical(lb, tmp_path, precision):
+    systems = synth.ensemble("single_16", "D3Q19") + [synth.system("D3Q19", n=8, system_id=1, seed=3)]
+    a = lb.Ensemble(systems, precision=precision, obs_every=5)
+    a.init()
+    a.step(12)
+    path = os.path.join(tmp_path, "ck.bin")
+    a.save(path)
+    a.step(13)
+    ref = [a.read_fields(k) for k in range(2)]
+    ref_obs = a.observables(0)
+    b = lb.Ensemble(systems, precision=precision, obs_every=5)
+    b.load(path)
+    assert b.get_step() == 12
+    b.step(13)
+    for k in range(2):
+        assert np.array_equal(b.read_fields(k), ref[k])
+    assert b.observables(0) == ref_obs
+    a.close()
+    b.close()
+
+
+def test_graph_replay_equals_plain_launches_and_is_deterministic(lb):
+    systems = synth.ensemble("fss_160", "D2Q9")[:6]
+    runs = []
+    for chunk in (0, 10, 10):
+        e = lb.Ensemble(systems, precision="fp32", obs_every=5, graph_chunk=chunk)
+        e.init()
+        e.step(3)        # unaligned start: plain launches to the chunk boundary
+        e.step(37)
+        runs.append(([e.read_fields(k) for k in range(len(systems))], e.observables(2)))
+        e.close()
+    for r in runs[1:]:
+        assert all(np.array_equal(a, b) for a, b in zip(runs[0][0], r[0]))
+        assert r[1] == runs[0][1]
+
+
+def test_a_system_evolves_the_same_alone_or_in_a_batch(lb):
+    systems = synth.ensemble("fss_160", "D3Q19")[:5]
+    e = lb.Ensemble(systems, precision="fp32")
+    e.init()
+    e.step(4)
+    batch = e.read_fields(3)
+    e.close()
+    e = lb.Ensemble([systems[3]], precision="fp32")
+    e.init()
+    e.step(4)
+    assert np.array_equal(e.read_fields(0), batch)
+    e.close()
