@@ -16,3 +16,9 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return os.path.join(ROOT, "tests", "golden")
+
+
+def pytest_sessionstart(session):
+    """Bring liblbfluct.so up to date (incremental nvcc build) before any test imports it."""
+    from paper_1202_4748_gb300 import _build
+    _build.build()
