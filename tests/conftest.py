@@ -20,5 +20,9 @@ def golden_dir():
 
 def pytest_sessionstart(session):
     """Bring liblbfluct.so up to date (incremental nvcc build) before any test imports it."""
-    from paper_1202_4748_gb300 import _build
-    _build.build()
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "lbfluct_build", os.path.join(ROOT, "paper_1202_4748_gb300", "_build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()
