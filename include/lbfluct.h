@@ -177,8 +177,9 @@ lb_status lb_derive(const lb_obs_level* level, double kT, double out[6]);
 /* Structure factor of Eq. 80 accumulated over the sk_every schedule, binned in
  * shells j = 1..nbins (k = 2 pi n / S, shell j holds j(j-1) < |n|^2 <= j(j+1)):
  * h_sum[j-1] = sum over samples and shell points of C(k), h_count[j-1] = number
- * of k points in the shell, *n_samples = snapshots.  Requires equal sides.
- * Synchronises.  Errors: LB_ERR_ARG, LB_ERR_UNSUPPORTED (sk disabled / sides). */
+ * of k points in the shell, *n_samples = snapshots.  Requires equal sides
+ * (checked at lb_create) and nbins <= ceil(sqrt(3) S / 2) + 2.  Synchronises.
+ * Errors: LB_ERR_ARG, LB_ERR_UNSUPPORTED (sk_every == 0). */
 lb_status lb_structure_factor(lb_ctx* ctx, int sys, double* h_sum, int64_t* h_count, int nbins,
                               int64_t* n_samples);
 

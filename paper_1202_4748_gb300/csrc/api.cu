@@ -39,7 +39,7 @@ struct SysHost {
 // Byte offsets of every region inside the workspace.
 struct Plan {
     size_t sys, tiles, pop0, pop1, step, status, d, dbar, site_items, site_partial, spans, red4, glob, levels,
-        S, E, bottom_items, up_items, rec, acc, field_tmp, total;
+        S, E, bottom_items, up_items, rec, acc, field_tmp, sk_sys, sk_tw, sk_acc, sk_b0, sk_b1, sk_bins, total;
     int n_tiles = 0, n_site_items = 0, n_levels = 0, n_bottom = 0, n_up = 0, n_rec = 0, max_depth = 0;
     int64_t n_sites = 0, n_blocks_pyr = 0, max_sites = 0;
     std::vector<int4> tiles_h, site_items_h;
@@ -47,6 +47,11 @@ struct Plan {
     std::vector<LevelDev> levels_h;
     std::vector<ObsItem> bottom_h, up_h;
     std::vector<int> up_first;   // up items of depth u: [up_first[u-1], up_first[u])
+    // structure factor
+    bool sk = false;
+    std::vector<SkSys> sk_h;
+    std::vector<int> tw_sides, tw_offs;
+    int tw_total = 0, tw_max = 0, sk_max_bins = 0;
 };
 
 int q_of(int lattice) { return lattice == LB_D2Q9 ? 9 : 19; }
@@ -68,6 +73,7 @@ lb_status validate(const lb_system_desc* s, int n, const lb_run_opts* o) {
             !std::isfinite(d.kT) || !std::isfinite(d.kappa))
             return LB_ERR_ARG;
         if (d.system_id >= (1u << 24)) return LB_ERR_ARG;
+        if (o->sk_every > 0 && (d.nx != d.ny || (d.lattice == LB_D3Q19 && d.nz != d.nx))) return LB_ERR_UNSUPPORTED;
         const int q = q_of(d.lattice), nc = d.lattice == LB_D2Q9 ? 3 : 4;
         for (int a = nc; a < q; ++a)
             if (!(d.tau[a] > 0.5) || !std::isfinite(d.tau[a])) return LB_ERR_ARG;
@@ -259,6 +265,34 @@ lb_status make_plan(const lb_system_desc* s, int n, const lb_run_opts* o, std::v
     P.n_up = int(P.up_h.size());
     P.n_rec = rec;
 
+    // structure factor tables
+    P.sk = o->sk_every > 0;
+    if (P.sk) {
+        auto table_of = [&](int n) {
+            for (size_t t = 0; t < P.tw_sides.size(); ++t)
+                if (P.tw_sides[t] == n) return P.tw_offs[t];
+            P.tw_sides.push_back(n);
+            P.tw_offs.push_back(P.tw_total);
+            P.tw_total += n;
+            P.tw_max = std::max(P.tw_max, n);
+            return P.tw_offs.back();
+        };
+        for (auto& h : sys) {
+            SkSys k;
+            k.nx = h.d.nx;
+            k.ny = h.d.ny;
+            k.nz = h.d.nz;
+            k.tw_x = table_of(h.d.nx);
+            k.tw_y = table_of(h.d.ny);
+            k.tw_z = table_of(h.d.nz);
+            k.site_offset = h.site_off;
+            k.inv_n = 1.0 / double(h.n);
+            P.sk_h.push_back(k);
+            const int side = h.d.nx;
+            P.sk_max_bins = std::max(P.sk_max_bins, int(std::ceil(std::sqrt(3.0) * side / 2.0)) + 2);
+        }
+    }
+
     // byte layout
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -287,6 +321,13 @@ lb_status make_plan(const lb_system_desc* s, int n, const lb_run_opts* o, std::v
     P.rec = take(sizeof(double) * REC * P.n_rec);
     P.acc = take(sizeof(double) * 7 * P.n_levels);
     P.field_tmp = take(sizeof(double) * P.max_sites);
+    const int64_t skn = P.sk ? P.n_sites : 0;
+    P.sk_sys = take(sizeof(SkSys) * (P.sk ? n : 0));
+    P.sk_tw = take(sizeof(double) * 2 * P.tw_total);
+    P.sk_acc = take(sizeof(double) * skn);
+    P.sk_b0 = take(sizeof(double) * 2 * skn);
+    P.sk_b1 = take(sizeof(double) * 2 * skn);
+    P.sk_bins = take(sizeof(double) * 2 * P.sk_max_bins);
     P.total = off;
     return LB_OK;
 }
@@ -395,6 +436,37 @@ cudaError_t sample_obs(lb_ctx* c, int buf, bool set_mass0, bool count) {
                             c->at<int>(P.status), c->stream);
 }
 
+// Structure-factor sample of the state in buffer `buf`; `have_d` when the
+// observable pass of the same step has already filled d and dbar.
+cudaError_t sample_sk(lb_ctx* c, int buf, bool have_d) {
+    const Plan& P = c->P;
+    cudaError_t e;
+    if (!have_d) {
+        e = sample_obs(c, buf, false, false);
+        if (e != cudaSuccess) return e;
+    }
+    const SysDev* sys = c->at<SysDev>(P.sys);
+    const SkSys* sk = c->at<SkSys>(P.sk_sys);
+    const int4* items = c->at<int4>(P.site_items);
+    double* b0 = c->at<double>(P.sk_b0);
+    double* b1 = c->at<double>(P.sk_b1);
+    e = launch_sk_x(sys, sk, items, P.n_site_items, c->at<double>(P.d), c->at<double>(P.dbar),
+                    c->at<double>(P.sk_tw), b0, c->stream);
+    if (e != cudaSuccess) return e;
+    e = launch_sk_pass(sk, items, P.n_site_items, 1, c->at<double>(P.sk_tw), b0, b1, c->stream);
+    if (e != cudaSuccess) return e;
+    const double* fin = b1;
+    c->launches += 2;
+    if (c->lattice == LB_D3Q19) {
+        e = launch_sk_pass(sk, items, P.n_site_items, 2, c->at<double>(P.sk_tw), b1, b0, c->stream);
+        if (e != cudaSuccess) return e;
+        fin = b0;
+        c->launches += 1;
+    }
+    c->launches += 1;
+    return launch_sk_accum(sk, items, P.n_site_items, fin, c->at<double>(P.sk_acc), c->stream);
+}
+
 // Launch `n` steps starting at host step c->step (device counter must equal it).
 cudaError_t launch_steps(lb_ctx* c, int64_t n) {
     const Plan& P = c->P;
@@ -414,8 +486,13 @@ cudaError_t launch_steps(lb_ctx* c, int64_t n) {
         if (e != cudaSuccess) return e;
         c->launches += 1;
         const int64_t t1 = t + 1;
-        if (c->opts.obs_every > 0 && t1 % c->opts.obs_every == 0) {
+        const bool obs_due = c->opts.obs_every > 0 && t1 % c->opts.obs_every == 0;
+        if (obs_due) {
             e = sample_obs(c, int(t1 & 1), false, true);
+            if (e != cudaSuccess) return e;
+        }
+        if (c->opts.sk_every > 0 && t1 % c->opts.sk_every == 0) {
+            e = sample_sk(c, int(t1 & 1), obs_due);
             if (e != cudaSuccess) return e;
         }
     }
@@ -453,6 +530,7 @@ lb_status reset_accumulators(lb_ctx* c) {
     LB_CHECK(cudaMemsetAsync(c->ws + P.acc, 0, sizeof(double) * 7 * P.n_levels, c->stream));
     LB_CHECK(cudaMemsetAsync(c->ws + P.glob, 0, sizeof(double) * 8 * c->n_sys, c->stream));
     LB_CHECK(cudaMemsetAsync(c->ws + P.status, 0, sizeof(int), c->stream));
+    if (P.sk) LB_CHECK(cudaMemsetAsync(c->ws + P.sk_acc, 0, sizeof(double) * P.n_sites, c->stream));
     return LB_OK;
 }
 
@@ -499,10 +577,6 @@ lb_status lb_create(const lb_system_desc* systems, int n_systems, const lb_run_o
         delete c;
         return st;
     }
-    if (opts->sk_every > 0) {
-        delete c;
-        return LB_ERR_UNSUPPORTED;
-    }
     if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) || bytes < c->P.total) {
         delete c;
         return LB_ERR_WORKSPACE;
@@ -535,6 +609,18 @@ lb_status lb_create(const lb_system_desc* systems, int n_systems, const lb_run_o
     if (P.n_up)
         ok = ok && cudaMemcpyAsync(c->ws + P.up_items, P.up_h.data(), sizeof(ObsItem) * P.n_up,
                                    cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+    if (P.sk) {
+        ok = ok && cudaMemcpyAsync(c->ws + P.sk_sys, P.sk_h.data(), sizeof(SkSys) * P.sk_h.size(),
+                                   cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+        // twiddle tables: sides and offsets staged through the bin scratch (ints fit in it)
+        std::vector<int> meta(P.tw_sides);
+        meta.insert(meta.end(), P.tw_offs.begin(), P.tw_offs.end());
+        int* dmeta = reinterpret_cast<int*>(c->ws + P.field_tmp);
+        ok = ok && cudaMemcpyAsync(dmeta, meta.data(), sizeof(int) * meta.size(), cudaMemcpyHostToDevice,
+                                   c->stream) == cudaSuccess;
+        ok = ok && launch_sk_twiddles(c->at<double>(P.sk_tw), dmeta, dmeta + P.tw_sides.size(),
+                                      int(P.tw_sides.size()), P.tw_max, c->stream) == cudaSuccess;
+    }
     ok = ok && cudaMemsetAsync(c->ws + P.step, 0, sizeof(int64_t), c->stream) == cudaSuccess;
     ok = ok && reset_accumulators(c) == LB_OK;
     ok = ok && cudaStreamSynchronize(c->stream) == cudaSuccess;
@@ -591,7 +677,8 @@ lb_status lb_step(lb_ctx* c, int64_t nsteps) {
     int64_t left = nsteps;
     while (left > 0) {
         const bool aligned = C > 0 && c->step % C == 0 && left >= C &&
-                             (c->opts.obs_every == 0 || C % c->opts.obs_every == 0);
+                             (c->opts.obs_every == 0 || C % c->opts.obs_every == 0) &&
+                             (c->opts.sk_every == 0 || C % c->opts.sk_every == 0);
         if (!aligned) {
             // plain launches up to the next chunk boundary (or all remaining)
             int64_t n = left;
@@ -697,12 +784,24 @@ lb_status lb_derive(const lb_obs_level* L, double kT, double out[6]) {
 }
 
 lb_status lb_structure_factor(lb_ctx* c, int sys, double* h_sum, int64_t* h_count, int nbins, int64_t* n_samples) {
-    (void)h_sum;
-    (void)h_count;
-    (void)nbins;
-    (void)n_samples;
-    if (!c || sys < 0 || sys >= c->n_sys) return LB_ERR_ARG;
-    return LB_ERR_UNSUPPORTED;
+    if (!c || sys < 0 || sys >= c->n_sys || nbins < 0 || (nbins > 0 && (!h_sum || !h_count))) return LB_ERR_ARG;
+    const Plan& P = c->P;
+    if (!P.sk) return LB_ERR_UNSUPPORTED;
+    if (nbins > P.sk_max_bins) return LB_ERR_ARG;
+    double* bins = c->at<double>(P.sk_bins);
+    LB_CHECK(launch_sk_bin(c->at<SkSys>(P.sk_sys), sys, c->at<double>(P.sk_acc), nbins, bins, bins + P.sk_max_bins,
+                           c->stream));
+    std::vector<double> hb(2 * size_t(P.sk_max_bins));
+    if (nbins > 0)
+        LB_CHECK(cudaMemcpyAsync(hb.data(), bins, sizeof(double) * 2 * P.sk_max_bins, cudaMemcpyDeviceToHost,
+                                 c->stream));
+    lb_status s = sync_and_check(c);
+    for (int j = 0; j < nbins; ++j) {
+        h_sum[j] = hb[j];
+        h_count[j] = int64_t(hb[P.sk_max_bins + j]);
+    }
+    if (n_samples) *n_samples = c->step / c->opts.sk_every;
+    return s;
 }
 
 lb_status lb_read_fields(lb_ctx* c, int sys, double* h_f) {

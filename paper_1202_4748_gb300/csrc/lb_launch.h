@@ -93,3 +93,28 @@ constexpr int BLOCKS_PER_THREAD = 4;
 constexpr int REC = 6;      // per record: sum m, m^2, |m|, m^4, e, e^2
 
 }  // namespace lbf
+
+namespace lbf {
+
+// ---- structure factor (Eq. 80) -------------------------------------------------
+struct SkSys {             // per system: sides, twiddle-table offsets, site offset
+    int32_t nx, ny, nz;
+    int32_t tw_x, tw_y, tw_z;   // offsets of W_n^j = exp(-2 pi i j / n) tables (complex)
+    int64_t site_offset;
+    double inv_n;               // 1 / sites
+};
+
+cudaError_t launch_sk_twiddles(double* tw, const int* sides, const int* offs, int n_tables, int max_n,
+                               cudaStream_t st);
+// x pass (real phi -> complex), then y and z passes (complex -> complex), then accumulate |F|^2 / N.
+cudaError_t launch_sk_x(const SysDev* sys, const SkSys* sk, const int4* items, int n_items, const double* d,
+                        const double* dbar, const double* tw, double* out, cudaStream_t st);
+cudaError_t launch_sk_pass(const SkSys* sk, const int4* items, int n_items, int axis, const double* tw,
+                           const double* in, double* out, cudaStream_t st);
+cudaError_t launch_sk_accum(const SkSys* sk, const int4* items, int n_items, const double* F, double* acc,
+                            cudaStream_t st);
+// per-shell sums of the accumulated C(k) of one system (one CTA per shell)
+cudaError_t launch_sk_bin(const SkSys* sk, int sys, const double* acc, int nbins, double* sums, double* counts,
+                          cudaStream_t st);
+
+}  // namespace lbf

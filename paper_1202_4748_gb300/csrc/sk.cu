@@ -1,0 +1,166 @@
+// Structure factor C(k) = N^-1 |sum_r phi(r) exp(-i k.r)|^2 (Eq. 80), accumulated
+// in FP64 over samples for every k of every system.  The discrete Fourier
+// transform is taken one axis at a time (x: real -> complex, then y, z) with
+// per-side twiddle tables W_n^j = exp(-2 pi i j / n); each output element sums
+// its line directly in a fixed order.  Shell binning (j(j-1) < |n|^2 <= j(j+1))
+// happens only when the accumulated spectrum is read.
+#include "lattice_kernels.cuh"
+#include "lb_launch.h"
+
+namespace lbf {
+
+namespace {
+
+__global__ void sk_twiddle_kernel(double* __restrict__ tw, const int* __restrict__ sides,
+                                  const int* __restrict__ offs, int n_tables, int max_n) {
+    const int t = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tables) return;
+    const int n = sides[t];
+    if (j >= n || j >= max_n) return;
+    double s, c;
+    sincospi(-2.0 * double(j) / double(n), &s, &c);
+    tw[2 * (offs[t] + j)] = c;
+    tw[2 * (offs[t] + j) + 1] = s;
+}
+
+// item: (system, first element, end element, unused); element e of a system
+// enumerates its sites in [z][y][x] order, and names the output (k_x, y, z) etc.
+__global__ void __launch_bounds__(AUX_THREADS)
+    sk_x_kernel(const SysDev* __restrict__ sysv, const SkSys* __restrict__ skv, const int4* __restrict__ items,
+                const double* __restrict__ d, const double* __restrict__ dbar, const double* __restrict__ tw,
+                double* __restrict__ out) {
+    const int4 it = items[blockIdx.x];
+    const SkSys K = skv[it.x];
+    const SysDev& S = sysv[it.x];
+    const double db = dbar[it.x];
+    const double inv_rbar = 1.0 / (S.rho_c + db);
+    for (int j = 0; j < SITES_PER_THREAD; ++j) {
+        const int e = it.y + j * AUX_THREADS + threadIdx.x;
+        if (e >= it.z) break;
+        const int kx = e % K.nx;
+        const int line = e - kx;
+        const double* row = d + K.site_offset + line;
+        double re = 0.0, im = 0.0;
+        int idx = 0;                      // (kx * x) mod nx, advanced incrementally
+        for (int x = 0; x < K.nx; ++x) {
+            const double phi = (row[x] - db) * inv_rbar;
+            re += phi * tw[2 * (K.tw_x + idx)];
+            im += phi * tw[2 * (K.tw_x + idx) + 1];
+            idx += kx;
+            if (idx >= K.nx) idx -= K.nx;
+        }
+        out[2 * (K.site_offset + e)] = re;
+        out[2 * (K.site_offset + e) + 1] = im;
+    }
+}
+
+__global__ void __launch_bounds__(AUX_THREADS)
+    sk_pass_kernel(const SkSys* __restrict__ skv, const int4* __restrict__ items, int axis,
+                   const double* __restrict__ tw, const double* __restrict__ in, double* __restrict__ out) {
+    const int4 it = items[blockIdx.x];
+    const SkSys K = skv[it.x];
+    const int n = axis == 1 ? K.ny : K.nz;
+    const int64_t stride = axis == 1 ? K.nx : int64_t(K.nx) * K.ny;
+    const int toff = axis == 1 ? K.tw_y : K.tw_z;
+    for (int j = 0; j < SITES_PER_THREAD; ++j) {
+        const int e = it.y + j * AUX_THREADS + threadIdx.x;
+        if (e >= it.z) break;
+        const int k = int((e / stride) % n);           // output wavenumber index along the axis
+        const int64_t base = e - int64_t(k) * stride;  // element with axis coordinate 0
+        const double* src = in + 2 * (K.site_offset + base);
+        double re = 0.0, im = 0.0;
+        int idx = 0;
+        for (int y = 0; y < n; ++y) {
+            const double ar = src[2 * (int64_t(y) * stride)], ai = src[2 * (int64_t(y) * stride) + 1];
+            const double wr = tw[2 * (toff + idx)], wi = tw[2 * (toff + idx) + 1];
+            re += ar * wr - ai * wi;
+            im += ar * wi + ai * wr;
+            idx += k;
+            if (idx >= n) idx -= n;
+        }
+        out[2 * (K.site_offset + e)] = re;
+        out[2 * (K.site_offset + e) + 1] = im;
+    }
+}
+
+__global__ void __launch_bounds__(AUX_THREADS)
+    sk_accum_kernel(const SkSys* __restrict__ skv, const int4* __restrict__ items, const double* __restrict__ F,
+                    double* __restrict__ acc) {
+    const int4 it = items[blockIdx.x];
+    const SkSys K = skv[it.x];
+    for (int j = 0; j < SITES_PER_THREAD; ++j) {
+        const int e = it.y + j * AUX_THREADS + threadIdx.x;
+        if (e >= it.z) break;
+        const int64_t g = K.site_offset + e;
+        const double re = F[2 * g], im = F[2 * g + 1];
+        acc[g] += (re * re + im * im) * K.inv_n;
+    }
+}
+
+__device__ __forceinline__ int wrapk(int k, int n) { return 2 * k < n ? k : k - n; }
+
+__global__ void __launch_bounds__(AUX_THREADS)
+    sk_bin_kernel(const SkSys* __restrict__ skv, int sys, const double* __restrict__ acc, double* __restrict__ sums,
+                  double* __restrict__ counts) {
+    __shared__ double sh[2 * AUX_THREADS];
+    const SkSys K = skv[sys];
+    const int bin = blockIdx.x + 1;                    // shells j = 1 .. nbins
+    const int64_t n = int64_t(K.nx) * K.ny * K.nz;
+    double v[2] = {0.0, 0.0};
+    const int64_t lo = int64_t(bin) * (bin - 1), hi = int64_t(bin) * (bin + 1);
+    for (int64_t e = threadIdx.x; e < n; e += AUX_THREADS) {
+        const int kx = int(e % K.nx), ky = int((e / K.nx) % K.ny), kz = int(e / (int64_t(K.nx) * K.ny));
+        const int64_t a = wrapk(kx, K.nx), b = wrapk(ky, K.ny), c = wrapk(kz, K.nz);
+        const int64_t n2 = a * a + b * b + c * c;
+        if (n2 > lo && n2 <= hi) {
+            v[0] += acc[K.site_offset + e];
+            v[1] += 1.0;
+        }
+    }
+    block_sum<2, AUX_THREADS>(v, sh);
+    if (threadIdx.x == 0) {
+        sums[blockIdx.x] = v[0];
+        counts[blockIdx.x] = v[1];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_sk_twiddles(double* tw, const int* sides, const int* offs, int n_tables, int max_n,
+                               cudaStream_t st) {
+    if (n_tables == 0) return cudaSuccess;
+    dim3 grid((max_n + 255) / 256, n_tables);
+    sk_twiddle_kernel<<<grid, 256, 0, st>>>(tw, sides, offs, n_tables, max_n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sk_x(const SysDev* sys, const SkSys* sk, const int4* items, int n_items, const double* d,
+                        const double* dbar, const double* tw, double* out, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    sk_x_kernel<<<n_items, AUX_THREADS, 0, st>>>(sys, sk, items, d, dbar, tw, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sk_pass(const SkSys* sk, const int4* items, int n_items, int axis, const double* tw,
+                           const double* in, double* out, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    sk_pass_kernel<<<n_items, AUX_THREADS, 0, st>>>(sk, items, axis, tw, in, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sk_accum(const SkSys* sk, const int4* items, int n_items, const double* F, double* acc,
+                            cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    sk_accum_kernel<<<n_items, AUX_THREADS, 0, st>>>(sk, items, F, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sk_bin(const SkSys* sk, int sys, const double* acc, int nbins, double* sums, double* counts,
+                          cudaStream_t st) {
+    if (nbins <= 0) return cudaSuccess;
+    sk_bin_kernel<<<nbins, AUX_THREADS, 0, st>>>(sk, sys, acc, sums, counts);
+    return cudaGetLastError();
+}
+
+}  // namespace lbf
