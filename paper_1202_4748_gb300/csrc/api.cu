@@ -360,6 +360,10 @@ SysDev to_dev(const SysHost& h) {
     }
     const int P = d.lattice == LB_D2Q9 ? 3 : 4, R = d.lattice == LB_D2Q9 ? 8 : 16;
     s.g_pair = 1.0 - gamma[P] * gamma[R];
+    s.bgk = 1;
+    for (int a = nc; a < q; ++a)
+        if (s.lam[a] != s.lam[nc]) s.bgk = 0;
+    s.lam_bgk = s.lam[nc];
     s.seed_lo = uint32_t(d.seed & 0xffffffffu);
     s.seed_hi = uint32_t(d.seed >> 32);
     s.system_id = d.system_id;
@@ -369,7 +373,7 @@ SysDev to_dev(const SysHost& h) {
 }  // namespace
 
 struct lb_ctx {
-    int lattice = 0, coupling = 0, fp32 = 0, q = 9, n_sys = 0, tile_id = 0;
+    int lattice = 0, coupling = 0, fp32 = 0, q = 9, n_sys = 0, tile_id = 0, bgk_only = 0;
     lb_run_opts opts{};
     std::vector<SysHost> sys;
     Plan P;
@@ -482,6 +486,7 @@ cudaError_t launch_steps(lb_ctx* c, int64_t n) {
         a.k = int(k);
         a.status = c->at<int>(P.status);
         a.tile_id = c->tile_id;
+        a.bgk_only = c->bgk_only;
         cudaError_t e = launch_step_any(c, a);
         if (e != cudaSuccess) return e;
         c->launches += 1;
@@ -593,6 +598,8 @@ lb_status lb_create(const lb_system_desc* systems, int n_systems, const lb_run_o
     const Plan& P = c->P;
     std::vector<SysDev> sd;
     for (auto& h : c->sys) sd.push_back(to_dev(h));
+    c->bgk_only = 1;
+    for (auto& s : sd) c->bgk_only &= s.bgk;
     bool ok = cudaMemcpyAsync(c->ws + P.sys, sd.data(), sizeof(SysDev) * sd.size(), cudaMemcpyHostToDevice,
                               c->stream) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(c->ws + P.tiles, P.tiles_h.data(), sizeof(int4) * P.n_tiles, cudaMemcpyHostToDevice,

@@ -5,15 +5,17 @@
 namespace lbf {
 
 namespace {
-constexpr int kTiles[][3] = {{16, 4, 4}, {32, 4, 2}, {32, 8, 1}};
+// (x, y, z-chunk) of the z-marching kernel
+constexpr int kTiles[][3] = {{16, 16, 16}, {32, 8, 16}, {16, 16, 32}, {16, 8, 16}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
 
 template <int CP, class Real>
 cudaError_t step_tile(const StepLaunch& a, cudaStream_t st) {
     switch (a.tile_id) {
-        case 0: return step_one<D3Q19, CP, Real, 16, 4, 4>(a, st);
-        case 1: return step_one<D3Q19, CP, Real, 32, 4, 2>(a, st);
-        case 2: return step_one<D3Q19, CP, Real, 32, 8, 1>(a, st);
+        case 0: return step_z<D3Q19, CP, Real, 16, 16, 16>(a, st);
+        case 1: return step_z<D3Q19, CP, Real, 32, 8, 16>(a, st);
+        case 2: return step_z<D3Q19, CP, Real, 16, 16, 32>(a, st);
+        case 3: return step_z<D3Q19, CP, Real, 16, 8, 16>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }

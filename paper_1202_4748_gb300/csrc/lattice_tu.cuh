@@ -8,8 +8,8 @@
 
 namespace lbf {
 
-template <class L, int CP, class Real, int TX, int TY, int TZ>
-cudaError_t step_one(const StepLaunch& a, cudaStream_t st) {
+template <class L, int CP, class Real, int TX, int TY, int TZ, bool BGK_ONLY>
+cudaError_t step_one_mode(const StepLaunch& a, cudaStream_t st) {
     StepArgs<Real> A;
     A.sys = a.sys;
     A.tiles = a.tiles;
@@ -18,8 +18,35 @@ cudaError_t step_one(const StepLaunch& a, cudaStream_t st) {
     A.step_ptr = a.step_ptr;
     A.k = a.k;
     A.status = a.status;
-    step_kernel<L, CP, Real, TX, TY, TZ><<<a.n_tiles, TX * TY * TZ, 0, st>>>(A);
+    step_kernel<L, CP, Real, TX, TY, TZ, BGK_ONLY><<<a.n_tiles, TX * TY * TZ, 0, st>>>(A);
     return cudaGetLastError();
+}
+
+template <class L, int CP, class Real, int TX, int TY, int ZC, bool BGK_ONLY>
+cudaError_t step_z_mode(const StepLaunch& a, cudaStream_t st) {
+    StepArgs<Real> A;
+    A.sys = a.sys;
+    A.tiles = a.tiles;
+    A.fin = static_cast<const Real*>(a.fin);
+    A.fout = static_cast<Real*>(a.fout);
+    A.step_ptr = a.step_ptr;
+    A.k = a.k;
+    A.status = a.status;
+    step_kernel_z<L, CP, Real, TX, TY, ZC, BGK_ONLY><<<a.n_tiles, TX * TY, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+// z-marching launch: tile = (TX, TY, z-chunk)
+template <class L, int CP, class Real, int TX, int TY, int ZC>
+cudaError_t step_z(const StepLaunch& a, cudaStream_t st) {
+    if (a.bgk_only) return step_z_mode<L, CP, Real, TX, TY, ZC, true>(a, st);
+    return step_z_mode<L, CP, Real, TX, TY, ZC, false>(a, st);
+}
+
+template <class L, int CP, class Real, int TX, int TY, int TZ>
+cudaError_t step_one(const StepLaunch& a, cudaStream_t st) {
+    if (a.bgk_only) return step_one_mode<L, CP, Real, TX, TY, TZ, true>(a, st);
+    return step_one_mode<L, CP, Real, TX, TY, TZ, false>(a, st);
 }
 
 template <class L, class Real>

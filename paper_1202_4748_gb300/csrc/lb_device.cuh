@@ -157,7 +157,8 @@ struct SysDev {
     double g_pair;                 // 1 - gamma_P gamma_R
     uint32_t seed_lo, seed_hi;
     uint32_t system_id;
-    int32_t pad;
+    int32_t bgk;                   // 1: every non-conserved mode relaxes at the same rate lam_bgk
+    double lam_bgk;
 };
 
 // ---------------------------------------------------------------------------
@@ -170,11 +171,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint32_t k0, uint32_t 
             k0 += 0x9E3779B9u;
             k1 += 0xBB67AE85u;
         }
-        const uint32_t hi_a = __umulhi(0xD2511F53u, ctr.x);
-        const uint32_t lo_a = 0xD2511F53u * ctr.x;
-        const uint32_t hi_b = __umulhi(0xCD9E8D57u, ctr.z);
-        const uint32_t lo_b = 0xCD9E8D57u * ctr.z;
-        ctr = make_uint4(hi_b ^ ctr.y ^ k0, lo_b, hi_a ^ ctr.w ^ k1, lo_a);
+        // one 32 x 32 -> 64-bit product per multiplier (high and low words together)
+        const uint64_t pa = uint64_t(0xD2511F53u) * ctr.x;
+        const uint64_t pb = uint64_t(0xCD9E8D57u) * ctr.z;
+        ctr = make_uint4(uint32_t(pb >> 32) ^ ctr.y ^ k0, uint32_t(pb), uint32_t(pa >> 32) ^ ctr.w ^ k1,
+                         uint32_t(pa));
     }
     return ctr;
 }
@@ -197,14 +198,18 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0,
     n0 = r * c;
     n1 = r * s;
 }
+// FP32 variant on the special-function unit: -2 ln U = -2 ln2 log2 U, clamped
+// at 0 because log2 of U within an ulp of 1 may come out slightly positive;
+// the angle is taken as 2 pi (U_b - 1/2) in [-pi, pi), where the hardware
+// sine/cosine are accurate, and the half turn is undone by the sign flips.
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
-    const float ua = (float(wa) + 0.5f) * 2.3283064365386963e-10f;
-    const float ub = (float(wb) + 0.5f) * 2.3283064365386963e-10f;
-    const float r = sqrtf(-2.0f * logf(ua));
+    const float ua = fmaf(float(wa), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float ub = fmaf(float(wb), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float r = sqrtf(fmaxf(-1.3862943611198906f * __log2f(ua), 0.0f));
     float s, c;
-    sincospif(2.0f * ub, &s, &c);
-    n0 = r * c;
-    n1 = r * s;
+    __sincosf(6.2831853071795865f * (ub - 0.5f), &s, &c);
+    n0 = -r * c;
+    n1 = -r * s;
 }
 
 // Periodic wrap of a coordinate that is at most one period outside [0, n).

@@ -1,13 +1,19 @@
 // Fused fluctuating LB time step (Eq. 61): pull-stream, moments (Eq. 62),
 // density gradients from a shared-memory halo, equilibrium (Eq. 65 or the
-// Landau-pressure form with a Guo body force), moment-space relaxation with
-// per-mode rates (Eq. 66), local Cholesky-factored noise (Eq. 68), aligned store.
+// Landau-pressure form with a Guo body force), relaxation (Eq. 66), local
+// Cholesky-factored noise (Eq. 68), aligned store.
 //
 // Storage: per system, SoA populations [q][z][y][x] holding deviations
 // delta f_i = f_i - f^eq_i(rho_c, u = 0), i.e. f_0 - rho_c on the rest velocity
 // and f_i elsewhere.  The buffer read by step t holds the post-collision
 // populations of step t-1 at their origin sites, so the pre-collision value
 // f_i(r, t) is pulled from r - c_i and every store is aligned.
+//
+// Relaxation: when every non-conserved mode relaxes at one rate (the paper's
+// single-tau BGK form of Eq. 61, and tau = 1 in every workload) the update is
+// done on the populations, f <- f - lam (f - f^eq) + (1 - lam/2) F_i + T^-1 xi,
+// which equals the moment-space form because T is linear and invertible;
+// otherwise each moment relaxes at its own rate in the basis of Eq. 66.
 #pragma once
 
 #include "lb_device.cuh"
@@ -34,14 +40,112 @@ struct HaloOf {
 // Linear site index inside a system.
 __device__ __forceinline__ int site_index(int x, int y, int z, int nx, int ny) { return x + nx * (y + ny * z); }
 
+// Wrapped neighbour coordinates of a site inside its system, as index offsets:
+// X[1 + d] = x + d, Y[1 + d] = (y + d) nx, Z[1 + d] = (z + d) nx ny  (d = -1, 0, 1).
+struct Nbr {
+    int X[3], Y[3], Z[3];
+    __device__ __forceinline__ Nbr(int x, int y, int z, int nx, int ny, int nz, bool d3) {
+        X[0] = x == 0 ? nx - 1 : x - 1;
+        X[1] = x;
+        X[2] = x == nx - 1 ? 0 : x + 1;
+        Y[0] = (y == 0 ? ny - 1 : y - 1) * nx;
+        Y[1] = y * nx;
+        Y[2] = (y == ny - 1 ? 0 : y + 1) * nx;
+        if (d3) {
+            const int pl = nx * ny;
+            Z[0] = (z == 0 ? nz - 1 : z - 1) * pl;
+            Z[1] = z * pl;
+            Z[2] = (z == nz - 1 ? 0 : z + 1) * pl;
+        } else {
+            Z[0] = Z[1] = Z[2] = 0;
+        }
+    }
+    // index of r + c for a compile-time velocity c
+    template <int CX, int CY, int CZ>
+    __device__ __forceinline__ int at() const { return X[1 + CX] + Y[1 + CY] + Z[1 + CZ]; }
+};
+
+// Neighbourhood views of a shared-memory field around the collided site:
+// at<cx, cy, cz>() is the value at r + c.
+template <class Real, int PX, int PY>
+struct TileView {          // one 3-D block with row pitch PX and plane pitch PX * PY
+    const Real* p;
+    int c;
+    template <int CX, int CY, int CZ>
+    __device__ __forceinline__ Real at() const { return p[c + CX + PX * (CY + PY * CZ)]; }
+};
+template <class Real, int PX>
+struct RingView {          // three planes (z - 1, z, z + 1) at arbitrary offsets, row pitch PX
+    const Real* p;
+    int zm, z0, zp, c;
+    template <int CX, int CY, int CZ>
+    __device__ __forceinline__ Real at() const {
+        return p[(CZ == 0 ? z0 : (CZ > 0 ? zp : zm)) + c + CX + PX * CY];
+    }
+};
+
+// Pull all q populations of the site described by `nb` (f_i(r) = buf_i(r - c_i)).
+template <class L, class Real>
+__device__ __forceinline__ void pull_site(const Real* __restrict__ fb, int64_t N, const Nbr& nb, Real (&f)[L::Q]) {
+    sfor<0, L::Q>([&](auto I) {
+        constexpr int i = I;
+        f[i] = fb[int64_t(i) * N + nb.template at<-L::c(i, 0), -L::c(i, 1), -L::c(i, 2)>()];
+    });
+}
+
+// Moment-space noise of Eq. 68 on the non-conserved modes: xi[a - NC].
+template <class L, class Real>
+__device__ __forceinline__ void noise_modes(const SysDev& S, uint32_t site, int64_t step, Real rho, Real cs2,
+                                            Real (&xi)[L::Q - L::NC], int* status) {
+    constexpr int Q = L::Q;
+    constexpr int K = Q - L::NC;
+    constexpr int NDRAW = (K + 3) / 4;
+    Real nrm[4 * NDRAW];
+    sfor<0, NDRAW>([&](auto D) {
+        constexpr int d = D;
+        const uint4 w = site_draw(S, site, step, uint32_t(d));
+        box_muller(w.x, w.y, nrm[4 * d + 0], nrm[4 * d + 1]);
+        box_muller(w.z, w.w, nrm[4 * d + 2], nrm[4 * d + 3]);
+    });
+    const Real sc = sqrt(Real(3) * (rho > Real(0) ? rho : Real(0)) * Real(S.kT));
+    // the coupled pair (P, R): M = [N + (1 - 3 c_s^2) v v^T] g, v_a = T_a(c = 0)
+    constexpr int P = L::PP, R = L::PR;
+    constexpr double vP = double(L::T(P, 0)), vR = double(L::T(R, 0));
+    constexpr double NP = norm2<L>(P), NR = norm2<L>(R);
+    const Real om = Real(1) - Real(3) * cs2;
+    const Real Mpp = (Real(NP) + om * Real(vP * vP)) * Real(S.g_diag[P]);
+    const Real Mrr = (Real(NR) + om * Real(vR * vR)) * Real(S.g_diag[R]);
+    const Real Mpr = om * Real(vP * vR) * Real(S.g_pair);
+    const Real det = Mpp * Mrr - Mpr * Mpr;
+    if (Mpp > Real(0) && det > Real(0)) {
+        const Real l11 = sqrt(Mpp);
+        const Real l21 = Mpr / l11;
+        const Real l22 = sqrt(det / Mpp);
+        const Real nP = nrm[P - L::NC], nR = nrm[R - L::NC];
+        xi[P - L::NC] = sc * l11 * nP;
+        xi[R - L::NC] = sc * (l21 * nP + l22 * nR);
+    } else {
+        atomicOr(status, ST_NOISE);
+        xi[P - L::NC] = Real(0);
+        xi[R - L::NC] = Real(0);
+    }
+    sfor<L::NC, Q>([&](auto A) {
+        constexpr int a = A;
+        if constexpr (a != P && a != R) {
+            constexpr double Na = norm2<L>(a);
+            xi[a - L::NC] = sc * sqrt(Real(Na) * Real(S.g_diag[a])) * nrm[a - L::NC];
+        }
+    });
+}
+
 // Collision of one site given its pulled deviations f[], the density halo and
 // (Guo) the Laplacian halo.  Returns post-collision deviations in f[].
-template <class L, int CP, class Real, int SX, int SY, int LX, int LY>
-__device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, const Real* __restrict__ srho,
-                                             const int cidx, const Real* __restrict__ slap, const int lidx,
+template <class L, int CP, class Real, bool BGK_ONLY, class RhoV, class LapV>
+__device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, const RhoV& rv, const LapV& lv,
                                              const SysDev& S, const uint32_t site, const int64_t step,
                                              int* status) {
     constexpr int Q = L::Q;
+    constexpr int K = Q - L::NC;
     const Real rho = Real(S.rho_c) + drho;
     if (!(rho > Real(0))) atomicOr(status, ST_RHO);
 
@@ -65,17 +169,19 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
     const Real p0 = rho * irc * df0 - f0;
     const Real cs2 = rho * irc * irc * (A_ + Real(3) * B_ * phi * phi);
 
-    Real feq[Q];
-    Real fsrc[Q];   // Guo population force
+    Real feq[BGK_ONLY ? 1 : Q];
+    Real fsrc[BGK_ONLY ? 1 : Q];   // Guo population force
     Real F[3] = {Real(0), Real(0), Real(0)};
+    // single-rate update f <- f - lam (f - f^eq) + (1 - lam/2) F_i done in the loops below
+    const Real lam_b = Real(S.lam_bgk);
+    const Real fs_b = Real(1) - Real(0.5) * lam_b;
     if constexpr (CP == MODEQ) {
         // d_a rho = 3 sum_i t_i c_ia rho(r+c_i);  lap rho = 6 sum_i t_i (rho(r+c_i) - rho(r))
         Real g[2] = {Real(0), Real(0)};
         Real lap = Real(0);
         sfor<1, Q>([&](auto I) {
             constexpr int i = I;
-            constexpr int off = L::c(i, 0) + SX * (L::c(i, 1) + SY * L::c(i, 2));
-            const Real rn = srho[cidx + off];
+            const Real rn = rv.template at<L::c(i, 0), L::c(i, 1), L::c(i, 2)>();
             if constexpr (L::c(i, 0) != 0) g[0] += Real(3.0 * L::w(i) * L::c(i, 0)) * rn;
             if constexpr (L::c(i, 1) != 0) g[1] += Real(3.0 * L::w(i) * L::c(i, 1)) * rn;
             lap += Real(6.0 * L::w(i)) * (rn - drho);
@@ -103,17 +209,19 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
             Real v = Real(pooley_w(i)) * (iso + rho * cu + Real(1.5) * xcc) + Real(pooley_wxx(i)) * gxx +
                      Real(pooley_wyy(i)) * gyy;
             if constexpr (pooley_wxy(i) != 0.0) v += Real(pooley_wxy(i)) * gxy;
-            feq[i] = v;
             s += v;
+            if constexpr (BGK_ONLY) f[i] -= lam_b * (f[i] - v);
+            else feq[i] = v;
         });
-        feq[0] = drho - s;   // deviation form of f_0 = rho - sum_{i>=1} f_i
+        // deviation form of f_0 = rho - sum_{i>=1} f_i
+        if constexpr (BGK_ONLY) f[0] -= lam_b * (f[0] - (drho - s));
+        else feq[0] = drho - s;
     } else {
         // Guo body force F = kappa rho grad(lap rho)
         Real gl[3] = {Real(0), Real(0), Real(0)};
         sfor<1, Q>([&](auto I) {
             constexpr int i = I;
-            constexpr int off = L::c(i, 0) + LX * (L::c(i, 1) + LY * L::c(i, 2));
-            const Real ln = slap[lidx + off];
+            const Real ln = lv.template at<L::c(i, 0), L::c(i, 1), L::c(i, 2)>();
             sfor<0, L::D>([&](auto A) {
                 constexpr int a = A;
                 if constexpr (L::c(i, a) != 0) gl[a] += Real(3.0 * L::w(i) * L::c(i, a)) * ln;
@@ -146,15 +254,62 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
             });
             constexpr double wi = L::w(i);
             const Real v = Real(wi) * (p3 + rho * (Real(3) * cu + Real(4.5) * cu * cu - Real(1.5) * uu));
-            feq[i] = v;
-            fsrc[i] = Real(wi) * (Real(3) * (cF - uF) + Real(9) * cu * cF);
+            const Real src = Real(wi) * (Real(3) * (cF - uF) + Real(9) * cu * cF);
             s += v;
+            if constexpr (BGK_ONLY) {
+                f[i] -= lam_b * (f[i] - v);
+                f[i] += fs_b * src;
+            } else {
+                feq[i] = v;
+                fsrc[i] = src;
+            }
         });
-        feq[0] = drho - s;
-        fsrc[0] = Real(-3.0 * L::w(0)) * uF;
+        if constexpr (BGK_ONLY) {
+            f[0] -= lam_b * (f[0] - (drho - s));
+            f[0] += fs_b * Real(-3.0 * L::w(0)) * uF;
+        } else {
+            feq[0] = drho - s;
+            fsrc[0] = Real(-3.0 * L::w(0)) * uF;
+        }
     }
 
-    // moments of f (deviation), relaxation of the non-conserved ones
+    Real xi[K];
+    sfor<0, K>([&](auto A) { xi[decltype(A)::value] = Real(0); });
+    if (S.kT > 0.0) noise_modes<L, Real>(S, site, step, rho, cs2, xi, status);
+
+    if constexpr (BGK_ONLY) {
+        // f already relaxed and forced; add the noise through f_i += sum_a t_i T_ai xi_a / N_a
+        sfor<0, Q>([&](auto I) {
+            constexpr int i = I;
+            Real v = f[i];
+            sfor<L::NC, Q>([&](auto A) {
+                constexpr int a = A;
+                constexpr double coef = tinv<L>(i, a);
+                if constexpr (coef != 0.0) v += Real(coef) * xi[a - L::NC];
+            });
+            f[i] = v;
+        });
+        return;
+    } else {
+    if (S.bgk) {
+        // single relaxation rate: population-space update plus T^-1 xi
+        const Real lam = Real(S.lam_bgk);
+        const Real fs = Real(1) - Real(0.5) * lam;
+        sfor<0, Q>([&](auto I) {
+            constexpr int i = I;
+            Real v = f[i] - lam * (f[i] - feq[i]);
+            if constexpr (CP == GUO) v += fs * fsrc[i];
+            sfor<L::NC, Q>([&](auto A) {
+                constexpr int a = A;
+                constexpr double coef = tinv<L>(i, a);
+                if constexpr (coef != 0.0) v += Real(coef) * xi[a - L::NC];
+            });
+            f[i] = v;
+        });
+        return;
+    }
+
+    // per-mode rates: moments of f (deviation), relaxation of the non-conserved ones
     Real m[Q];
     sfor<0, Q>([&](auto A) {
         constexpr int a = A;
@@ -191,6 +346,7 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
             });
             m[a] += (Real(1) - Real(0.5) * lam) * fh;
         }
+        m[a] += xi[a - L::NC];
     });
     if constexpr (CP == GUO) {
         sfor<0, L::D>([&](auto A) {
@@ -198,48 +354,6 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
             m[1 + a] += F[a];   // (T F)_a = F_a on the momentum rows
         });
     }
-
-    // noise (Eq. 68): xi = sqrt(3 rho kT) L n on the non-conserved modes
-    const Real kT = Real(S.kT);
-    if (kT > Real(0)) {
-        constexpr int K = Q - L::NC;
-        constexpr int NDRAW = (K + 3) / 4;
-        Real nrm[4 * NDRAW];
-        sfor<0, NDRAW>([&](auto D) {
-            constexpr int d = D;
-            const uint4 w = site_draw(S, site, step, uint32_t(d));
-            box_muller(w.x, w.y, nrm[4 * d + 0], nrm[4 * d + 1]);
-            box_muller(w.z, w.w, nrm[4 * d + 2], nrm[4 * d + 3]);
-        });
-        const Real sc = sqrt(Real(3) * (rho > Real(0) ? rho : Real(0)) * kT);
-        // the coupled pair (P, R): M = [N + (1 - 3 c_s^2) v v^T] g, v_a = T_a(c = 0)
-        constexpr int P = L::PP, R = L::PR;
-        constexpr double vP = double(L::T(P, 0)), vR = double(L::T(R, 0));
-        constexpr double NP = norm2<L>(P), NR = norm2<L>(R);
-        const Real om = Real(1) - Real(3) * cs2;
-        const Real Mpp = (Real(NP) + om * Real(vP * vP)) * Real(S.g_diag[P]);
-        const Real Mrr = (Real(NR) + om * Real(vR * vR)) * Real(S.g_diag[R]);
-        const Real Mpr = om * Real(vP * vR) * Real(S.g_pair);
-        const Real det = Mpp * Mrr - Mpr * Mpr;
-        if (Mpp > Real(0) && det > Real(0)) {
-            const Real l11 = sqrt(Mpp);
-            const Real l21 = Mpr / l11;
-            const Real l22 = sqrt(det / Mpp);
-            const Real nP = nrm[P - L::NC], nR = nrm[R - L::NC];
-            m[P] += sc * l11 * nP;
-            m[R] += sc * (l21 * nP + l22 * nR);
-        } else {
-            atomicOr(status, ST_NOISE);
-        }
-        sfor<L::NC, Q>([&](auto A) {
-            constexpr int a = A;
-            if constexpr (a != P && a != R) {
-                constexpr double Na = norm2<L>(a);
-                m[a] += sc * sqrt(Real(Na) * Real(S.g_diag[a])) * nrm[a - L::NC];
-            }
-        });
-    }
-
     // back to populations: f_i = t_i sum_a T_ai m_a / N_a
     sfor<0, Q>([&](auto I) {
         constexpr int i = I;
@@ -251,9 +365,10 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
         });
         f[i] = s;
     });
+    }
 }
 
-template <class L, int CP, class Real, int TX, int TY, int TZ>
+template <class L, int CP, class Real, int TX, int TY, int TZ, bool BGK_ONLY>
 __global__ void __launch_bounds__(TX* TY* TZ)
     step_kernel(const StepArgs<Real> A) {
     constexpr int Q = L::Q;
@@ -280,14 +395,9 @@ __global__ void __launch_bounds__(TX* TY* TZ)
     Real f[Q];
     Real drho = Real(0);
     if (valid) {
-        sfor<0, Q>([&](auto I) {
-            constexpr int i = I;
-            const int sx = L::c(i, 0) == 0 ? x : wrap1(x - L::c(i, 0), nx);
-            const int sy = L::c(i, 1) == 0 ? y : wrap1(y - L::c(i, 1), ny);
-            const int sz = L::D == 3 ? (L::c(i, 2) == 0 ? z : wrap1(z - L::c(i, 2), nz)) : 0;
-            f[i] = fb[int64_t(i) * N + site_index(sx, sy, sz, nx, ny)];
-            drho += f[i];
-        });
+        const Nbr nb(x, y, z, nx, ny, nz, L::D == 3);
+        pull_site<L, Real>(fb, N, nb, f);
+        sfor<0, Q>([&](auto I) { drho += f[decltype(I)::value]; });
     }
     const int cidx = (tz + HZ) * SX * SY + (ty + H) * SX + (tx + H);
 
@@ -303,15 +413,10 @@ __global__ void __launch_bounds__(TX* TY* TZ)
         if (interior && gx < nx && gy < ny && gz < nz) continue;
         Real v = Real(0);
         if (gx < nx + H && gy < ny + H && gz < nz + HZ) {
-            // the wrapped base lies in [0, n), so its pulls need a single-branch wrap
-            const int wx = wrapm(gx, nx), wy = wrapm(gy, ny), wz = L::D == 3 ? wrapm(gz, nz) : 0;
-            sfor<0, Q>([&](auto I) {
-                constexpr int i = I;
-                const int sx = L::c(i, 0) == 0 ? wx : wrap1(wx - L::c(i, 0), nx);
-                const int sy = L::c(i, 1) == 0 ? wy : wrap1(wy - L::c(i, 1), ny);
-                const int sz = L::D == 3 ? (L::c(i, 2) == 0 ? wz : wrap1(wz - L::c(i, 2), nz)) : 0;
-                v += fb[int64_t(i) * N + site_index(sx, sy, sz, nx, ny)];
-            });
+            const Nbr nb(wrapm(gx, nx), wrapm(gy, ny), L::D == 3 ? wrapm(gz, nz) : 0, nx, ny, nz, L::D == 3);
+            Real g[Q];
+            pull_site<L, Real>(fb, N, nb, g);
+            sfor<0, Q>([&](auto I) { v += g[decltype(I)::value]; });
         }
         srho[idx] = v;
     }
@@ -339,13 +444,122 @@ __global__ void __launch_bounds__(TX* TY* TZ)
 
     const int site = site_index(x, y, z, nx, ny);
     const int64_t step = *A.step_ptr + A.k;
-    collide_site<L, CP, Real, SX, SY, LX, LY>(f, drho, srho, cidx, slap, lidx, S, uint32_t(site), step, A.status);
+    const TileView<Real, SX, SY> rv{srho, cidx};
+    const TileView<Real, LX, LY> lv{slap, lidx};
+    collide_site<L, CP, Real, BGK_ONLY>(f, drho, rv, lv, S, uint32_t(site), step, A.status);
 
     Real* __restrict__ fo = A.fout + S.pop_offset;
     sfor<0, Q>([&](auto I) {
         constexpr int i = I;
         fo[int64_t(i) * N + site] = f[i];
     });
+}
+
+}  // namespace lbf
+
+namespace lbf {
+
+// z-marching variant for 3-D lattices.  A CTA owns a TX x TY column of sites
+// and walks a chunk of ZC planes.  The density deviation of each plane is
+// computed once on the column's footprint (halo H in x and y) into a ring of
+// 2H+1 planes in shared memory, the Laplacian (Guo force) into a ring of 3
+// planes, so every footprint value is formed once per chunk instead of once
+// per tile, and the collision of plane z follows two planes behind.
+template <class L, int CP, class Real, int TX, int TY, int ZC, bool BGK_ONLY>
+__global__ void __launch_bounds__(TX* TY)
+    step_kernel_z(const StepArgs<Real> A) {
+    static_assert(L::D == 3, "z-marching is for 3-D lattices");
+    constexpr int Q = L::Q;
+    constexpr int H = HaloOf<L, CP>::H;
+    constexpr int SX = TX + 2 * H, SY = TY + 2 * H, SP = SX * SY;     // rho footprint plane
+    constexpr int NR = 2 * H + 1;                                     // rho ring planes
+    constexpr int LX = TX + 2, LY = TY + 2, LP = LX * LY;             // Laplacian plane (Guo)
+    constexpr int NL = CP == GUO ? 3 : 1;
+    constexpr int NT = TX * TY;
+    __shared__ Real srho[NR * SP];
+    __shared__ Real slap[NL * LP];
+
+    const int4 tl = A.tiles[blockIdx.x];
+    const SysDev& S = A.sys[tl.x];
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const int64_t N = S.n_sites;
+    const Real* __restrict__ fb = A.fin + S.pop_offset;
+    Real* __restrict__ fo = A.fout + S.pop_offset;
+    const int z0 = tl.w, z1 = min(z0 + ZC, nz);
+    const int64_t step = *A.step_ptr + A.k;
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int x = tl.y + tx, y = tl.z + ty;
+    const bool valid_xy = x < nx && y < ny;
+
+    // planes of rho needed: z0 - H .. z1 - 1 + H; collision of plane zc trails rho by H
+    for (int zz = z0 - H; zz < z1 + H; ++zz) {
+        const int slot = (zz - z0 + 2 * NR) % NR;
+        const int wz = wrapm(zz, nz);
+        for (int idx = tid; idx < SP; idx += NT) {
+            const int px = idx % SX, py = idx / SX;
+            const int gx = tl.y + px - H, gy = tl.z + py - H;
+            Real v = Real(0);
+            if (gx < nx + H && gy < ny + H) {
+                const Nbr nb(wrapm(gx, nx), wrapm(gy, ny), wz, nx, ny, nz, true);
+                Real g[Q];
+                pull_site<L, Real>(fb, N, nb, g);
+                sfor<0, Q>([&](auto I) { v += g[decltype(I)::value]; });
+            }
+            srho[slot * SP + idx] = v;
+        }
+        __syncthreads();
+        if constexpr (CP == GUO) {
+            // Laplacian of plane zl = zz - 1 on the column + 1 (needs rho planes zl-1 .. zl+1)
+            const int zl = zz - 1;
+            if (zl >= z0 - 1) {
+                const int lslot = (zl - z0 + 6) % 3;
+                const int r0 = (zl - z0 + 2 * NR) % NR;
+                const int rm = (zl - 1 - z0 + 2 * NR) % NR;
+                const int rp = (zl + 1 - z0 + 2 * NR) % NR;
+                for (int idx = tid; idx < LP; idx += NT) {
+                    const int px = idx % LX, py = idx / LX;
+                    const int c = (py + H - 1) * SX + (px + H - 1);
+                    const Real rc = srho[r0 * SP + c];
+                    Real lap = Real(0);
+                    sfor<1, Q>([&](auto I) {
+                        constexpr int i = I;
+                        constexpr int cz = L::c(i, 2);
+                        constexpr int off = L::c(i, 0) + SX * L::c(i, 1);
+                        const int pl = cz == 0 ? r0 : (cz > 0 ? rp : rm);
+                        lap += Real(6.0 * L::w(i)) * (srho[pl * SP + c + off] - rc);
+                    });
+                    slap[lslot * LP + idx] = lap;
+                }
+            }
+            __syncthreads();
+        }
+        // collision of plane zc = zz - H
+        const int zc = zz - H;
+        if (zc >= z0 && valid_xy) {
+            const Nbr nb(x, y, zc, nx, ny, nz, true);
+            Real f[Q];
+            pull_site<L, Real>(fb, N, nb, f);
+            Real drho = Real(0);
+            sfor<0, Q>([&](auto I) { drho += f[decltype(I)::value]; });
+            const int site = site_index(x, y, zc, nx, ny);
+            // the collision reads rho (MODEQ) or the Laplacian (GUO) around the site;
+            // GUO needs only lap planes zc-1..zc+1, addressed through a 3-plane view
+            const RingView<Real, SX> rv{srho, ((zc - 1 - z0 + 2 * NR) % NR) * SP, ((zc - z0 + 2 * NR) % NR) * SP,
+                                        ((zc + 1 - z0 + 2 * NR) % NR) * SP, (ty + H) * SX + (tx + H)};
+            const RingView<Real, LX> lv{slap, ((zc - 1 - z0 + 6) % 3) * LP, ((zc - z0 + 6) % 3) * LP,
+                                        ((zc + 1 - z0 + 6) % 3) * LP, (ty + 1) * LX + (tx + 1)};
+            collide_site<L, CP, Real, BGK_ONLY>(f, drho, rv, lv, S, uint32_t(site), step, A.status);
+            sfor<0, Q>([&](auto I) {
+                constexpr int i = I;
+                fo[int64_t(i) * N + site] = f[i];
+            });
+        }
+        // the next iteration overwrites a rho slot and (Guo) a Laplacian slot that
+        // the collision above may still read
+        __syncthreads();
+    }
 }
 
 }  // namespace lbf
