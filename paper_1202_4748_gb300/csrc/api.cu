@@ -68,7 +68,7 @@ lb_status validate(const lb_system_desc* s, int n, const lb_run_opts* o) {
         if (d.coupling == LB_MODEQ && d.lattice != LB_D2Q9) return LB_ERR_ARG;
         if (d.nx < 1 || d.ny < 1 || d.nz < 1) return LB_ERR_ARG;
         if (d.lattice == LB_D2Q9 && d.nz != 1) return LB_ERR_ARG;
-        if (int64_t(d.nx) * d.ny * d.nz >= (int64_t(1) << 31)) return LB_ERR_ARG;
+        if (int64_t(d.nx) * d.ny * d.nz * q_of(d.lattice) >= (int64_t(1) << 31)) return LB_ERR_ARG;
         if (!(d.rho_c > 0) || !std::isfinite(d.a) || !std::isfinite(d.b) || !(d.kappa >= 0) || !(d.kT >= 0) ||
             !std::isfinite(d.kT) || !std::isfinite(d.kappa))
             return LB_ERR_ARG;
@@ -342,6 +342,7 @@ SysDev to_dev(const SysHost& h) {
     s.ny = d.ny;
     s.nz = d.nz;
     s.small = (d.nx < H + 1 || d.ny < H + 1 || (d.lattice == LB_D3Q19 && d.nz < H + 1)) ? 1 : 0;
+    s.ns = int32_t(h.n);
     s.n_sites = h.n;
     s.site_offset = h.site_off;
     s.pop_offset = h.pop_off;
@@ -598,8 +599,12 @@ lb_status lb_create(const lb_system_desc* systems, int n_systems, const lb_run_o
     const Plan& P = c->P;
     std::vector<SysDev> sd;
     for (auto& h : c->sys) sd.push_back(to_dev(h));
-    c->bgk_only = 1;
-    for (auto& s : sd) c->bgk_only &= s.bgk;
+    // collision specialisation: 2 = one rate, equal to 1 everywhere; 1 = one rate per system; 0 = per mode
+    c->bgk_only = 2;
+    for (auto& s : sd) {
+        if (!s.bgk) c->bgk_only = 0;
+        else if (s.lam_bgk != 1.0 && c->bgk_only == 2) c->bgk_only = 1;
+    }
     bool ok = cudaMemcpyAsync(c->ws + P.sys, sd.data(), sizeof(SysDev) * sd.size(), cudaMemcpyHostToDevice,
                               c->stream) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(c->ws + P.tiles, P.tiles_h.data(), sizeof(int4) * P.n_tiles, cudaMemcpyHostToDevice,

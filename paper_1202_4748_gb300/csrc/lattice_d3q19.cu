@@ -6,16 +6,16 @@ namespace lbf {
 
 namespace {
 // (x, y, z-chunk) of the z-marching kernel
-constexpr int kTiles[][3] = {{16, 16, 16}, {32, 8, 16}, {16, 16, 32}, {16, 8, 16}};
+constexpr int kTiles[][3] = {{16, 16, 32}, {32, 8, 32}, {16, 16, 16}, {16, 8, 32}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
 
 template <int CP, class Real>
 cudaError_t step_tile(const StepLaunch& a, cudaStream_t st) {
     switch (a.tile_id) {
-        case 0: return step_z<D3Q19, CP, Real, 16, 16, 16>(a, st);
-        case 1: return step_z<D3Q19, CP, Real, 32, 8, 16>(a, st);
-        case 2: return step_z<D3Q19, CP, Real, 16, 16, 32>(a, st);
-        case 3: return step_z<D3Q19, CP, Real, 16, 8, 16>(a, st);
+        case 0: return step_z<D3Q19, CP, Real, 16, 16, 32>(a, st);
+        case 1: return step_z<D3Q19, CP, Real, 32, 8, 32>(a, st);
+        case 2: return step_z<D3Q19, CP, Real, 16, 16, 16>(a, st);
+        case 3: return step_z<D3Q19, CP, Real, 16, 8, 32>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -8,7 +8,7 @@
 
 namespace lbf {
 
-template <class L, int CP, class Real, int TX, int TY, int TZ, bool BGK_ONLY>
+template <class L, int CP, class Real, int TX, int TY, int TZ, int MODE>
 cudaError_t step_one_mode(const StepLaunch& a, cudaStream_t st) {
     StepArgs<Real> A;
     A.sys = a.sys;
@@ -18,11 +18,11 @@ cudaError_t step_one_mode(const StepLaunch& a, cudaStream_t st) {
     A.step_ptr = a.step_ptr;
     A.k = a.k;
     A.status = a.status;
-    step_kernel<L, CP, Real, TX, TY, TZ, BGK_ONLY><<<a.n_tiles, TX * TY * TZ, 0, st>>>(A);
+    step_kernel<L, CP, Real, TX, TY, TZ, MODE><<<a.n_tiles, TX * TY * TZ, 0, st>>>(A);
     return cudaGetLastError();
 }
 
-template <class L, int CP, class Real, int TX, int TY, int ZC, bool BGK_ONLY>
+template <class L, int CP, class Real, int TX, int TY, int ZC, int MODE>
 cudaError_t step_z_mode(const StepLaunch& a, cudaStream_t st) {
     StepArgs<Real> A;
     A.sys = a.sys;
@@ -32,21 +32,23 @@ cudaError_t step_z_mode(const StepLaunch& a, cudaStream_t st) {
     A.step_ptr = a.step_ptr;
     A.k = a.k;
     A.status = a.status;
-    step_kernel_z<L, CP, Real, TX, TY, ZC, BGK_ONLY><<<a.n_tiles, TX * TY, 0, st>>>(A);
+    step_kernel_z<L, CP, Real, TX, TY, ZC, MODE><<<a.n_tiles, TX * TY, 0, st>>>(A);
     return cudaGetLastError();
 }
 
 // z-marching launch: tile = (TX, TY, z-chunk)
 template <class L, int CP, class Real, int TX, int TY, int ZC>
 cudaError_t step_z(const StepLaunch& a, cudaStream_t st) {
-    if (a.bgk_only) return step_z_mode<L, CP, Real, TX, TY, ZC, true>(a, st);
-    return step_z_mode<L, CP, Real, TX, TY, ZC, false>(a, st);
+    if (a.bgk_only == 2) return step_z_mode<L, CP, Real, TX, TY, ZC, 2>(a, st);
+    if (a.bgk_only == 1) return step_z_mode<L, CP, Real, TX, TY, ZC, 1>(a, st);
+    return step_z_mode<L, CP, Real, TX, TY, ZC, 0>(a, st);
 }
 
 template <class L, int CP, class Real, int TX, int TY, int TZ>
 cudaError_t step_one(const StepLaunch& a, cudaStream_t st) {
-    if (a.bgk_only) return step_one_mode<L, CP, Real, TX, TY, TZ, true>(a, st);
-    return step_one_mode<L, CP, Real, TX, TY, TZ, false>(a, st);
+    if (a.bgk_only == 2) return step_one_mode<L, CP, Real, TX, TY, TZ, 2>(a, st);
+    if (a.bgk_only == 1) return step_one_mode<L, CP, Real, TX, TY, TZ, 1>(a, st);
+    return step_one_mode<L, CP, Real, TX, TY, TZ, 0>(a, st);
 }
 
 template <class L, class Real>

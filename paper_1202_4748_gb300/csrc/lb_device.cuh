@@ -126,6 +126,21 @@ __host__ __device__ constexpr double tinv(int i, int a) {
     return L::w(i) * double(L::T(a, i)) / norm2<L>(a);
 }
 
+// M_a,bc = sum_i t_i T_ai c_ib c_ic: second-moment projection of mode a.
+template <class L>
+__host__ __device__ constexpr double mproj(int a, int b, int c) {
+    double s = 0.0;
+    for (int i = 0; i < L::Q; ++i) s += L::w(i) * double(L::T(a, i)) * L::c(i, b) * L::c(i, c);
+    return s;
+}
+// Parity of mode a under c -> -c (+1 even, -1 odd), read off the basis.
+template <class L>
+__host__ __device__ constexpr int mode_parity(int a) {
+    for (int i = 1; i < L::Q; ++i)
+        if (L::T(a, i) != 0) return L::T(a, i) == L::T(a, i + ((i & 1) ? 1 : -1)) ? 1 : -1;
+    return 1;
+}
+
 enum Coupling { MODEQ = 0, GUO = 1 };
 
 // Modified-equilibrium weights of Eq. 65 (D2Q9 order above; index 0 unused).
@@ -145,7 +160,9 @@ __host__ __device__ constexpr double pooley_wxy(int i) {
 // ---------------------------------------------------------------------------
 struct SysDev {
     int32_t nx, ny, nz;
-    int32_t small;          // 1 if some side is too short for the single-branch wrap
+    int32_t small;          // 1 if some side is shorter than 3 (the footprint wrap needs a modulo)
+    int32_t ns;             // n_sites as 32 bit (q * n_sites < 2^31 is checked on the host)
+    int32_t pad0;
     int64_t n_sites;
     int64_t site_offset;    // first site of this system in the concatenated site arrays
     int64_t pop_offset;     // first population element: pop_offset + i * n_sites + site
@@ -212,6 +229,8 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, 
     n1 = -r * s;
 }
 
+// Periodic wrap of a coordinate in [-n, 2n).
+__device__ __forceinline__ int wrap2(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 // Periodic wrap of a coordinate that is at most one period outside [0, n).
 __device__ __forceinline__ int wrap1(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 // Any coordinate.

@@ -22,7 +22,7 @@ struct StepLaunch {
     int k;
     int* status;
     int tile_id;            // index into the lattice's tile-shape table
-    int bgk_only;           // every system relaxes all non-conserved modes at one rate
+    int bgk_only;           // 0: per-mode rates; 1: one rate per system; 2: one rate, equal to 1
 };
 
 // Tile shapes compiled for each lattice (x, y, z); index = tile_id.

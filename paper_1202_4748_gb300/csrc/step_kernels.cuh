@@ -86,10 +86,10 @@ struct RingView {          // three planes (z - 1, z, z + 1) at arbitrary offset
 
 // Pull all q populations of the site described by `nb` (f_i(r) = buf_i(r - c_i)).
 template <class L, class Real>
-__device__ __forceinline__ void pull_site(const Real* __restrict__ fb, int64_t N, const Nbr& nb, Real (&f)[L::Q]) {
+__device__ __forceinline__ void pull_site(const Real* __restrict__ fb, int N, const Nbr& nb, Real (&f)[L::Q]) {
     sfor<0, L::Q>([&](auto I) {
         constexpr int i = I;
-        f[i] = fb[int64_t(i) * N + nb.template at<-L::c(i, 0), -L::c(i, 1), -L::c(i, 2)>()];
+        f[i] = fb[i * N + nb.template at<-L::c(i, 0), -L::c(i, 1), -L::c(i, 2)>()];
     });
 }
 
@@ -136,6 +136,127 @@ __device__ __forceinline__ void noise_modes(const SysDev& S, uint32_t site, int6
             xi[a - L::NC] = sc * sqrt(Real(Na) * Real(S.g_diag[a])) * nrm[a - L::NC];
         }
     });
+}
+
+// f_i = t_i sum_a T_ai w_a / N_a for a full moment vector w, using the pairs
+// (i, i+1), i odd, of opposite velocities: f_i = E + O, f_{i+1} = E - O with E
+// (O) the sum over modes even (odd) in c.
+template <class L, class Real>
+__device__ __forceinline__ void from_moments(const Real (&w)[L::Q], Real (&out)[L::Q]) {
+    {
+        Real s = Real(0);
+        sfor<0, L::Q>([&](auto A) {
+            constexpr int a = A;
+            constexpr double coef = tinv<L>(0, a);
+            if constexpr (coef != 0.0) s += Real(coef) * w[a];
+        });
+        out[0] = s;
+    }
+    sfor<0, (L::Q - 1) / 2>([&](auto P) {
+        constexpr int i = 1 + 2 * int(P);
+        Real e = Real(0), o = Real(0);
+        sfor<0, L::Q>([&](auto A) {
+            constexpr int a = A;
+            constexpr double coef = tinv<L>(i, a);
+            if constexpr (coef != 0.0) {
+                if constexpr (mode_parity<L>(a) > 0) e += Real(coef) * w[a];
+                else o += Real(coef) * w[a];
+            }
+        });
+        out[i] = e + o;
+        out[i + 1] = e - o;
+    });
+}
+
+// Single-rate collision of the Landau-pressure / Guo form in moment space with
+// closed-form moments (lattice-general, derived from the equilibrium of the
+// population form):  for a non-conserved mode a,
+//   m^eq_a - T_a(0) rho_c = T_a(0) (drho - 3 p0) + 9/2 rho u.M_a.u,
+//   (T F_i)_a = 9 u.M_a.F,   M_a,bc = sum_i t_i T_ai c_ib c_ic,
+// and f <- (1 - lam) f + T^-1 w with w = (lam drho, lam j + F, lam m^eq + (1 - lam/2) F^ + xi).
+template <class L, class Real, bool TAU1, class LapV>
+__device__ __forceinline__ void collide_guo_bgk(Real (&f)[L::Q], const Real drho, const LapV& lv, const SysDev& S,
+                                                const uint32_t site, const int64_t step, int* status) {
+    constexpr int Q = L::Q;
+    constexpr int K = Q - L::NC;
+    const Real rho = Real(S.rho_c) + drho;
+    if (!(rho > Real(0))) atomicOr(status, ST_RHO);
+    Real j[3] = {Real(0), Real(0), Real(0)};
+    sfor<1, Q>([&](auto I) {
+        constexpr int i = I;
+        sfor<0, L::D>([&](auto A) {
+            constexpr int a = A;
+            if constexpr (L::c(i, a) == 1) j[a] += f[i];
+            if constexpr (L::c(i, a) == -1) j[a] -= f[i];
+        });
+    });
+    const Real irc = Real(S.inv_rho_c);
+    const Real phi = drho * irc;
+    const Real A_ = Real(S.a), B_ = Real(S.b), kap = Real(S.kappa);
+    const Real df0 = phi * (A_ + B_ * phi * phi);
+    const Real f0 = phi * phi * (Real(0.5) * A_ + Real(0.25) * B_ * phi * phi);
+    const Real p0 = rho * irc * df0 - f0;
+    const Real cs2 = rho * irc * irc * (A_ + Real(3) * B_ * phi * phi);
+    // Guo body force F = kappa rho grad(lap rho)
+    Real gl[3] = {Real(0), Real(0), Real(0)};
+    sfor<1, Q>([&](auto I) {
+        constexpr int i = I;
+        const Real ln = lv.template at<L::c(i, 0), L::c(i, 1), L::c(i, 2)>();
+        sfor<0, L::D>([&](auto A) {
+            constexpr int a = A;
+            if constexpr (L::c(i, a) != 0) gl[a] += Real(3.0 * L::w(i) * L::c(i, a)) * ln;
+        });
+    });
+    const Real ir = Real(1) / rho;
+    Real u[3] = {Real(0), Real(0), Real(0)}, F[3] = {Real(0), Real(0), Real(0)};
+    sfor<0, L::D>([&](auto A) {
+        constexpr int a = A;
+        F[a] = kap * rho * gl[a];
+        u[a] = (j[a] + Real(0.5) * F[a]) * ir;
+    });
+    Real xi[K];
+    sfor<0, K>([&](auto A) { xi[decltype(A)::value] = Real(0); });
+    if (S.kT > 0.0) noise_modes<L, Real>(S, site, step, rho, cs2, xi, status);
+
+    const Real lam = TAU1 ? Real(1) : Real(S.lam_bgk);
+    const Real fs = Real(1) - Real(0.5) * lam;
+    const Real iso = drho - Real(3) * p0;
+    const Real r45 = Real(4.5) * rho;
+    Real w[Q];
+    w[0] = lam * drho;
+    sfor<0, L::D>([&](auto A) {
+        constexpr int a = A;
+        w[1 + a] = lam * j[a] + F[a];
+    });
+    sfor<L::NC, Q>([&](auto A) {
+        constexpr int a = A;
+        Real uMu = Real(0), uMF = Real(0);
+        sfor<0, L::D>([&](auto B) {
+            constexpr int b = B;
+            sfor<0, L::D>([&](auto C) {
+                constexpr int c = C;
+                constexpr double m = mproj<L>(a, b, c);
+                if constexpr (m != 0.0) {
+                    uMu += Real(m) * u[b] * u[c];
+                    uMF += Real(m) * u[b] * F[c];
+                }
+            });
+        });
+        Real meq = r45 * uMu;
+        if constexpr (L::T(a, 0) != 0) meq += Real(L::T(a, 0)) * iso;
+        w[a] = lam * meq + fs * Real(9) * uMF + xi[a - L::NC];
+    });
+    if constexpr (TAU1) {
+        from_moments<L, Real>(w, f);          // the pre-collision f is fully relaxed away
+    } else {
+        Real out[Q];
+        from_moments<L, Real>(w, out);
+        const Real keep = Real(1) - lam;
+        sfor<0, Q>([&](auto I) {
+            constexpr int i = I;
+            f[i] = keep * f[i] + out[i];
+        });
+    }
 }
 
 // Collision of one site given its pulled deviations f[], the density halo and
@@ -368,9 +489,11 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
     }
 }
 
-template <class L, int CP, class Real, int TX, int TY, int TZ, bool BGK_ONLY>
+template <class L, int CP, class Real, int TX, int TY, int TZ, int MODE>
 __global__ void __launch_bounds__(TX* TY* TZ)
     step_kernel(const StepArgs<Real> A) {
+    constexpr bool BGK_ONLY = MODE >= 1;
+    constexpr bool TAU1 = MODE == 2;
     constexpr int Q = L::Q;
     constexpr int H = HaloOf<L, CP>::H;
     constexpr int HZ = HaloOf<L, CP>::HZ;
@@ -383,7 +506,7 @@ __global__ void __launch_bounds__(TX* TY* TZ)
     const int4 tl = A.tiles[blockIdx.x];
     const SysDev& S = A.sys[tl.x];
     const int nx = S.nx, ny = S.ny, nz = S.nz;
-    const int64_t N = S.n_sites;
+    const int N = S.ns;
     const Real* __restrict__ fb = A.fin + S.pop_offset;
 
     const int tid = threadIdx.x;
@@ -413,7 +536,9 @@ __global__ void __launch_bounds__(TX* TY* TZ)
         if (interior && gx < nx && gy < ny && gz < nz) continue;
         Real v = Real(0);
         if (gx < nx + H && gy < ny + H && gz < nz + HZ) {
-            const Nbr nb(wrapm(gx, nx), wrapm(gy, ny), L::D == 3 ? wrapm(gz, nz) : 0, nx, ny, nz, L::D == 3);
+            const bool sm = S.small != 0;
+            const Nbr nb(sm ? wrapm(gx, nx) : wrap2(gx, nx), sm ? wrapm(gy, ny) : wrap2(gy, ny),
+                         L::D == 3 ? (sm ? wrapm(gz, nz) : wrap2(gz, nz)) : 0, nx, ny, nz, L::D == 3);
             Real g[Q];
             pull_site<L, Real>(fb, N, nb, g);
             sfor<0, Q>([&](auto I) { v += g[decltype(I)::value]; });
@@ -446,12 +571,15 @@ __global__ void __launch_bounds__(TX* TY* TZ)
     const int64_t step = *A.step_ptr + A.k;
     const TileView<Real, SX, SY> rv{srho, cidx};
     const TileView<Real, LX, LY> lv{slap, lidx};
-    collide_site<L, CP, Real, BGK_ONLY>(f, drho, rv, lv, S, uint32_t(site), step, A.status);
+    if constexpr (CP == GUO && BGK_ONLY)
+        collide_guo_bgk<L, Real, TAU1>(f, drho, lv, S, uint32_t(site), step, A.status);
+    else
+        collide_site<L, CP, Real, BGK_ONLY>(f, drho, rv, lv, S, uint32_t(site), step, A.status);
 
     Real* __restrict__ fo = A.fout + S.pop_offset;
     sfor<0, Q>([&](auto I) {
         constexpr int i = I;
-        fo[int64_t(i) * N + site] = f[i];
+        fo[i * N + site] = f[i];
     });
 }
 
@@ -465,10 +593,12 @@ namespace lbf {
 // 2H+1 planes in shared memory, the Laplacian (Guo force) into a ring of 3
 // planes, so every footprint value is formed once per chunk instead of once
 // per tile, and the collision of plane z follows two planes behind.
-template <class L, int CP, class Real, int TX, int TY, int ZC, bool BGK_ONLY>
+template <class L, int CP, class Real, int TX, int TY, int ZC, int MODE>
 __global__ void __launch_bounds__(TX* TY)
     step_kernel_z(const StepArgs<Real> A) {
     static_assert(L::D == 3, "z-marching is for 3-D lattices");
+    constexpr bool BGK_ONLY = MODE >= 1;
+    constexpr bool TAU1 = MODE == 2;
     constexpr int Q = L::Q;
     constexpr int H = HaloOf<L, CP>::H;
     constexpr int SX = TX + 2 * H, SY = TY + 2 * H, SP = SX * SY;     // rho footprint plane
@@ -482,7 +612,7 @@ __global__ void __launch_bounds__(TX* TY)
     const int4 tl = A.tiles[blockIdx.x];
     const SysDev& S = A.sys[tl.x];
     const int nx = S.nx, ny = S.ny, nz = S.nz;
-    const int64_t N = S.n_sites;
+    const int N = S.ns;
     const Real* __restrict__ fb = A.fin + S.pop_offset;
     Real* __restrict__ fo = A.fout + S.pop_offset;
     const int z0 = tl.w, z1 = min(z0 + ZC, nz);
@@ -496,13 +626,15 @@ __global__ void __launch_bounds__(TX* TY)
     // planes of rho needed: z0 - H .. z1 - 1 + H; collision of plane zc trails rho by H
     for (int zz = z0 - H; zz < z1 + H; ++zz) {
         const int slot = (zz - z0 + 2 * NR) % NR;
-        const int wz = wrapm(zz, nz);
+        const bool sm = S.small != 0;
+        const int wz = sm ? wrapm(zz, nz) : wrap2(zz, nz);
         for (int idx = tid; idx < SP; idx += NT) {
             const int px = idx % SX, py = idx / SX;
             const int gx = tl.y + px - H, gy = tl.z + py - H;
             Real v = Real(0);
             if (gx < nx + H && gy < ny + H) {
-                const Nbr nb(wrapm(gx, nx), wrapm(gy, ny), wz, nx, ny, nz, true);
+                const Nbr nb(sm ? wrapm(gx, nx) : wrap2(gx, nx), sm ? wrapm(gy, ny) : wrap2(gy, ny), wz, nx, ny, nz,
+                             true);
                 Real g[Q];
                 pull_site<L, Real>(fb, N, nb, g);
                 sfor<0, Q>([&](auto I) { v += g[decltype(I)::value]; });
@@ -550,15 +682,19 @@ __global__ void __launch_bounds__(TX* TY)
                                         ((zc + 1 - z0 + 2 * NR) % NR) * SP, (ty + H) * SX + (tx + H)};
             const RingView<Real, LX> lv{slap, ((zc - 1 - z0 + 6) % 3) * LP, ((zc - z0 + 6) % 3) * LP,
                                         ((zc + 1 - z0 + 6) % 3) * LP, (ty + 1) * LX + (tx + 1)};
-            collide_site<L, CP, Real, BGK_ONLY>(f, drho, rv, lv, S, uint32_t(site), step, A.status);
+            if constexpr (CP == GUO && BGK_ONLY)
+                collide_guo_bgk<L, Real, TAU1>(f, drho, lv, S, uint32_t(site), step, A.status);
+            else
+                collide_site<L, CP, Real, BGK_ONLY>(f, drho, rv, lv, S, uint32_t(site), step, A.status);
             sfor<0, Q>([&](auto I) {
                 constexpr int i = I;
-                fo[int64_t(i) * N + site] = f[i];
+                fo[i * N + site] = f[i];
             });
         }
-        // the next iteration overwrites a rho slot and (Guo) a Laplacian slot that
-        // the collision above may still read
-        __syncthreads();
+        // no barrier needed here: the next writes to the rho ring (slot of plane
+        // zz + 1) and to the Laplacian ring (plane zz) come after the next
+        // iteration's first barrier, and the collision above reads neither
+        // (it reads rho planes zz - 3 .. zz - 1 and Laplacian planes zz - 3 .. zz - 1)
     }
 }
 

@@ -302,3 +302,22 @@ def test_structure_factor_matches_oracle(lb, lattice, n, obs_every):
     assert np.array_equal(counts, want_c)
     assert np.allclose(sums, want_s, rtol=1e-10, atol=1e-14 * want_s.max())
     ens.close()
+
+
+@pytest.mark.parametrize("lattice,coupling,shape", [("D2Q9", "modeq", (33, 18, 1)), ("D2Q9", "guo", (21, 30, 1)),
+                                                     ("D3Q19", "guo", (18, 11, 35))])
+@pytest.mark.parametrize("tau", [0.8, 1.0])
+def test_single_rate_collision_paths(lb, lattice, coupling, shape, tau):
+    """One relaxation rate for every non-conserved mode (the paper's BGK form):
+    the population-space (tau != 1) and fully relaxed (tau = 1) code paths."""
+    q = 9 if lattice == "D2Q9" else 19
+    s = _sys(lattice, coupling, *shape, a=-0.001, b=0.1, kappa=0.01, kT=1e-4, tau=[tau] * q, seed=3)
+    p = params_of(s)
+    f0 = oracle_state(p)
+    for prec, tol, n in (("fp64", TOL64, 7), ("fp32", TOL32, 1)):
+        ens = lb.Ensemble([s], precision=prec)
+        ens.write_fields(0, f0)
+        start = ens.read_fields(0)
+        ens.step(n)
+        assert rel_err(ens.read_fields(0), lbm.run(start, 0, n, p)) < tol, prec
+        ens.close()
