@@ -361,6 +361,10 @@ SysDev to_dev(const SysHost& h) {
     }
     const int P = d.lattice == LB_D2Q9 ? 3 : 4, R = d.lattice == LB_D2Q9 ? 8 : 16;
     s.g_pair = 1.0 - gamma[P] * gamma[R];
+    for (int a = 0; a < q; ++a) {
+        const double Na = d.lattice == LB_D2Q9 ? norm2<D2Q9>(a) : norm2<D3Q19>(a);
+        s.namp[a] = std::sqrt(Na * s.g_diag[a]);
+    }
     s.bgk = 1;
     for (int a = nc; a < q; ++a)
         if (s.lam[a] != s.lam[nc]) s.bgk = 0;

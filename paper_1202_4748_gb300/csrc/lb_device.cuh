@@ -172,6 +172,7 @@ struct SysDev {
     double lam[LB_MAX_Q_DEV];
     double g_diag[LB_MAX_Q_DEV];   // 1 - gamma_a^2
     double g_pair;                 // 1 - gamma_P gamma_R
+    double namp[LB_MAX_Q_DEV];     // sqrt(N_a (1 - gamma_a^2)): amplitude of an uncoupled mode
     uint32_t seed_lo, seed_hi;
     uint32_t system_id;
     int32_t bgk;                   // 1: every non-conserved mode relaxes at the same rate lam_bgk

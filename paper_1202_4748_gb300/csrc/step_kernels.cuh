@@ -131,10 +131,7 @@ __device__ __forceinline__ void noise_modes(const SysDev& S, uint32_t site, int6
     }
     sfor<L::NC, Q>([&](auto A) {
         constexpr int a = A;
-        if constexpr (a != P && a != R) {
-            constexpr double Na = norm2<L>(a);
-            xi[a - L::NC] = sc * sqrt(Real(Na) * Real(S.g_diag[a])) * nrm[a - L::NC];
-        }
+        if constexpr (a != P && a != R) xi[a - L::NC] = sc * Real(S.namp[a]) * nrm[a - L::NC];
     });
 }
 
@@ -641,20 +638,20 @@ __global__ void __launch_bounds__(TX* TY)
     for (int zz = z0 - H; zz < z1 + H; ++zz) {
         const int slot = (zz - z0 + 2 * NR) % NR;
         const int wz = sm ? wrapm(zz, nz) : wrap2(zz, nz);
-        // own column site: pull, keep the populations, density into the footprint
-        {
+        // own column site: pull, keep the populations, density into the footprint.
+        // Only a valid site writes its slot; slots of columns beyond a short side
+        // hold periodic images and are filled by the halo loop below.
+        if (valid_xy) {
             Real v = Real(0);
-            if (valid_xy) {
-                const Nbr nb(x, y, wz, nx, ny, nz, true);
-                Real g[Q];
-                pull_site<L, Real>(fb, N, nb, g);
-                Real* dst = sown + ((zz - z0 + 3 * NF) % NF) * Q * NT + tid;
-                sfor<0, Q>([&](auto I) {
-                    constexpr int i = I;
-                    v += g[i];
-                    dst[i * NT] = g[i];
-                });
-            }
+            const Nbr nb(x, y, wz, nx, ny, nz, true);
+            Real g[Q];
+            pull_site<L, Real>(fb, N, nb, g);
+            Real* dst = sown + ((zz - z0 + 3 * NF) % NF) * Q * NT + tid;
+            sfor<0, Q>([&](auto I) {
+                constexpr int i = I;
+                v += g[i];
+                dst[i * NT] = g[i];
+            });
             srho[slot * SP + own] = v;
         }
         // halo ring (and column slots beyond a short side): density only
