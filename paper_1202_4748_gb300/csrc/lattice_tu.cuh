@@ -32,15 +32,7 @@ cudaError_t step_z_mode(const StepLaunch& a, cudaStream_t st) {
     A.step_ptr = a.step_ptr;
     A.k = a.k;
     A.status = a.status;
-    constexpr size_t smem = ZLayout<L, CP, Real, TX, TY, ZC>::bytes;
-    auto kern = step_kernel_z<L, CP, Real, TX, TY, ZC, MODE>;
-    static bool configured = false;     // one attribute call per instantiation (host side)
-    if (!configured) {
-        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    kern<<<a.n_tiles, TX * TY, smem, st>>>(A);
+    step_kernel_z<L, CP, Real, TX, TY, ZC, MODE><<<a.n_tiles, TX * TY, 0, st>>>(A);
     return cudaGetLastError();
 }
 

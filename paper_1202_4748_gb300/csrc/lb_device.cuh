@@ -230,6 +230,14 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, 
     n1 = -r * s;
 }
 
+// Reciprocal and reciprocal square root: exact-rounding library calls in
+// double, the special-function unit in float (the FP32 path's error budget is
+// ~1e-5 of the populations; these are good to a few ulp).
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
+
 // Periodic wrap of a coordinate in [-n, 2n).
 __device__ __forceinline__ int wrap2(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 // Periodic wrap of a coordinate that is at most one period outside [0, n).

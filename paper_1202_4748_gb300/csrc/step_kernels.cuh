@@ -118,9 +118,10 @@ __device__ __forceinline__ void noise_modes(const SysDev& S, uint32_t site, int6
     const Real Mpr = om * Real(vP * vR) * Real(S.g_pair);
     const Real det = Mpp * Mrr - Mpr * Mpr;
     if (Mpp > Real(0) && det > Real(0)) {
-        const Real l11 = sqrt(Mpp);
-        const Real l21 = Mpr / l11;
-        const Real l22 = sqrt(det / Mpp);
+        const Real r = fast_rsqrt(Mpp);
+        const Real l11 = Mpp * r;
+        const Real l21 = Mpr * r;
+        const Real l22 = sqrt(det) * r;
         const Real nP = nrm[P - L::NC], nR = nrm[R - L::NC];
         xi[P - L::NC] = sc * l11 * nP;
         xi[R - L::NC] = sc * (l21 * nP + l22 * nR);
@@ -204,7 +205,7 @@ __device__ __forceinline__ void collide_guo_bgk(Real (&f)[L::Q], const Real drho
             if constexpr (L::c(i, a) != 0) gl[a] += Real(3.0 * L::w(i) * L::c(i, a)) * ln;
         });
     });
-    const Real ir = Real(1) / rho;
+    const Real ir = fast_rcp(rho);
     Real u[3] = {Real(0), Real(0), Real(0)}, F[3] = {Real(0), Real(0), Real(0)};
     sfor<0, L::D>([&](auto A) {
         constexpr int a = A;
@@ -585,22 +586,16 @@ __global__ void __launch_bounds__(TX* TY* TZ)
 namespace lbf {
 
 // z-marching variant for 3-D lattices.  A CTA owns a TX x TY column of sites
-// and walks a chunk of ZC planes.  For each plane zz it pulls the populations
-// of its own column (one site per thread, kept in a private shared-memory ring
-// three planes deep) and of the halo ring around it, forms the density
-// deviation once per footprint site into a ring of 2H+1 planes, the Laplacian
-// (Guo force) into a ring of 3 planes, and collides plane zz - H, whose
-// populations it reads back from its private ring.
+// and walks a chunk of ZC planes.  (Keeping each thread's own populations in
+// shared memory instead of re-reading them was measured slower: the carve-out
+// takes the L1 space that serves the overlapping footprint pulls.)  The density deviation of each plane is
+// computed once on the column's footprint (halo H in x and y) into a ring of
+// 2H+1 planes in shared memory, the Laplacian (Guo force) into a ring of 3
+// planes, so every footprint value is formed once per chunk instead of once
+// per tile, and the collision of plane z follows two planes behind.
 template <class L, int CP, class Real, int TX, int TY, int ZC>
 struct ZLayout {
-    static constexpr int H = HaloOf<L, CP>::H;
-    static constexpr int SX = TX + 2 * H, SY = TY + 2 * H, SP = SX * SY;   // rho footprint plane
-    static constexpr int NR = 2 * H + 1;                                   // rho ring planes
-    static constexpr int LX = TX + 2, LY = TY + 2, LP = LX * LY;           // Laplacian plane
-    static constexpr int NL = CP == GUO ? 3 : 1;
-    static constexpr int NT = TX * TY;
-    static constexpr int NF = H + 1;                                       // own-population ring planes
-    static constexpr size_t bytes = sizeof(Real) * (size_t(NR) * SP + size_t(NL) * LP + size_t(NF) * L::Q * NT);
+    static constexpr size_t bytes = 0;     // static shared memory only
 };
 
 template <class L, int CP, class Real, int TX, int TY, int ZC, int MODE>
@@ -609,15 +604,15 @@ __global__ void __launch_bounds__(TX* TY)
     static_assert(L::D == 3, "z-marching is for 3-D lattices");
     constexpr bool BGK_ONLY = MODE >= 1;
     constexpr bool TAU1 = MODE == 2;
-    using Z = ZLayout<L, CP, Real, TX, TY, ZC>;
     constexpr int Q = L::Q;
-    constexpr int H = Z::H, SX = Z::SX, SY = Z::SY, SP = Z::SP, NR = Z::NR;
-    constexpr int LX = Z::LX, LP = Z::LP, NT = Z::NT, NF = Z::NF;
-    (void)SY;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real* srho = reinterpret_cast<Real*>(smem_raw);
-    Real* slap = srho + NR * SP;
-    Real* sown = slap + Z::NL * LP;           // [plane slot][i][thread]
+    constexpr int H = HaloOf<L, CP>::H;
+    constexpr int SX = TX + 2 * H, SY = TY + 2 * H, SP = SX * SY;     // rho footprint plane
+    constexpr int NR = 2 * H + 1;                                     // rho ring planes
+    constexpr int LX = TX + 2, LY = TY + 2, LP = LX * LY;             // Laplacian plane (Guo)
+    constexpr int NL = CP == GUO ? 3 : 1;
+    constexpr int NT = TX * TY;
+    __shared__ Real srho[NR * SP];
+    __shared__ Real slap[NL * LP];
 
     const int4 tl = A.tiles[blockIdx.x];
     const SysDev& S = A.sys[tl.x];
@@ -627,39 +622,20 @@ __global__ void __launch_bounds__(TX* TY)
     Real* __restrict__ fo = A.fout + S.pop_offset;
     const int z0 = tl.w, z1 = min(z0 + ZC, nz);
     const int64_t step = *A.step_ptr + A.k;
-    const bool sm = S.small != 0;
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const int x = tl.y + tx, y = tl.z + ty;
     const bool valid_xy = x < nx && y < ny;
-    const int own = (ty + H) * SX + (tx + H);          // this thread's slot in a footprint plane
 
+    // planes of rho needed: z0 - H .. z1 - 1 + H; collision of plane zc trails rho by H
     for (int zz = z0 - H; zz < z1 + H; ++zz) {
         const int slot = (zz - z0 + 2 * NR) % NR;
+        const bool sm = S.small != 0;
         const int wz = sm ? wrapm(zz, nz) : wrap2(zz, nz);
-        // own column site: pull, keep the populations, density into the footprint.
-        // Only a valid site writes its slot; slots of columns beyond a short side
-        // hold periodic images and are filled by the halo loop below.
-        if (valid_xy) {
-            Real v = Real(0);
-            const Nbr nb(x, y, wz, nx, ny, nz, true);
-            Real g[Q];
-            pull_site<L, Real>(fb, N, nb, g);
-            Real* dst = sown + ((zz - z0 + 3 * NF) % NF) * Q * NT + tid;
-            sfor<0, Q>([&](auto I) {
-                constexpr int i = I;
-                v += g[i];
-                dst[i * NT] = g[i];
-            });
-            srho[slot * SP + own] = v;
-        }
-        // halo ring (and column slots beyond a short side): density only
         for (int idx = tid; idx < SP; idx += NT) {
             const int px = idx % SX, py = idx / SX;
             const int gx = tl.y + px - H, gy = tl.z + py - H;
-            const bool interior = px >= H && px < H + TX && py >= H && py < H + TY;
-            if (interior && gx < nx && gy < ny) continue;
             Real v = Real(0);
             if (gx < nx + H && gy < ny + H) {
                 const Nbr nb(sm ? wrapm(gx, nx) : wrap2(gx, nx), sm ? wrapm(gy, ny) : wrap2(gy, ny), wz, nx, ny, nz,
@@ -696,20 +672,19 @@ __global__ void __launch_bounds__(TX* TY)
             }
             __syncthreads();
         }
-        // collision of plane zc = zz - H from this thread's own ring
+        // collision of plane zc = zz - H
         const int zc = zz - H;
         if (zc >= z0 && valid_xy) {
+            const Nbr nb(x, y, zc, nx, ny, nz, true);
             Real f[Q];
-            const Real* srcf = sown + ((zc - z0 + 3 * NF) % NF) * Q * NT + tid;
+            pull_site<L, Real>(fb, N, nb, f);
             Real drho = Real(0);
-            sfor<0, Q>([&](auto I) {
-                constexpr int i = I;
-                f[i] = srcf[i * NT];
-                drho += f[i];
-            });
+            sfor<0, Q>([&](auto I) { drho += f[decltype(I)::value]; });
             const int site = site_index(x, y, zc, nx, ny);
+            // the collision reads rho (MODEQ) or the Laplacian (GUO) around the site;
+            // GUO needs only lap planes zc-1..zc+1, addressed through a 3-plane view
             const RingView<Real, SX> rv{srho, ((zc - 1 - z0 + 2 * NR) % NR) * SP, ((zc - z0 + 2 * NR) % NR) * SP,
-                                        ((zc + 1 - z0 + 2 * NR) % NR) * SP, own};
+                                        ((zc + 1 - z0 + 2 * NR) % NR) * SP, (ty + H) * SX + (tx + H)};
             const RingView<Real, LX> lv{slap, ((zc - 1 - z0 + 6) % 3) * LP, ((zc - z0 + 6) % 3) * LP,
                                         ((zc + 1 - z0 + 6) % 3) * LP, (ty + 1) * LX + (tx + 1)};
             if constexpr (CP == GUO && BGK_ONLY)
@@ -721,10 +696,10 @@ __global__ void __launch_bounds__(TX* TY)
                 fo[i * N + site] = f[i];
             });
         }
-        // no barrier here: the next iteration's ring writes (rho slot of plane
-        // zz + 1, Laplacian slot of plane zz) follow its first barrier, and the
-        // own-population slot it writes (plane zz + 1) is private to each thread
-        // and differs from the one just read (plane zz - H)
+        // no barrier needed here: the next writes to the rho ring (slot of plane
+        // zz + 1) and to the Laplacian ring (plane zz) come after the next
+        // iteration's first barrier, and the collision above reads neither
+        // (it reads rho planes zz - 3 .. zz - 1 and Laplacian planes zz - 3 .. zz - 1)
     }
 }
 

@@ -321,3 +321,24 @@ def test_single_rate_collision_paths(lb, lattice, coupling, shape, tau):
         ens.step(n)
         assert rel_err(ens.read_fields(0), lbm.run(start, 0, n, p)) < tol, prec
         ens.close()
+
+
+def test_autotuner_times_every_tile_and_caches(lb, tmp_path):
+    from paper_1202_4748_gb300 import autotune
+    systems = synth.ensemble("fss_160", "D3Q19")[:8]
+    cache = os.path.join(tmp_path, "tiles.json")
+    best, ms = autotune.tune(systems, "fp32", cache=cache, steps=4, warmup=2)
+    assert set(ms) == set(autotune.TILES["D3Q19"]) and best in ms
+    assert all(v > 0 for v in ms.values())
+    best2, ms2 = autotune.tune(systems, "fp32", cache=cache)
+    assert best2 == best and ms2 == ms
+    # every tile gives the same trajectory (the tile only changes the schedule)
+    runs = []
+    for tile in autotune.TILES["D3Q19"]:
+        e = lb.Ensemble(systems[:3], precision="fp32", tile=tile)
+        e.init()
+        e.step(3)
+        runs.append([e.read_fields(k) for k in range(3)])
+        e.close()
+    for r in runs[1:]:
+        assert all(np.array_equal(a, b) for a, b in zip(runs[0], r))
