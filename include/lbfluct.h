@@ -96,14 +96,18 @@ typedef struct {
  *   graph_chunk if > 0 (even), lb_step replays CUDA graphs of graph_chunk
  *               steps (with the observable launches inside) when the step
  *               counter is a multiple of graph_chunk; 0 = plain launches.
- *   tile        tile shape of the step kernel (0 = library default).       */
+ *   tile        tile shape of the step kernel (0 = library default): (x, y, 1)
+ *               on D2Q9; on D3Q19 (x, y, z-chunk) of the z-marching kernel.
+ *   occupancy   resident CTAs per SM the step kernel was compiled for (its
+ *               register budget); 0 = the tile's default.  Must match a
+ *               compiled variant, else LB_ERR_UNSUPPORTED.                  */
 typedef struct {
     int32_t precision;
     int32_t obs_every;
     int32_t sk_every;
     int32_t graph_chunk;
     int32_t tile[3];
-    int32_t reserved;
+    int32_t occupancy;
 } lb_run_opts;
 
 /* FP64 accumulators of one block level (Eqs. 46-50).  Blocks have dims

@@ -46,7 +46,7 @@ class lb_system_desc(ctypes.Structure):
 class lb_run_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("obs_every", ctypes.c_int32),
                 ("sk_every", ctypes.c_int32), ("graph_chunk", ctypes.c_int32),
-                ("tile", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32)]
+                ("tile", ctypes.c_int32 * 3), ("occupancy", ctypes.c_int32)]
 
 
 class lb_obs_level(ctypes.Structure):
@@ -130,12 +130,13 @@ def make_desc(systems):
     return arr
 
 
-def make_opts(precision="fp64", obs_every=0, sk_every=0, graph_chunk=0, tile=(0, 0, 0)):
+def make_opts(precision="fp64", obs_every=0, sk_every=0, graph_chunk=0, tile=(0, 0, 0), occupancy=0):
     o = lb_run_opts()
     o.precision = {"fp64": LB_FP64, "fp32": LB_FP32_DEVIATION}.get(precision, precision)
     o.obs_every, o.sk_every, o.graph_chunk = int(obs_every), int(sk_every), int(graph_chunk)
     for k in range(3):
         o.tile[k] = int(tile[k])
+    o.occupancy = int(occupancy)
     return o
 
 

@@ -12,11 +12,12 @@ import os
 
 from . import Ensemble, LBError, LB_ERR_UNSUPPORTED
 
-# Compiled tile shapes (must match the tables in csrc/lattice_d2q9.cu and lattice_d3q19.cu):
-# D2Q9 tiles are (x, y, 1); D3Q19 tiles are (x, y, z-chunk) of the z-marching kernel.
+# Compiled variants (must match the tables in csrc/lattice_d2q9.cu and lattice_d3q19.cu):
+# D2Q9 tiles are (x, y, 1); D3Q19 tiles are (x, y, z-chunk) of the z-marching kernel;
+# the last entry is the resident-CTA target of the register budget (0 = default).
 TILES = {
-    "D2Q9": [(32, 8, 1), (64, 4, 1), (128, 2, 1)],
-    "D3Q19": [(16, 16, 32), (32, 8, 32), (16, 16, 16), (16, 8, 32)],
+    "D2Q9": [(32, 8, 1, 0), (64, 4, 1, 0), (128, 2, 1, 0)],
+    "D3Q19": [(16, 16, 32, 4), (16, 16, 32, 3), (32, 8, 32, 4), (16, 16, 16, 4), (16, 8, 32, 6)],
 }
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "lbfluct_tiles.json")
 
@@ -33,7 +34,7 @@ def ensemble_key(systems, precision):
 def time_tile(systems, precision, tile, steps=20, warmup=5):
     """Mean milliseconds per step of the step kernel for one tile shape."""
     import torch
-    ens = Ensemble(systems, precision=precision, tile=tile)
+    ens = Ensemble(systems, precision=precision, tile=tile[:3], occupancy=tile[3])
     try:
         ens.init(amplitude=0.01)
         ens.step(warmup)

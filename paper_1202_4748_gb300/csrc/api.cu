@@ -115,19 +115,23 @@ std::vector<LevelHost> make_levels(const lb_system_desc& d, int& imax, bool& uni
     return out;
 }
 
-int tile_table(int lattice, int (*t)[3]) {
+int tile_table(int lattice, int (*t)[4]) {
     return lattice == LB_D2Q9 ? tile_shapes_d2q9(t, 16) : tile_shapes_d3q19(t, 16);
 }
 
+// The first compiled variant matching the requested shape (and occupancy, if given).
 lb_status choose_tile(int lattice, const lb_run_opts* o, int& tile_id, int tdim[3]) {
-    int t[16][3];
+    int t[16][4];
     const int nt = tile_table(lattice, t);
     tile_id = 0;
-    if (o->tile[0] > 0) {
+    if (o->tile[0] > 0 || o->occupancy > 0) {
         tile_id = -1;
-        for (int k = 0; k < nt; ++k)
-            if (t[k][0] == o->tile[0] && t[k][1] == o->tile[1] && t[k][2] == (o->tile[2] > 0 ? o->tile[2] : 1))
-                tile_id = k;
+        for (int k = 0; k < nt && tile_id < 0; ++k) {
+            const bool shape = o->tile[0] <= 0 || (t[k][0] == o->tile[0] && t[k][1] == o->tile[1] &&
+                                                   t[k][2] == (o->tile[2] > 0 ? o->tile[2] : 1));
+            const bool occ = o->occupancy <= 0 || t[k][3] == o->occupancy;
+            if (shape && occ) tile_id = k;
+        }
         if (tile_id < 0) return LB_ERR_UNSUPPORTED;
     }
     for (int k = 0; k < 3; ++k) tdim[k] = t[tile_id][k];

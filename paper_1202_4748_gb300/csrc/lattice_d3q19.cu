@@ -5,25 +5,26 @@
 namespace lbf {
 
 namespace {
-// (x, y, z-chunk) of the z-marching kernel
-constexpr int kTiles[][3] = {{16, 16, 32}, {32, 8, 32}, {16, 16, 16}, {16, 8, 32}};
+// (x, y, z-chunk, resident CTAs per SM) of the z-marching kernel
+constexpr int kTiles[][4] = {{16, 16, 32, 4}, {16, 16, 32, 3}, {32, 8, 32, 4}, {16, 16, 16, 4}, {16, 8, 32, 6}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
 
 template <int CP, class Real>
 cudaError_t step_tile(const StepLaunch& a, cudaStream_t st) {
     switch (a.tile_id) {
-        case 0: return step_z<D3Q19, CP, Real, 16, 16, 32>(a, st);
-        case 1: return step_z<D3Q19, CP, Real, 32, 8, 32>(a, st);
-        case 2: return step_z<D3Q19, CP, Real, 16, 16, 16>(a, st);
-        case 3: return step_z<D3Q19, CP, Real, 16, 8, 32>(a, st);
+        case 0: return step_z<D3Q19, CP, Real, 16, 16, 32, 4>(a, st);
+        case 1: return step_z<D3Q19, CP, Real, 16, 16, 32, 3>(a, st);
+        case 2: return step_z<D3Q19, CP, Real, 32, 8, 32, 4>(a, st);
+        case 3: return step_z<D3Q19, CP, Real, 16, 16, 16, 4>(a, st);
+        case 4: return step_z<D3Q19, CP, Real, 16, 8, 32, 6>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }
 }  // namespace
 
-int tile_shapes_d3q19(int (*out)[3], int max) {
+int tile_shapes_d3q19(int (*out)[4], int max) {
     for (int t = 0; t < kNumTiles && t < max; ++t)
-        for (int k = 0; k < 3; ++k) out[t][k] = kTiles[t][k];
+        for (int k = 0; k < 4; ++k) out[t][k] = kTiles[t][k];
     return kNumTiles;
 }
 

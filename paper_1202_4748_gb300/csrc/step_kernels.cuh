@@ -598,8 +598,8 @@ struct ZLayout {
     static constexpr size_t bytes = 0;     // static shared memory only
 };
 
-template <class L, int CP, class Real, int TX, int TY, int ZC, int MODE>
-__global__ void __launch_bounds__(TX* TY)
+template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB, int MODE>
+__global__ void __launch_bounds__(TX* TY, MINB)
     step_kernel_z(const StepArgs<Real> A) {
     static_assert(L::D == 3, "z-marching is for 3-D lattices");
     constexpr bool BGK_ONLY = MODE >= 1;

@@ -335,7 +335,7 @@ def test_autotuner_times_every_tile_and_caches(lb, tmp_path):
     # every tile gives the same trajectory (the tile only changes the schedule)
     runs = []
     for tile in autotune.TILES["D3Q19"]:
-        e = lb.Ensemble(systems[:3], precision="fp32", tile=tile)
+        e = lb.Ensemble(systems[:3], precision="fp32", tile=tile[:3], occupancy=tile[3])
         e.init()
         e.step(3)
         runs.append([e.read_fields(k) for k in range(3)])
