@@ -17,7 +17,7 @@ from . import Ensemble, LBError, LB_ERR_UNSUPPORTED
 # the last entry is the resident-CTA target of the register budget (0 = default).
 TILES = {
     "D2Q9": [(32, 8, 1, 0), (64, 4, 1, 0), (128, 2, 1, 0)],
-    "D3Q19": [(16, 16, 32, 4), (16, 16, 32, 3), (32, 8, 32, 4), (16, 16, 16, 4), (16, 8, 32, 6)],
+    "D3Q19": [(16, 16, 16, 4), (16, 16, 32, 4), (16, 16, 8, 4), (32, 16, 16, 2), (16, 8, 16, 6), (32, 8, 16, 4)],
 }
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "lbfluct_tiles.json")
 
