@@ -31,6 +31,7 @@ LB_FP64, LB_FP32_DEVIATION = 0, 1
 LB_INIT_UNIFORM_NOISE, LB_INIT_FROM_RHO = 0, 1
 LB_MAX_Q = 19
 LB_MAX_LEVELS = 32
+LB_NOALLOC_MAX_SITES = 1 << 18
 Q_OF = {LB_D2Q9: 9, LB_D3Q19: 19}
 
 
@@ -82,6 +83,8 @@ _SIG = {
     "lb_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "lb_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "lb_kernel_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "lb_block_moments_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
+                                                ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P]),
     "lb_destroy": (None, [_P]),
     "lb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lb_version": (ctypes.c_char_p, []),
