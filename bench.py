@@ -39,7 +39,7 @@ WORKLOADS = {
     "fss_160_fp64": dict(ensemble="fss_160", lattice="D3Q19", precision="fp64"),
 }
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
 KERNEL_SOURCES = ["paper_1202_4748_gb300/csrc/step_kernels.cuh", "paper_1202_4748_gb300/csrc/lb_device.cuh"]
 
 
@@ -179,15 +179,21 @@ def load_peak():
         return 6800.0, "fallback"
 
 
-def load_traffic():
+def load_traffic(workload):
+    """DRAM bytes per step-kernel launch from the committed ncu summary ("key: value"
+    lines), if it was taken on this kernel source and this workload; else None."""
     try:
         with open(TRAFFIC_FILE) as fh:
-            t = json.load(fh)
-    except (OSError, ValueError):
+            t = dict(line.split(":", 1) for line in fh if ":" in line and not line.startswith("#"))
+    except OSError:
         return None
-    if t.get("kernel_source_hash") != kernel_source_hash():
+    t = {k.strip(): v.strip() for k, v in t.items()}
+    if t.get("kernel_source_hash") != kernel_source_hash() or t.get("workload") != workload:
         return None
-    return t
+    try:
+        return float(t["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def main():
@@ -288,7 +294,7 @@ def main():
     bytes_per_launch = sites * q * 2 * es
     achieved = bytes_per_launch / (kern_ms * 1e-3) / 1e9
     peak, peak_kind = load_peak()
-    traffic = load_traffic()
+    traffic = load_traffic(args.workload)
 
     # ---- end to end through the public API from pinned host memory -----------
     import numpy as np
@@ -332,7 +338,7 @@ def main():
             "config": describe(wl, systems),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
-                         "traffic": (traffic["bytes_per_launch_scaled"] if traffic else None),
+                         "traffic": traffic,
                          "kernel": "step_kernel", "kernel_ms": round(kern_ms, 5),
                          "bytes_per_launch": bytes_per_launch,
                          "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
