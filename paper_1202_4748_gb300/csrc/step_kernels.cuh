@@ -704,3 +704,154 @@ __global__ void __launch_bounds__(TX* TY, MINB)
 }
 
 }  // namespace lbf
+
+namespace lbf {
+
+// ---- asynchronous copies global -> shared (cp.async, 4- or 8-byte granules) ----
+__device__ __forceinline__ void cp_async_elem(void* smem_dst, const float* gsrc) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(void* smem_dst, const double* gsrc) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
+
+// z-marching with the footprint of the next plane copied asynchronously.  The
+// pulled populations of plane zz + 1's footprint (all q of them, one element
+// per copy, so wrapped and shifted addresses need no alignment) land in a
+// second shared buffer while plane zz's density is summed and plane zz - H is
+// collided; the collision's arithmetic thus overlaps the footprint's memory
+// traffic.  Shared memory: 2 footprint buffers (2 q SP values) + rings.
+template <class L, int CP, class Real, int TX, int TY, int ZC>
+struct ZALayout {
+    static constexpr int H = HaloOf<L, CP>::H;
+    static constexpr int SX = TX + 2 * H, SY = TY + 2 * H, SP = SX * SY;
+    static constexpr int NR = 2 * H + 1;
+    static constexpr int LX = TX + 2, LY = TY + 2, LP = LX * LY;
+    static constexpr int NL = CP == GUO ? 3 : 1;
+    static constexpr size_t bytes = sizeof(Real) * (size_t(2) * L::Q * SP + size_t(NR) * SP + size_t(NL) * LP);
+};
+
+template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB, int MODE>
+__global__ void __launch_bounds__(TX* TY, MINB)
+    step_kernel_za(const StepArgs<Real> A) {
+    static_assert(L::D == 3, "z-marching is for 3-D lattices");
+    constexpr bool BGK_ONLY = MODE >= 1;
+    constexpr bool TAU1 = MODE == 2;
+    using Z = ZALayout<L, CP, Real, TX, TY, ZC>;
+    constexpr int Q = L::Q;
+    constexpr int H = Z::H, SX = Z::SX, SP = Z::SP, NR = Z::NR, LX = Z::LX, LP = Z::LP;
+    constexpr int NT = TX * TY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real* fbuf = reinterpret_cast<Real*>(smem_raw);       // [2][Q][SP]
+    Real* srho = fbuf + 2 * Q * SP;                        // [NR][SP]
+    Real* slap = srho + NR * SP;                           // [3][LP]
+
+    const int4 tl = A.tiles[blockIdx.x];
+    const SysDev& S = A.sys[tl.x];
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const int N = S.ns;
+    const Real* __restrict__ fb = A.fin + S.pop_offset;
+    Real* __restrict__ fo = A.fout + S.pop_offset;
+    const int z0 = tl.w, z1 = min(z0 + ZC, nz);
+    const int64_t step = *A.step_ptr + A.k;
+    const bool sm = S.small != 0;
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int x = tl.y + tx, y = tl.z + ty;
+    const bool valid_xy = x < nx && y < ny;
+
+    // copy the pulled footprint of plane zz into buffer b (positions beyond the
+    // system, which no valid site reads, are zero-filled)
+    auto issue = [&](int zz, int b) {
+        const int wz = sm ? wrapm(zz, nz) : wrap2(zz, nz);
+        Real* dst = fbuf + b * Q * SP;
+        for (int idx = tid; idx < SP; idx += NT) {
+            const int px = idx % SX, py = idx / SX;
+            const int gx = tl.y + px - H, gy = tl.z + py - H;
+            if (gx < nx + H && gy < ny + H) {
+                const Nbr nb(sm ? wrapm(gx, nx) : wrap2(gx, nx), sm ? wrapm(gy, ny) : wrap2(gy, ny), wz, nx, ny, nz,
+                             true);
+                sfor<0, Q>([&](auto I) {
+                    constexpr int i = I;
+                    cp_async_elem(dst + i * SP + idx, fb + (i * N + nb.template at<-L::c(i, 0), -L::c(i, 1),
+                                                                                   -L::c(i, 2)>()));
+                });
+            } else {
+                sfor<0, Q>([&](auto I) { dst[decltype(I)::value * SP + idx] = Real(0); });
+            }
+        }
+        cp_async_commit();
+    };
+
+    issue(z0 - H, 0);
+    for (int zz = z0 - H; zz < z1 + H; ++zz) {
+        const int b = (zz - z0 + H) & 1;
+        const bool more = zz + 1 < z1 + H;
+        if (more) issue(zz + 1, b ^ 1);          // the buffer was last read before the previous barrier
+        if (more) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncthreads();
+        // density of plane zz on the footprint
+        const int slot = (zz - z0 + 2 * NR) % NR;
+        const Real* src = fbuf + b * Q * SP;
+        for (int idx = tid; idx < SP; idx += NT) {
+            Real v = Real(0);
+            sfor<0, Q>([&](auto I) { v += src[decltype(I)::value * SP + idx]; });
+            srho[slot * SP + idx] = v;
+        }
+        __syncthreads();
+        if constexpr (CP == GUO) {
+            const int zl = zz - 1;
+            if (zl >= z0 - 1) {
+                const int lslot = (zl - z0 + 6) % 3;
+                const int r0 = (zl - z0 + 2 * NR) % NR;
+                const int rm = (zl - 1 - z0 + 2 * NR) % NR;
+                const int rp = (zl + 1 - z0 + 2 * NR) % NR;
+                for (int idx = tid; idx < LP; idx += NT) {
+                    const int px = idx % LX, py = idx / LX;
+                    const int c = (py + H - 1) * SX + (px + H - 1);
+                    const Real rc = srho[r0 * SP + c];
+                    Real lap = Real(0);
+                    sfor<1, Q>([&](auto I) {
+                        constexpr int i = I;
+                        constexpr int cz = L::c(i, 2);
+                        constexpr int off = L::c(i, 0) + SX * L::c(i, 1);
+                        const int pl = cz == 0 ? r0 : (cz > 0 ? rp : rm);
+                        lap += Real(6.0 * L::w(i)) * (srho[pl * SP + c + off] - rc);
+                    });
+                    slap[lslot * LP + idx] = lap;
+                }
+            }
+            __syncthreads();
+        }
+        const int zc = zz - H;
+        if (zc >= z0 && valid_xy) {
+            const Nbr nb(x, y, zc, nx, ny, nz, true);
+            Real f[Q];
+            pull_site<L, Real>(fb, N, nb, f);
+            Real drho = Real(0);
+            sfor<0, Q>([&](auto I) { drho += f[decltype(I)::value]; });
+            const int site = site_index(x, y, zc, nx, ny);
+            const RingView<Real, SX> rv{srho, ((zc - 1 - z0 + 2 * NR) % NR) * SP, ((zc - z0 + 2 * NR) % NR) * SP,
+                                        ((zc + 1 - z0 + 2 * NR) % NR) * SP, (ty + H) * SX + (tx + H)};
+            const RingView<Real, LX> lv{slap, ((zc - 1 - z0 + 6) % 3) * LP, ((zc - z0 + 6) % 3) * LP,
+                                        ((zc + 1 - z0 + 6) % 3) * LP, (ty + 1) * LX + (tx + 1)};
+            if constexpr (CP == GUO && BGK_ONLY)
+                collide_guo_bgk<L, Real, TAU1>(f, drho, lv, S, uint32_t(site), step, A.status);
+            else
+                collide_site<L, CP, Real, BGK_ONLY>(f, drho, rv, lv, S, uint32_t(site), step, A.status);
+            sfor<0, Q>([&](auto I) {
+                constexpr int i = I;
+                fo[i * N + site] = f[i];
+            });
+        }
+    }
+}
+
+}  // namespace lbf
