@@ -38,7 +38,7 @@ struct SysHost {
 
 // Byte offsets of every region inside the workspace.
 struct Plan {
-    size_t sys, tiles, pop0, pop1, step, status, d, dbar, site_items, site_partial, spans, red4, glob, levels,
+    size_t sys, phys, tiles, pop0, pop1, step, status, d, dbar, site_items, site_partial, spans, red4, glob, levels,
         S, E, bottom_items, up_items, rec, acc, field_tmp, sk_sys, sk_tw, sk_acc, sk_b0, sk_b1, sk_bins, total;
     int n_tiles = 0, n_site_items = 0, n_levels = 0, n_bottom = 0, n_up = 0, n_rec = 0, max_depth = 0;
     int64_t n_sites = 0, n_blocks_pyr = 0, max_sites = 0;
@@ -305,6 +305,7 @@ lb_status make_plan(const lb_system_desc* s, int n, const lb_run_opts* o, std::v
         return at;
     };
     P.sys = take(sizeof(SysDev) * n);
+    P.phys = take(sizeof(SysPhys<double>) * n);
     P.tiles = take(sizeof(int4) * P.n_tiles);
     P.pop0 = take(es * q * P.n_sites);
     P.pop1 = take(es * q * P.n_sites);
@@ -334,6 +335,27 @@ lb_status make_plan(const lb_system_desc* s, int n, const lb_run_opts* o, std::v
     P.sk_bins = take(sizeof(double) * 2 * P.sk_max_bins);
     P.total = off;
     return LB_OK;
+}
+
+template <class Real>
+SysPhys<Real> to_phys(const SysDev& s, int q) {
+    SysPhys<Real> p;
+    std::memset(&p, 0, sizeof(p));
+    p.rho_c = Real(s.rho_c);
+    p.inv_rho_c = Real(s.inv_rho_c);
+    p.a = Real(s.a);
+    p.b = Real(s.b);
+    p.kappa = Real(s.kappa);
+    p.kT = Real(s.kT);
+    p.nu = Real(s.nu);
+    p.lam_bgk = Real(s.lam_bgk);
+    p.g_pair = Real(s.g_pair);
+    for (int a = 0; a < q; ++a) {
+        p.lam[a] = Real(s.lam[a]);
+        p.g_diag[a] = Real(s.g_diag[a]);
+        p.namp[a] = Real(s.namp[a]);
+    }
+    return p;
 }
 
 SysDev to_dev(const SysHost& h) {
@@ -487,6 +509,7 @@ cudaError_t launch_steps(lb_ctx* c, int64_t n) {
         const int64_t t = c->step + k;
         StepLaunch a;
         a.sys = c->at<SysDev>(P.sys);
+        a.phys = c->ws + P.phys;
         a.tiles = c->at<int4>(P.tiles);
         a.n_tiles = P.n_tiles;
         a.fin = c->pop(int(t & 1));
@@ -615,6 +638,18 @@ lb_status lb_create(const lb_system_desc* systems, int n_systems, const lb_run_o
     }
     bool ok = cudaMemcpyAsync(c->ws + P.sys, sd.data(), sizeof(SysDev) * sd.size(), cudaMemcpyHostToDevice,
                               c->stream) == cudaSuccess;
+    // physics in the step kernel's precision (staged on the host, copied synchronously)
+    if (c->fp32) {
+        std::vector<SysPhys<float>> ph;
+        for (auto& s : sd) ph.push_back(to_phys<float>(s, c->q));
+        ok = ok && cudaMemcpy(c->ws + P.phys, ph.data(), sizeof(SysPhys<float>) * ph.size(),
+                              cudaMemcpyHostToDevice) == cudaSuccess;
+    } else {
+        std::vector<SysPhys<double>> ph;
+        for (auto& s : sd) ph.push_back(to_phys<double>(s, c->q));
+        ok = ok && cudaMemcpy(c->ws + P.phys, ph.data(), sizeof(SysPhys<double>) * ph.size(),
+                              cudaMemcpyHostToDevice) == cudaSuccess;
+    }
     ok = ok && cudaMemcpyAsync(c->ws + P.tiles, P.tiles_h.data(), sizeof(int4) * P.n_tiles, cudaMemcpyHostToDevice,
                                c->stream) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(c->ws + P.site_items, P.site_items_h.data(), sizeof(int4) * P.n_site_items,

@@ -12,6 +12,7 @@ template <class L, int CP, class Real, int TX, int TY, int TZ, int MODE>
 cudaError_t step_one_mode(const StepLaunch& a, cudaStream_t st) {
     StepArgs<Real> A;
     A.sys = a.sys;
+    A.phys = static_cast<const SysPhys<Real>*>(a.phys);
     A.tiles = a.tiles;
     A.fin = static_cast<const Real*>(a.fin);
     A.fout = static_cast<Real*>(a.fout);
@@ -26,6 +27,7 @@ template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB, int MOD
 cudaError_t step_z_mode(const StepLaunch& a, cudaStream_t st) {
     StepArgs<Real> A;
     A.sys = a.sys;
+    A.phys = static_cast<const SysPhys<Real>*>(a.phys);
     A.tiles = a.tiles;
     A.fin = static_cast<const Real*>(a.fin);
     A.fout = static_cast<Real*>(a.fout);

@@ -179,6 +179,17 @@ struct SysDev {
     double lam_bgk;
 };
 
+// Physical parameters of a system in the arithmetic precision of the step
+// kernel (converted once on the host, so the FP32 kernel issues no FP64
+// conversions per site).
+template <class Real>
+struct SysPhys {
+    Real rho_c, inv_rho_c, a, b, kappa, kT, nu, lam_bgk, g_pair, pad;
+    Real lam[LB_MAX_Q_DEV];
+    Real g_diag[LB_MAX_Q_DEV];
+    Real namp[LB_MAX_Q_DEV];
+};
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
 // ---------------------------------------------------------------------------

@@ -14,6 +14,7 @@ constexpr int SITES_PER_THREAD = 4;     // sites per thread in a site-pass item
 
 struct StepLaunch {
     const SysDev* sys;
+    const void* phys;       // SysPhys<float> or SysPhys<double> per system
     const int4* tiles;
     int n_tiles;
     const void* fin;

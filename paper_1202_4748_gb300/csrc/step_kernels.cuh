@@ -23,6 +23,7 @@ namespace lbf {
 template <class Real>
 struct StepArgs {
     const SysDev* sys;
+    const SysPhys<Real>* phys;   // per-system physics in the kernel's precision
     const int4* tiles;        // (system, x0, y0, z0) per CTA
     const Real* fin;
     Real* fout;
@@ -95,8 +96,8 @@ __device__ __forceinline__ void pull_site(const Real* __restrict__ fb, int N, co
 
 // Moment-space noise of Eq. 68 on the non-conserved modes: xi[a - NC].
 template <class L, class Real>
-__device__ __forceinline__ void noise_modes(const SysDev& S, uint32_t site, int64_t step, Real rho, Real cs2,
-                                            Real (&xi)[L::Q - L::NC], int* status) {
+__device__ __forceinline__ void noise_modes(const SysDev& S, const SysPhys<Real>& P, uint32_t site, int64_t step,
+                                            Real rho, Real cs2, Real (&xi)[L::Q - L::NC], int* status) {
     constexpr int Q = L::Q;
     constexpr int K = Q - L::NC;
     constexpr int NDRAW = (K + 3) / 4;
@@ -107,32 +108,32 @@ __device__ __forceinline__ void noise_modes(const SysDev& S, uint32_t site, int6
         box_muller(w.x, w.y, nrm[4 * d + 0], nrm[4 * d + 1]);
         box_muller(w.z, w.w, nrm[4 * d + 2], nrm[4 * d + 3]);
     });
-    const Real sc = sqrt(Real(3) * (rho > Real(0) ? rho : Real(0)) * Real(S.kT));
-    // the coupled pair (P, R): M = [N + (1 - 3 c_s^2) v v^T] g, v_a = T_a(c = 0)
-    constexpr int P = L::PP, R = L::PR;
-    constexpr double vP = double(L::T(P, 0)), vR = double(L::T(R, 0));
-    constexpr double NP = norm2<L>(P), NR = norm2<L>(R);
+    const Real sc = sqrt(Real(3) * (rho > Real(0) ? rho : Real(0)) * P.kT);
+    // the coupled pair (MP, MR): M = [N + (1 - 3 c_s^2) v v^T] g, v_a = T_a(c = 0)
+    constexpr int MP = L::PP, MR = L::PR;
+    constexpr double vP = double(L::T(MP, 0)), vR = double(L::T(MR, 0));
+    constexpr double NP = norm2<L>(MP), NR = norm2<L>(MR);
     const Real om = Real(1) - Real(3) * cs2;
-    const Real Mpp = (Real(NP) + om * Real(vP * vP)) * Real(S.g_diag[P]);
-    const Real Mrr = (Real(NR) + om * Real(vR * vR)) * Real(S.g_diag[R]);
-    const Real Mpr = om * Real(vP * vR) * Real(S.g_pair);
+    const Real Mpp = (Real(NP) + om * Real(vP * vP)) * P.g_diag[MP];
+    const Real Mrr = (Real(NR) + om * Real(vR * vR)) * P.g_diag[MR];
+    const Real Mpr = om * Real(vP * vR) * P.g_pair;
     const Real det = Mpp * Mrr - Mpr * Mpr;
     if (Mpp > Real(0) && det > Real(0)) {
         const Real r = fast_rsqrt(Mpp);
         const Real l11 = Mpp * r;
         const Real l21 = Mpr * r;
         const Real l22 = sqrt(det) * r;
-        const Real nP = nrm[P - L::NC], nR = nrm[R - L::NC];
-        xi[P - L::NC] = sc * l11 * nP;
-        xi[R - L::NC] = sc * (l21 * nP + l22 * nR);
+        const Real nP = nrm[MP - L::NC], nR = nrm[MR - L::NC];
+        xi[MP - L::NC] = sc * l11 * nP;
+        xi[MR - L::NC] = sc * (l21 * nP + l22 * nR);
     } else {
         atomicOr(status, ST_NOISE);
-        xi[P - L::NC] = Real(0);
-        xi[R - L::NC] = Real(0);
+        xi[MP - L::NC] = Real(0);
+        xi[MR - L::NC] = Real(0);
     }
     sfor<L::NC, Q>([&](auto A) {
         constexpr int a = A;
-        if constexpr (a != P && a != R) xi[a - L::NC] = sc * Real(S.namp[a]) * nrm[a - L::NC];
+        if constexpr (a != MP && a != MR) xi[a - L::NC] = sc * P.namp[a] * nrm[a - L::NC];
     });
 }
 
@@ -174,10 +175,11 @@ __device__ __forceinline__ void from_moments(const Real (&w)[L::Q], Real (&out)[
 // and f <- (1 - lam) f + T^-1 w with w = (lam drho, lam j + F, lam m^eq + (1 - lam/2) F^ + xi).
 template <class L, class Real, bool TAU1, class LapV>
 __device__ __forceinline__ void collide_guo_bgk(Real (&f)[L::Q], const Real drho, const LapV& lv, const SysDev& S,
-                                                const uint32_t site, const int64_t step, int* status) {
+                                                const SysPhys<Real>& P, const uint32_t site, const int64_t step,
+                                                int* status) {
     constexpr int Q = L::Q;
     constexpr int K = Q - L::NC;
-    const Real rho = Real(S.rho_c) + drho;
+    const Real rho = P.rho_c + drho;
     if (!(rho > Real(0))) atomicOr(status, ST_RHO);
     Real j[3] = {Real(0), Real(0), Real(0)};
     sfor<1, Q>([&](auto I) {
@@ -188,9 +190,9 @@ __device__ __forceinline__ void collide_guo_bgk(Real (&f)[L::Q], const Real drho
             if constexpr (L::c(i, a) == -1) j[a] -= f[i];
         });
     });
-    const Real irc = Real(S.inv_rho_c);
+    const Real irc = P.inv_rho_c;
     const Real phi = drho * irc;
-    const Real A_ = Real(S.a), B_ = Real(S.b), kap = Real(S.kappa);
+    const Real A_ = P.a, B_ = P.b, kap = P.kappa;
     const Real df0 = phi * (A_ + B_ * phi * phi);
     const Real f0 = phi * phi * (Real(0.5) * A_ + Real(0.25) * B_ * phi * phi);
     const Real p0 = rho * irc * df0 - f0;
@@ -214,9 +216,9 @@ __device__ __forceinline__ void collide_guo_bgk(Real (&f)[L::Q], const Real drho
     });
     Real xi[K];
     sfor<0, K>([&](auto A) { xi[decltype(A)::value] = Real(0); });
-    if (S.kT > 0.0) noise_modes<L, Real>(S, site, step, rho, cs2, xi, status);
+    if (P.kT > Real(0)) noise_modes<L, Real>(S, P, site, step, rho, cs2, xi, status);
 
-    const Real lam = TAU1 ? Real(1) : Real(S.lam_bgk);
+    const Real lam = TAU1 ? Real(1) : P.lam_bgk;
     const Real fs = Real(1) - Real(0.5) * lam;
     const Real iso = drho - Real(3) * p0;
     const Real r45 = Real(4.5) * rho;
@@ -261,11 +263,11 @@ __device__ __forceinline__ void collide_guo_bgk(Real (&f)[L::Q], const Real drho
 // (Guo) the Laplacian halo.  Returns post-collision deviations in f[].
 template <class L, int CP, class Real, bool BGK_ONLY, class RhoV, class LapV>
 __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, const RhoV& rv, const LapV& lv,
-                                             const SysDev& S, const uint32_t site, const int64_t step,
-                                             int* status) {
+                                             const SysDev& S, const SysPhys<Real>& P, const uint32_t site,
+                                             const int64_t step, int* status) {
     constexpr int Q = L::Q;
     constexpr int K = Q - L::NC;
-    const Real rho = Real(S.rho_c) + drho;
+    const Real rho = P.rho_c + drho;
     if (!(rho > Real(0))) atomicOr(status, ST_RHO);
 
     // conserved moments j = sum_i c_i f_i
@@ -280,9 +282,9 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
     });
 
     // thermodynamics (Eqs. 1, 3 and below Eq. 64)
-    const Real irc = Real(S.inv_rho_c);
+    const Real irc = P.inv_rho_c;
     const Real phi = drho * irc;
-    const Real A_ = Real(S.a), B_ = Real(S.b), kap = Real(S.kappa);
+    const Real A_ = P.a, B_ = P.b, kap = P.kappa;
     const Real df0 = phi * (A_ + B_ * phi * phi);
     const Real f0 = phi * phi * (Real(0.5) * A_ + Real(0.25) * B_ * phi * phi);
     const Real p0 = rho * irc * df0 - f0;
@@ -292,7 +294,7 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
     Real fsrc[BGK_ONLY ? 1 : Q];   // Guo population force
     Real F[3] = {Real(0), Real(0), Real(0)};
     // single-rate update f <- f - lam (f - f^eq) + (1 - lam/2) F_i done in the loops below
-    const Real lam_b = Real(S.lam_bgk);
+    const Real lam_b = P.lam_bgk;
     const Real fs_b = Real(1) - Real(0.5) * lam_b;
     if constexpr (CP == MODEQ) {
         // d_a rho = 3 sum_i t_i c_ia rho(r+c_i);  lap rho = 6 sum_i t_i (rho(r+c_i) - rho(r))
@@ -307,7 +309,7 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
         });
         const Real ir = Real(1) / rho;
         const Real ux = j[0] * ir, uy = j[1] * ir;
-        const Real nu = Real(S.nu);
+        const Real nu = P.nu;
         const Real iso = p0 - kap * rho * lap;                     // p0 - kappa rho lap rho
         const Real udg = ux * g[0] + uy * g[1];
         // X_ab = rho u_a u_b + nu (u_a d_b rho + u_b d_a rho + u.grad rho delta_ab)
@@ -394,7 +396,7 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
 
     Real xi[K];
     sfor<0, K>([&](auto A) { xi[decltype(A)::value] = Real(0); });
-    if (S.kT > 0.0) noise_modes<L, Real>(S, site, step, rho, cs2, xi, status);
+    if (P.kT > Real(0)) noise_modes<L, Real>(S, P, site, step, rho, cs2, xi, status);
 
     if constexpr (BGK_ONLY) {
         // f already relaxed and forced; add the noise through f_i += sum_a t_i T_ai xi_a / N_a
@@ -412,7 +414,7 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
     } else {
     if (S.bgk) {
         // single relaxation rate: population-space update plus T^-1 xi
-        const Real lam = Real(S.lam_bgk);
+        const Real lam = P.lam_bgk;
         const Real fs = Real(1) - Real(0.5) * lam;
         sfor<0, Q>([&](auto I) {
             constexpr int i = I;
@@ -452,7 +454,7 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
             else if constexpr (t == -1) me -= feq[i];
             else if constexpr (t != 0) me += Real(t) * feq[i];
         });
-        const Real lam = Real(S.lam[a]);
+        const Real lam = P.lam[a];
         m[a] -= lam * (m[a] - me);
         if constexpr (CP == GUO) {
             Real fh = Real(0);
@@ -570,9 +572,9 @@ __global__ void __launch_bounds__(TX* TY* TZ)
     const TileView<Real, SX, SY> rv{srho, cidx};
     const TileView<Real, LX, LY> lv{slap, lidx};
     if constexpr (CP == GUO && BGK_ONLY)
-        collide_guo_bgk<L, Real, TAU1>(f, drho, lv, S, uint32_t(site), step, A.status);
+        collide_guo_bgk<L, Real, TAU1>(f, drho, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
     else
-        collide_site<L, CP, Real, BGK_ONLY>(f, drho, rv, lv, S, uint32_t(site), step, A.status);
+        collide_site<L, CP, Real, BGK_ONLY>(f, drho, rv, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
 
     Real* __restrict__ fo = A.fout + S.pop_offset;
     sfor<0, Q>([&](auto I) {
@@ -688,9 +690,9 @@ __global__ void __launch_bounds__(TX* TY, MINB)
             const RingView<Real, LX> lv{slap, ((zc - 1 - z0 + 6) % 3) * LP, ((zc - z0 + 6) % 3) * LP,
                                         ((zc + 1 - z0 + 6) % 3) * LP, (ty + 1) * LX + (tx + 1)};
             if constexpr (CP == GUO && BGK_ONLY)
-                collide_guo_bgk<L, Real, TAU1>(f, drho, lv, S, uint32_t(site), step, A.status);
+                collide_guo_bgk<L, Real, TAU1>(f, drho, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
             else
-                collide_site<L, CP, Real, BGK_ONLY>(f, drho, rv, lv, S, uint32_t(site), step, A.status);
+                collide_site<L, CP, Real, BGK_ONLY>(f, drho, rv, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
             sfor<0, Q>([&](auto I) {
                 constexpr int i = I;
                 fo[i * N + site] = f[i];
@@ -700,157 +702,6 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         // zz + 1) and to the Laplacian ring (plane zz) come after the next
         // iteration's first barrier, and the collision above reads neither
         // (it reads rho planes zz - 3 .. zz - 1 and Laplacian planes zz - 3 .. zz - 1)
-    }
-}
-
-}  // namespace lbf
-
-namespace lbf {
-
-// ---- asynchronous copies global -> shared (cp.async, 4- or 8-byte granules) ----
-__device__ __forceinline__ void cp_async_elem(void* smem_dst, const float* gsrc) {
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_elem(void* smem_dst, const double* gsrc) {
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int PENDING>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
-
-// z-marching with the footprint of the next plane copied asynchronously.  The
-// pulled populations of plane zz + 1's footprint (all q of them, one element
-// per copy, so wrapped and shifted addresses need no alignment) land in a
-// second shared buffer while plane zz's density is summed and plane zz - H is
-// collided; the collision's arithmetic thus overlaps the footprint's memory
-// traffic.  Shared memory: 2 footprint buffers (2 q SP values) + rings.
-template <class L, int CP, class Real, int TX, int TY, int ZC>
-struct ZALayout {
-    static constexpr int H = HaloOf<L, CP>::H;
-    static constexpr int SX = TX + 2 * H, SY = TY + 2 * H, SP = SX * SY;
-    static constexpr int NR = 2 * H + 1;
-    static constexpr int LX = TX + 2, LY = TY + 2, LP = LX * LY;
-    static constexpr int NL = CP == GUO ? 3 : 1;
-    static constexpr size_t bytes = sizeof(Real) * (size_t(2) * L::Q * SP + size_t(NR) * SP + size_t(NL) * LP);
-};
-
-template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB, int MODE>
-__global__ void __launch_bounds__(TX* TY, MINB)
-    step_kernel_za(const StepArgs<Real> A) {
-    static_assert(L::D == 3, "z-marching is for 3-D lattices");
-    constexpr bool BGK_ONLY = MODE >= 1;
-    constexpr bool TAU1 = MODE == 2;
-    using Z = ZALayout<L, CP, Real, TX, TY, ZC>;
-    constexpr int Q = L::Q;
-    constexpr int H = Z::H, SX = Z::SX, SP = Z::SP, NR = Z::NR, LX = Z::LX, LP = Z::LP;
-    constexpr int NT = TX * TY;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real* fbuf = reinterpret_cast<Real*>(smem_raw);       // [2][Q][SP]
-    Real* srho = fbuf + 2 * Q * SP;                        // [NR][SP]
-    Real* slap = srho + NR * SP;                           // [3][LP]
-
-    const int4 tl = A.tiles[blockIdx.x];
-    const SysDev& S = A.sys[tl.x];
-    const int nx = S.nx, ny = S.ny, nz = S.nz;
-    const int N = S.ns;
-    const Real* __restrict__ fb = A.fin + S.pop_offset;
-    Real* __restrict__ fo = A.fout + S.pop_offset;
-    const int z0 = tl.w, z1 = min(z0 + ZC, nz);
-    const int64_t step = *A.step_ptr + A.k;
-    const bool sm = S.small != 0;
-
-    const int tid = threadIdx.x;
-    const int tx = tid % TX, ty = tid / TX;
-    const int x = tl.y + tx, y = tl.z + ty;
-    const bool valid_xy = x < nx && y < ny;
-
-    // copy the pulled footprint of plane zz into buffer b (positions beyond the
-    // system, which no valid site reads, are zero-filled)
-    auto issue = [&](int zz, int b) {
-        const int wz = sm ? wrapm(zz, nz) : wrap2(zz, nz);
-        Real* dst = fbuf + b * Q * SP;
-        for (int idx = tid; idx < SP; idx += NT) {
-            const int px = idx % SX, py = idx / SX;
-            const int gx = tl.y + px - H, gy = tl.z + py - H;
-            if (gx < nx + H && gy < ny + H) {
-                const Nbr nb(sm ? wrapm(gx, nx) : wrap2(gx, nx), sm ? wrapm(gy, ny) : wrap2(gy, ny), wz, nx, ny, nz,
-                             true);
-                sfor<0, Q>([&](auto I) {
-                    constexpr int i = I;
-                    cp_async_elem(dst + i * SP + idx, fb + (i * N + nb.template at<-L::c(i, 0), -L::c(i, 1),
-                                                                                   -L::c(i, 2)>()));
-                });
-            } else {
-                sfor<0, Q>([&](auto I) { dst[decltype(I)::value * SP + idx] = Real(0); });
-            }
-        }
-        cp_async_commit();
-    };
-
-    issue(z0 - H, 0);
-    for (int zz = z0 - H; zz < z1 + H; ++zz) {
-        const int b = (zz - z0 + H) & 1;
-        const bool more = zz + 1 < z1 + H;
-        if (more) issue(zz + 1, b ^ 1);          // the buffer was last read before the previous barrier
-        if (more) cp_async_wait<1>();
-        else cp_async_wait<0>();
-        __syncthreads();
-        // density of plane zz on the footprint
-        const int slot = (zz - z0 + 2 * NR) % NR;
-        const Real* src = fbuf + b * Q * SP;
-        for (int idx = tid; idx < SP; idx += NT) {
-            Real v = Real(0);
-            sfor<0, Q>([&](auto I) { v += src[decltype(I)::value * SP + idx]; });
-            srho[slot * SP + idx] = v;
-        }
-        __syncthreads();
-        if constexpr (CP == GUO) {
-            const int zl = zz - 1;
-            if (zl >= z0 - 1) {
-                const int lslot = (zl - z0 + 6) % 3;
-                const int r0 = (zl - z0 + 2 * NR) % NR;
-                const int rm = (zl - 1 - z0 + 2 * NR) % NR;
-                const int rp = (zl + 1 - z0 + 2 * NR) % NR;
-                for (int idx = tid; idx < LP; idx += NT) {
-                    const int px = idx % LX, py = idx / LX;
-                    const int c = (py + H - 1) * SX + (px + H - 1);
-                    const Real rc = srho[r0 * SP + c];
-                    Real lap = Real(0);
-                    sfor<1, Q>([&](auto I) {
-                        constexpr int i = I;
-                        constexpr int cz = L::c(i, 2);
-                        constexpr int off = L::c(i, 0) + SX * L::c(i, 1);
-                        const int pl = cz == 0 ? r0 : (cz > 0 ? rp : rm);
-                        lap += Real(6.0 * L::w(i)) * (srho[pl * SP + c + off] - rc);
-                    });
-                    slap[lslot * LP + idx] = lap;
-                }
-            }
-            __syncthreads();
-        }
-        const int zc = zz - H;
-        if (zc >= z0 && valid_xy) {
-            const Nbr nb(x, y, zc, nx, ny, nz, true);
-            Real f[Q];
-            pull_site<L, Real>(fb, N, nb, f);
-            Real drho = Real(0);
-            sfor<0, Q>([&](auto I) { drho += f[decltype(I)::value]; });
-            const int site = site_index(x, y, zc, nx, ny);
-            const RingView<Real, SX> rv{srho, ((zc - 1 - z0 + 2 * NR) % NR) * SP, ((zc - z0 + 2 * NR) % NR) * SP,
-                                        ((zc + 1 - z0 + 2 * NR) % NR) * SP, (ty + H) * SX + (tx + H)};
-            const RingView<Real, LX> lv{slap, ((zc - 1 - z0 + 6) % 3) * LP, ((zc - z0 + 6) % 3) * LP,
-                                        ((zc + 1 - z0 + 6) % 3) * LP, (ty + 1) * LX + (tx + 1)};
-            if constexpr (CP == GUO && BGK_ONLY)
-                collide_guo_bgk<L, Real, TAU1>(f, drho, lv, S, uint32_t(site), step, A.status);
-            else
-                collide_site<L, CP, Real, BGK_ONLY>(f, drho, rv, lv, S, uint32_t(site), step, A.status);
-            sfor<0, Q>([&](auto I) {
-                constexpr int i = I;
-                fo[i * N + site] = f[i];
-            });
-        }
     }
 }
 
