@@ -100,7 +100,10 @@ typedef struct {
  *               on D2Q9; on D3Q19 (x, y, z-chunk) of the z-marching kernel.
  *   occupancy   resident CTAs per SM the step kernel was compiled for (its
  *               register budget); 0 = the tile's default.  Must match a
- *               compiled variant, else LB_ERR_UNSUPPORTED.                  */
+ *               compiled variant, else LB_ERR_UNSUPPORTED.
+ *   variant     if > 0, selects compiled step-kernel variant number
+ *               variant - 1 of lb_kernel_variants() directly (overrides
+ *               tile and occupancy); 0 = by tile / occupancy / default.      */
 typedef struct {
     int32_t precision;
     int32_t obs_every;
@@ -108,6 +111,7 @@ typedef struct {
     int32_t graph_chunk;
     int32_t tile[3];
     int32_t occupancy;
+    int32_t variant;
 } lb_run_opts;
 
 /* FP64 accumulators of one block level (Eqs. 46-50).  Blocks have dims
@@ -205,6 +209,13 @@ lb_status lb_get_step(lb_ctx* ctx, int64_t* step);
  * is bit-identical to an uninterrupted one.  Errors: LB_ERR_IO, LB_ERR_ARG. */
 lb_status lb_save(lb_ctx* ctx, const char* path);
 lb_status lb_load(lb_ctx* ctx, const char* path);
+
+/* Step-kernel variants compiled for a lattice (LB_D2Q9 or LB_D3Q19): writes up
+ * to max_rows rows of 5 int32 (tile x, tile y, tile z or z-chunk, resident CTAs
+ * per SM of the register budget (0 = default), prefetch flag) into out
+ * (nullable) and returns the number of variants (negative lb_status on error).
+ * Row 0 is the default.  Used by the autotuner; no device call. */
+int lb_kernel_variants(int lattice, int32_t* out, int max_rows);
 
 /* Number of kernels this context has launched so far (graph replays count
  * every kernel node).  Instrumentation for benchmarks; no device call. */

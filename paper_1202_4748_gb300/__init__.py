@@ -47,7 +47,7 @@ class lb_system_desc(ctypes.Structure):
 class lb_run_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("obs_every", ctypes.c_int32),
                 ("sk_every", ctypes.c_int32), ("graph_chunk", ctypes.c_int32),
-                ("tile", ctypes.c_int32 * 3), ("occupancy", ctypes.c_int32)]
+                ("tile", ctypes.c_int32 * 3), ("occupancy", ctypes.c_int32), ("variant", ctypes.c_int32)]
 
 
 class lb_obs_level(ctypes.Structure):
@@ -83,6 +83,7 @@ _SIG = {
     "lb_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "lb_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "lb_kernel_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "lb_kernel_variants": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int]),
     "lb_block_moments_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
                                                 ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P]),
     "lb_destroy": (None, [_P]),
@@ -133,14 +134,26 @@ def make_desc(systems):
     return arr
 
 
-def make_opts(precision="fp64", obs_every=0, sk_every=0, graph_chunk=0, tile=(0, 0, 0), occupancy=0):
+def make_opts(precision="fp64", obs_every=0, sk_every=0, graph_chunk=0, tile=(0, 0, 0), occupancy=0, variant=0):
     o = lb_run_opts()
     o.precision = {"fp64": LB_FP64, "fp32": LB_FP32_DEVIATION}.get(precision, precision)
     o.obs_every, o.sk_every, o.graph_chunk = int(obs_every), int(sk_every), int(graph_chunk)
     for k in range(3):
         o.tile[k] = int(tile[k])
     o.occupancy = int(occupancy)
+    o.variant = int(variant)
     return o
+
+
+def kernel_variants(lattice):
+    """Compiled step-kernel variants of a lattice: list of (x, y, z, occupancy, prefetch)."""
+    code = _LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
+    n = lb_kernel_variants(code, None, 0)
+    if n < 0:
+        raise LBError(n, "lb_kernel_variants")
+    buf = (ctypes.c_int32 * (5 * n))()
+    lb_kernel_variants(code, buf, n)
+    return [tuple(buf[5 * r + k] for k in range(5)) for r in range(n)]
 
 
 def workspace_bytes(systems, **opts):

@@ -1,25 +1,31 @@
-"""Tile-shape autotuner for the fused step kernel.
+"""Step-kernel variant autotuner.
 
-For a given ensemble, every tile shape compiled into the library for its
-lattice is timed on the device (CUDA events around a plain run of step
-launches, after a warm-up) through the public API, and the fastest shape is
+For a given ensemble, every step-kernel variant compiled into the library for
+its lattice (tile shape, register budget, prefetch; listed by
+``lb_kernel_variants``) is timed on the device (CUDA events around a plain run
+of step launches, after a warm-up) through the public API, and the fastest is
 returned.  Results are cached in a JSON file keyed by lattice, coupling,
-precision and the multiset of system sizes, so a later run of the same
-ensemble picks its tile without re-timing.
+precision and the multiset of system sizes, so a later run of the same ensemble
+picks its variant without re-timing.  A variant is named by its row
+``(x, y, z, occupancy, prefetch)``; ``Ensemble(..., variant=variant_index(...))``
+selects it.
 """
 import json
 import os
 
-from . import Ensemble, LBError, LB_ERR_UNSUPPORTED
+from . import Ensemble, LBError, LB_ERR_UNSUPPORTED, kernel_variants
 
-# Compiled variants (must match the tables in csrc/lattice_d2q9.cu and lattice_d3q19.cu):
-# D2Q9 tiles are (x, y, 1); D3Q19 tiles are (x, y, z-chunk) of the z-marching kernel;
-# the last entry is the resident-CTA target of the register budget (0 = default).
-TILES = {
-    "D2Q9": [(32, 8, 1, 0), (64, 4, 1, 0), (128, 2, 1, 0)],
-    "D3Q19": [(16, 16, 16, 4), (16, 16, 32, 4), (16, 16, 8, 4), (32, 16, 16, 2), (16, 8, 16, 6), (32, 8, 16, 4)],
-}
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "lbfluct_tiles.json")
+
+
+def variants(lattice):
+    """The compiled variants of a lattice, row 0 the default."""
+    return kernel_variants(lattice)
+
+
+def variant_index(lattice, row):
+    """The ``variant`` option (1-based) that selects a compiled variant row."""
+    return variants(lattice).index(tuple(row)) + 1
 
 
 def ensemble_key(systems, precision):
@@ -31,10 +37,10 @@ def ensemble_key(systems, precision):
                             ";".join("%dx%dx%d*%d" % (k + (v,)) for k, v in sorted(counts.items())))
 
 
-def time_tile(systems, precision, tile, steps=20, warmup=5):
-    """Mean milliseconds per step of the step kernel for one tile shape."""
+def time_variant(systems, precision, index, steps=20, warmup=5):
+    """Mean milliseconds per step with compiled variant ``index`` (0-based)."""
     import torch
-    ens = Ensemble(systems, precision=precision, tile=tile[:3], occupancy=tile[3])
+    ens = Ensemble(systems, precision=precision, variant=index + 1)
     try:
         ens.init(amplitude=0.01)
         ens.step(warmup)
@@ -51,7 +57,9 @@ def time_tile(systems, precision, tile, steps=20, warmup=5):
 
 
 def tune(systems, precision="fp32", cache=DEFAULT_CACHE, steps=20, warmup=5, refresh=False):
-    """Return (best tile, {tile: ms}) for this ensemble, using the cache when present."""
+    """Return (best variant row, {row: ms}) for this ensemble, using the cache when present."""
+    lattice = systems[0]["lattice"]
+    rows = variants(lattice)
     key = ensemble_key(systems, precision)
     table = {}
     if cache and os.path.exists(cache) and not refresh:
@@ -60,13 +68,13 @@ def tune(systems, precision="fp32", cache=DEFAULT_CACHE, steps=20, warmup=5, ref
                 table = json.load(fh)
         except (OSError, ValueError):
             table = {}
-        if key in table:
-            ent = table[key]
+        ent = table.get(key)
+        if ent is not None and tuple(ent["best"]) in rows:
             return tuple(ent["best"]), {tuple(map(int, k.split("x"))): v for k, v in ent["ms"].items()}
     results = {}
-    for tile in TILES[systems[0]["lattice"]]:
+    for i, row in enumerate(rows):
         try:
-            results[tile] = time_tile(systems, precision, tile, steps, warmup)
+            results[row] = time_variant(systems, precision, i, steps, warmup)
         except LBError as e:
             if e.status != LB_ERR_UNSUPPORTED:
                 raise

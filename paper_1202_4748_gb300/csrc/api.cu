@@ -115,16 +115,21 @@ std::vector<LevelHost> make_levels(const lb_system_desc& d, int& imax, bool& uni
     return out;
 }
 
-int tile_table(int lattice, int (*t)[4]) {
-    return lattice == LB_D2Q9 ? tile_shapes_d2q9(t, 16) : tile_shapes_d3q19(t, 16);
+int tile_table(int lattice, int (*t)[5]) {
+    return lattice == LB_D2Q9 ? tile_shapes_d2q9(t, 32) : tile_shapes_d3q19(t, 32);
 }
 
-// The first compiled variant matching the requested shape (and occupancy, if given).
+// The variant given by index, else the first compiled variant matching the
+// requested shape (and occupancy, if given), else the default (index 0).
 lb_status choose_tile(int lattice, const lb_run_opts* o, int& tile_id, int tdim[3]) {
-    int t[16][4];
+    int t[32][5];
     const int nt = tile_table(lattice, t);
     tile_id = 0;
-    if (o->tile[0] > 0 || o->occupancy > 0) {
+    if (o->variant < 0) return LB_ERR_ARG;
+    if (o->variant > 0) {
+        if (o->variant > nt) return LB_ERR_UNSUPPORTED;
+        tile_id = o->variant - 1;
+    } else if (o->tile[0] > 0 || o->occupancy > 0) {
         tile_id = -1;
         for (int k = 0; k < nt && tile_id < 0; ++k) {
             const bool shape = o->tile[0] <= 0 || (t[k][0] == o->tile[0] && t[k][1] == o->tile[1] &&
@@ -974,6 +979,15 @@ lb_status lb_load(lb_ctx* c, const char* path) {
     c->sticky = LB_OK;
     c->has_state = true;
     return LB_OK;
+}
+
+int lb_kernel_variants(int lattice, int32_t* out, int max_rows) {
+    if (lattice != LB_D2Q9 && lattice != LB_D3Q19) return int(LB_ERR_ARG);
+    int t[32][5];
+    const int nt = tile_table(lattice, t);
+    for (int r = 0; r < nt && r < max_rows && out; ++r)
+        for (int k = 0; k < 5; ++k) out[5 * r + k] = t[r][k];
+    return nt;
 }
 
 lb_status lb_kernel_launches(lb_ctx* c, int64_t* count) {

@@ -5,7 +5,8 @@
 namespace lbf {
 
 namespace {
-constexpr int kTiles[][4] = {{32, 8, 1, 0}, {64, 4, 1, 0}, {128, 2, 1, 0}};
+// (x, y, 1, resident CTAs per SM (0 = default), prefetch (unused))
+constexpr int kTiles[][5] = {{32, 8, 1, 0, 0}, {64, 4, 1, 0, 0}, {128, 2, 1, 0, 0}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
 
 template <int CP, class Real>
@@ -19,9 +20,9 @@ cudaError_t step_tile(const StepLaunch& a, cudaStream_t st) {
 }
 }  // namespace
 
-int tile_shapes_d2q9(int (*out)[4], int max) {
+int tile_shapes_d2q9(int (*out)[5], int max) {
     for (int t = 0; t < kNumTiles && t < max; ++t)
-        for (int k = 0; k < 4; ++k) out[t][k] = kTiles[t][k];
+        for (int k = 0; k < 5; ++k) out[t][k] = kTiles[t][k];
     return kNumTiles;
 }
 

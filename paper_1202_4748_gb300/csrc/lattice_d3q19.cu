@@ -1,33 +1,41 @@
 // D3Q19 instantiations (3-D variant): Guo-forced form with the Landau
 // pressure in the equilibrium, FP64 and FP32-deviation storage.
+#include <utility>
+
 #include "lattice_tu.cuh"
 
 namespace lbf {
 
 namespace {
-// (x, y, z-chunk, resident CTAs per SM) of the z-marching kernel
-// (the first entry is the default: fastest on the 160-system ensemble by the autotuner)
-constexpr int kTiles[][4] = {{16, 16, 16, 4}, {16, 16, 32, 4}, {16, 16, 8, 4}, {32, 16, 16, 2},
-                             {16, 8, 16, 6}, {32, 8, 16, 4}};
+// (x, y, z-chunk, resident CTAs per SM, prefetch of the collided site) of the
+// z-marching kernel; the first entry is the default (fastest on the 160-system
+// ensemble by the autotuner)
+constexpr int kTiles[][5] = {{16, 16, 16, 4, 0}, {16, 16, 32, 4, 0}, {16, 16, 8, 4, 0}, {16, 8, 16, 6, 0},
+                             {16, 16, 16, 4, 1}, {16, 16, 16, 3, 1}, {16, 8, 16, 6, 1}, {16, 16, 32, 3, 1}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
+
+template <int CP, class Real, int I>
+cudaError_t step_variant(const StepLaunch& a, cudaStream_t st) {
+    return step_z<D3Q19, CP, Real, kTiles[I][0], kTiles[I][1], kTiles[I][2], kTiles[I][3], kTiles[I][4] != 0>(a, st);
+}
+
+template <int CP, class Real, int... I>
+cudaError_t step_tile_of(const StepLaunch& a, cudaStream_t st, std::integer_sequence<int, I...>) {
+    using Fn = cudaError_t (*)(const StepLaunch&, cudaStream_t);
+    static constexpr Fn table[] = {&step_variant<CP, Real, I>...};
+    if (a.tile_id < 0 || a.tile_id >= int(sizeof...(I))) return cudaErrorInvalidValue;
+    return table[a.tile_id](a, st);
+}
 
 template <int CP, class Real>
 cudaError_t step_tile(const StepLaunch& a, cudaStream_t st) {
-    switch (a.tile_id) {
-        case 0: return step_z<D3Q19, CP, Real, 16, 16, 16, 4>(a, st);
-        case 1: return step_z<D3Q19, CP, Real, 16, 16, 32, 4>(a, st);
-        case 2: return step_z<D3Q19, CP, Real, 16, 16, 8, 4>(a, st);
-        case 3: return step_z<D3Q19, CP, Real, 32, 16, 16, 2>(a, st);
-        case 4: return step_z<D3Q19, CP, Real, 16, 8, 16, 6>(a, st);
-        case 5: return step_z<D3Q19, CP, Real, 32, 8, 16, 4>(a, st);
-        default: return cudaErrorInvalidValue;
-    }
+    return step_tile_of<CP, Real>(a, st, std::make_integer_sequence<int, kNumTiles>{});
 }
 }  // namespace
 
-int tile_shapes_d3q19(int (*out)[4], int max) {
+int tile_shapes_d3q19(int (*out)[5], int max) {
     for (int t = 0; t < kNumTiles && t < max; ++t)
-        for (int k = 0; k < 4; ++k) out[t][k] = kTiles[t][k];
+        for (int k = 0; k < 5; ++k) out[t][k] = kTiles[t][k];
     return kNumTiles;
 }
 

@@ -145,9 +145,25 @@ __global__ void __launch_bounds__(AUX_THREADS)
         Real(in[site] - (i == 0 ? S.rho_c : 0.0));
 }
 
+// Compensated sum (Knuth's TwoSum): s + c carries the exact sum of the added
+// values up to the rounding of c, i.e. to about eps^2 relative.
+template <class Real>
+struct CompSum {
+    Real s = Real(0), c = Real(0);
+    __device__ __forceinline__ void add(Real v) {
+        const Real t = s + v;
+        const Real bp = t - s;
+        c += (s - (t - bp)) + (v - bp);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
 // Observable site pass: d(r) = rho(r, t) - rho_c = sum_i delta f_i(r - c_i) and
-// j(r) = sum_i c_i f_i(r - c_i), summed in FP64.  Writes d and per-item
-// partial sums (sum d, sum jx, sum jy, sum jz).
+// j(r) = sum_i c_i f_i(r - c_i), to FP64 accuracy (FP64 sums for FP64 storage;
+// compensated FP32 sums for FP32 storage, which keeps the per-population work
+// off the FP64 pipe).  Writes d and per-item partial sums (sum d, sum jx,
+// sum jy, sum jz) in FP64.
 template <class L, class Real>
 __global__ void __launch_bounds__(AUX_THREADS)
     obs_site_kernel(const SysDev* __restrict__ sysv, const int4* __restrict__ items, const Real* __restrict__ fbuf,
@@ -163,22 +179,25 @@ __global__ void __launch_bounds__(AUX_THREADS)
         if (site >= it.z) break;
         int x, y, z;
         site_coords(site, nx, ny, x, y, z);
-        double r = 0.0, m[3] = {0.0, 0.0, 0.0};
+        CompSum<Real> r, m[3];
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
             const int sx = wrap1(x - L::c(i, 0), nx), sy = wrap1(y - L::c(i, 1), ny);
             const int sz = L::D == 3 ? wrap1(z - L::c(i, 2), nz) : 0;
-            const double v = double(fb[int64_t(i) * S.n_sites + (sx + nx * (sy + ny * sz))]);
-            r += v;
+            const Real v = fb[int64_t(i) * S.n_sites + (sx + nx * (sy + ny * sz))];
+            r.add(v);
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-                if (L::c(i, a) != 0) m[a] += L::c(i, a) * v;
+            for (int a = 0; a < 3; ++a) {
+                if (L::c(i, a) == 1) m[a].add(v);
+                if (L::c(i, a) == -1) m[a].add(-v);
+            }
         }
-        d[S.site_offset + site] = r;
-        acc[0] += r;
-        acc[1] += m[0];
-        acc[2] += m[1];
-        acc[3] += m[2];
+        const double rv = r.value();
+        d[S.site_offset + site] = rv;
+        acc[0] += rv;
+        acc[1] += m[0].value();
+        acc[2] += m[1].value();
+        acc[3] += m[2].value();
     }
     block_sum<4, AUX_THREADS>(acc, sh);
     if (threadIdx.x == 0) {

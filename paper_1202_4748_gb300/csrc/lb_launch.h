@@ -26,9 +26,10 @@ struct StepLaunch {
     int bgk_only;           // 0: per-mode rates; 1: one rate per system; 2: one rate, equal to 1
 };
 
-// Tile variants compiled for each lattice (x, y, z, resident CTAs per SM); index = tile_id.
-int tile_shapes_d2q9(int (*out)[4], int max);
-int tile_shapes_d3q19(int (*out)[4], int max);
+// Step-kernel variants compiled for each lattice: (x, y, z, resident CTAs per
+// SM, prefetch); index = tile_id.
+int tile_shapes_d2q9(int (*out)[5], int max);
+int tile_shapes_d3q19(int (*out)[5], int max);
 
 cudaError_t launch_step_d2q9(int coupling, int fp32, const StepLaunch& a, cudaStream_t st);
 cudaError_t launch_step_d3q19(int coupling, int fp32, const StepLaunch& a, cudaStream_t st);

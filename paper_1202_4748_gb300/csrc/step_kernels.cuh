@@ -600,7 +600,7 @@ struct ZLayout {
     static constexpr size_t bytes = 0;     // static shared memory only
 };
 
-template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB, int MODE>
+template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB, int MODE, bool PREF>
 __global__ void __launch_bounds__(TX* TY, MINB)
     step_kernel_z(const StepArgs<Real> A) {
     static_assert(L::D == 3, "z-marching is for 3-D lattices");
@@ -632,6 +632,14 @@ __global__ void __launch_bounds__(TX* TY, MINB)
 
     // planes of rho needed: z0 - H .. z1 - 1 + H; collision of plane zc trails rho by H
     for (int zz = z0 - H; zz < z1 + H; ++zz) {
+        const int zc = zz - H;
+        const bool collide = zc >= z0 && valid_xy;
+        // PREF: the collided site's populations are requested before the footprint
+        // and Laplacian phases, so their latency overlaps that work
+        Real f[Q];
+        if constexpr (PREF) {
+            if (collide) pull_site<L, Real>(fb, N, Nbr(x, y, zc, nx, ny, nz, true), f);
+        }
         const int slot = (zz - z0 + 2 * NR) % NR;
         const bool sm = S.small != 0;
         const int wz = sm ? wrapm(zz, nz) : wrap2(zz, nz);
@@ -675,11 +683,8 @@ __global__ void __launch_bounds__(TX* TY, MINB)
             __syncthreads();
         }
         // collision of plane zc = zz - H
-        const int zc = zz - H;
-        if (zc >= z0 && valid_xy) {
-            const Nbr nb(x, y, zc, nx, ny, nz, true);
-            Real f[Q];
-            pull_site<L, Real>(fb, N, nb, f);
+        if (collide) {
+            if constexpr (!PREF) pull_site<L, Real>(fb, N, Nbr(x, y, zc, nx, ny, nz, true), f);
             Real drho = Real(0);
             sfor<0, Q>([&](auto I) { drho += f[decltype(I)::value]; });
             const int site = site_index(x, y, zc, nx, ny);

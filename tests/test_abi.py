@@ -123,3 +123,23 @@ def test_derive_matches_oracle_formulas():
     assert np.isclose(out[4], want["U_L"], rtol=1e-13)
     L.n = 0
     assert lb.lb_derive(ctypes.byref(L), kT, out) == lb.LB_ERR_ARG
+
+
+def test_kernel_variant_table():
+    import paper_1202_4748_gb300 as lb
+    for lat in ("D2Q9", "D3Q19"):
+        rows = lb.kernel_variants(lat)
+        assert len(rows) >= 3 and len(set(rows)) == len(rows)
+        for x, y, z, occ, pref in rows:
+            assert x > 0 and y > 0 and z > 0 and occ >= 0 and pref in (0, 1)
+            assert x * y <= 1024 and x % 16 == 0
+        if lat == "D2Q9":
+            assert all(r[2] == 1 for r in rows)
+    assert lb.lb_kernel_variants(7, None, 0) == lb.LB_ERR_ARG
+    # a variant index past the table is rejected at plan time
+    s = synth.system("D3Q19", n=16)
+    n = len(lb.kernel_variants("D3Q19"))
+    with pytest.raises(lb.LBError) as e:
+        lb.workspace_bytes([s], precision="fp32", variant=n + 1)
+    assert e.value.status == lb.LB_ERR_UNSUPPORTED
+    assert lb.workspace_bytes([s], precision="fp32", variant=n) > 0

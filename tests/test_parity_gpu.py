@@ -323,19 +323,20 @@ def test_single_rate_collision_paths(lb, lattice, coupling, shape, tau):
         ens.close()
 
 
-def test_autotuner_times_every_tile_and_caches(lb, tmp_path):
+def test_autotuner_times_every_variant_and_caches(lb, tmp_path):
     from paper_1202_4748_gb300 import autotune
     systems = synth.ensemble("fss_160", "D3Q19")[:8]
+    rows = autotune.variants("D3Q19")
     cache = os.path.join(tmp_path, "tiles.json")
     best, ms = autotune.tune(systems, "fp32", cache=cache, steps=4, warmup=2)
-    assert set(ms) == set(autotune.TILES["D3Q19"]) and best in ms
+    assert set(ms) == set(rows) and best in ms
     assert all(v > 0 for v in ms.values())
     best2, ms2 = autotune.tune(systems, "fp32", cache=cache)
     assert best2 == best and ms2 == ms
-    # every tile gives the same trajectory (the tile only changes the schedule)
+    # every variant gives the same trajectory (it only changes the schedule)
     runs = []
-    for tile in autotune.TILES["D3Q19"]:
-        e = lb.Ensemble(systems[:3], precision="fp32", tile=tile[:3], occupancy=tile[3])
+    for i in range(len(rows)):
+        e = lb.Ensemble(systems[:3], precision="fp32", variant=i + 1)
         e.init()
         e.step(3)
         runs.append([e.read_fields(k) for k in range(3)])
