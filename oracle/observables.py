@@ -17,6 +17,19 @@ division is exact, then the single-site level (1, 1, 1) if not yet reached.
 For a 2-D lattice the z extent of a block is 1.  Level i = 0 is the whole
 system, where m = 0 by mass conservation (kept as a check).
 
+Order-parameter distribution (Sec. II D): P_L(m) is the histogram of the
+block values m_L^(b) of a level over all blocks and samples.  Bins (a
+convention of this project): nbins equal bins on [lo, hi); a value goes to bin
+floor(t) with t = (m - lo) * (nbins / (hi - lo)) evaluated in FP64, below lo to
+an underflow count and at or above hi (or NaN) to an overflow count.  From a
+histogram symmetric about m = 0 the estimators of Sec. IV (order-parameter
+distribution results) are: M_L as the position of the maximum of P_L, chi_L
+from the peak height through the Gaussian forms of P_L (one central peak:
+chi_L = L^d / (2 pi kT P_max^2); two displaced peaks, each carrying half the
+weight: chi_L = L^d / (8 pi kT P_max^2)), and chi_L from the variance of a
+Gaussian fitted to the peak (chi_L = L^d sigma^2 / kT), after an optional
+central region |m| < m_cut is set to zero (also in the normalisation).
+
 Structure factor (Eq. 80): C(k) = N^-1 |sum_r phi(r) exp(-i k.r)|^2, with the
 discrete Fourier transform taken by numpy's FFT (a library primitive).  Shell
 binning (a convention of this project): on an S^d lattice, k = 2 pi n / S with
@@ -136,6 +149,88 @@ def bin_shells(ck_sum, shape, nbins):
     return sums, counts
 
 
+def histogram(m, lo, hi, nbins):
+    """[underflow, bin 0 .. nbins-1, overflow] counts of the values ``m``."""
+    m = np.asarray(m, dtype=np.float64).ravel()
+    inv_w = float(nbins) / (hi - lo)
+    t = (m - lo) * inv_w
+    out = np.zeros(nbins + 2, dtype=np.int64)
+    under = t < 0
+    inside = (t >= 0) & (t < nbins)
+    out[0] = under.sum()
+    out[-1] = m.size - under.sum() - inside.sum()        # t >= nbins or NaN
+    np.add.at(out, 1 + np.floor(t[inside]).astype(np.int64), 1)
+    return out
+
+
+def sample_histograms(phi, lv, lo, hi, nbins):
+    """Per-level histogram increments of one snapshot of phi."""
+    return np.stack([histogram(block_means(phi, blk), lo, hi, nbins) for blk in lv])
+
+
+def histogram_estimates(counts, lo, hi, vol, kT, m_cut=0.0, frac=0.2):
+    """Estimators of M_L and chi_L from one level's histogram (see module docstring).
+
+    The range must be symmetric (lo = -hi).  Steps: bin centres m_k; bins with
+    |m_k| < m_cut zeroed; N = kept bins + underflow + overflow; the histogram
+    symmetrised, P_s(k) = (c_k + c_{nbins-1-k}) / 2; the peak k* = the first
+    maximum of P_s over the upper half m_k >= 0; P_max = P_s(k*) / (N w); the
+    peak is central when k* is the innermost upper bin.  The Gaussian fit is a
+    least-squares fit of log P_s = alpha + beta m + gamma m^2, weighted by the
+    counts, over the contiguous bins around k* with P_s >= frac P_s(k*) (for a
+    central peak on both sides of m = 0, else in the upper half);
+    sigma^2 = -1 / (2 gamma), centre -beta / (2 gamma).
+    """
+    counts = np.asarray(counts, dtype=np.float64)
+    nb = counts.size - 2
+    if not (lo == -hi and hi > 0 and nb >= 2 and vol > 0 and kT > 0):
+        raise ValueError("need a symmetric range, >= 2 bins, vol > 0 and kT > 0")
+    w = (hi - lo) / nb
+    centres = lo + (np.arange(nb) + 0.5) * w
+    c = counts[1:-1].copy()
+    c[np.abs(centres) < m_cut] = 0.0
+    n_all = c.sum() + counts[0] + counts[-1]
+    ps = 0.5 * (c + c[::-1])
+    k_in = nb // 2                          # innermost bin with centre >= 0
+    upper = ps[k_in:]
+    nan = float("nan")
+    out = dict(m_max=nan, P_max=nan, chi_peak=nan, M_fit=nan, sigma2_fit=nan, chi_fit=nan, n_fit=0,
+               central=True, hist_abs_m=nan, hist_m2=nan, n_total=n_all)
+    if n_all <= 0 or upper.max() <= 0:
+        return out
+    ks = k_in + int(np.argmax(upper))
+    out["m_max"] = centres[ks]
+    out["P_max"] = ps[ks] / (n_all * w)
+    central = ks == k_in
+    out["central"] = bool(central)
+    out["chi_peak"] = vol / ((2.0 if central else 8.0) * np.pi * kT * out["P_max"] ** 2)
+    lo_k = ks
+    floor = frac * ps[ks]
+    kmin = 0 if central else k_in
+    while lo_k - 1 >= kmin and ps[lo_k - 1] >= floor:
+        lo_k -= 1
+    hi_k = ks
+    while hi_k + 1 < nb and ps[hi_k + 1] >= floor:
+        hi_k += 1
+    sel = np.arange(lo_k, hi_k + 1)
+    if sel.size >= 3:
+        x = centres[sel]
+        y = np.log(ps[sel])
+        wt = ps[sel]
+        A = np.stack([np.ones_like(x), x, x * x], axis=1)
+        coef = np.linalg.solve(A.T @ (wt[:, None] * A), A.T @ (wt * y))
+        if coef[2] < 0:
+            out["sigma2_fit"] = -0.5 / coef[2]
+            out["M_fit"] = -coef[1] / (2.0 * coef[2])
+            out["chi_fit"] = vol * out["sigma2_fit"] / kT
+        out["n_fit"] = int(sel.size)
+    kept = c.sum()
+    if kept > 0:
+        out["hist_abs_m"] = float((np.abs(centres) * c).sum() / kept)
+        out["hist_m2"] = float((centres * centres * c).sum() / kept)
+    return out
+
+
 class Recorder:
     """Accumulates block observables (and optionally C(k)) every ``every`` steps.
 
@@ -143,11 +238,13 @@ class Recorder:
     Also records the FP64 mass sum rho and momentum sum j at each sample.
     """
 
-    def __init__(self, p, every, sk_every=0):
+    def __init__(self, p, every, sk_every=0, hist=None):
         self.p = p
         self.lv = levels(p)
         self.every = every
         self.sk_every = sk_every
+        self.hist_cfg = hist                    # (nbins, lo, hi) or None
+        self.hist = np.zeros((len(self.lv), hist[0] + 2), dtype=np.int64) if hist else None
         self.acc = np.zeros((len(self.lv), len(ACC_FIELDS)))
         self.ck = np.zeros(p.shape)
         self.n_sk = 0
@@ -158,6 +255,9 @@ class Recorder:
         if self.every > 0 and t > 0 and t % self.every == 0:
             phi = order_parameter(f)
             self.acc += sample(phi, self.lv)
+            if self.hist is not None:
+                nb, lo, hi = self.hist_cfg
+                self.hist += sample_histograms(phi, self.lv, lo, hi, nb)
             self.mass.append(lbm.density(f).sum())
             self.mom.append(lbm.momentum(f, self.p.lat).reshape(3, -1).sum(axis=1))
         if self.sk_every > 0 and t > 0 and t % self.sk_every == 0:
