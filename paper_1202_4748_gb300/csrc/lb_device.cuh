@@ -228,13 +228,16 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0,
     n1 = r * s;
 }
 // FP32 variant on the special-function unit: -2 ln U = -2 ln2 log2 U, clamped
-// at 0 because log2 of U within an ulp of 1 may come out slightly positive;
-// the angle is taken as 2 pi (U_b - 1/2) in [-pi, pi), where the hardware
-// sine/cosine are accurate, and the half turn is undone by the sign flips.
+// at a tiny positive value because log2 of U within an ulp of 1 may come out
+// slightly positive, and its square root taken as x rsqrt(x) (a few ulp; the
+// IEEE-rounded square root costs several more instructions); the angle is
+// taken as 2 pi (U_b - 1/2) in [-pi, pi), where the hardware sine/cosine are
+// accurate, and the half turn is undone by the sign flips.
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
     const float ua = fmaf(float(wa), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     const float ub = fmaf(float(wb), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const float r = sqrtf(fmaxf(-1.3862943611198906f * __log2f(ua), 0.0f));
+    const float r2 = fmaxf(-1.3862943611198906f * __log2f(ua), 1e-30f);
+    const float r = r2 * rsqrtf(r2);
     float s, c;
     __sincosf(6.2831853071795865f * (ub - 0.5f), &s, &c);
     n0 = -r * c;
@@ -248,6 +251,9 @@ __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
+// Square root of x >= 0: exact rounding in double; x rsqrt(x) in float (0 at 0).
+__device__ __forceinline__ double fast_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 
 // Periodic wrap of a coordinate in [-n, 2n).
 __device__ __forceinline__ int wrap2(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }

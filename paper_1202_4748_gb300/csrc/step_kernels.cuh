@@ -108,7 +108,7 @@ __device__ __forceinline__ void noise_modes(const SysDev& S, const SysPhys<Real>
         box_muller(w.x, w.y, nrm[4 * d + 0], nrm[4 * d + 1]);
         box_muller(w.z, w.w, nrm[4 * d + 2], nrm[4 * d + 3]);
     });
-    const Real sc = sqrt(Real(3) * (rho > Real(0) ? rho : Real(0)) * P.kT);
+    const Real sc = fast_sqrt(Real(3) * (rho > Real(0) ? rho : Real(0)) * P.kT);
     // the coupled pair (MP, MR): M = [N + (1 - 3 c_s^2) v v^T] g, v_a = T_a(c = 0)
     constexpr int MP = L::PP, MR = L::PR;
     constexpr double vP = double(L::T(MP, 0)), vR = double(L::T(MR, 0));
@@ -122,7 +122,7 @@ __device__ __forceinline__ void noise_modes(const SysDev& S, const SysPhys<Real>
         const Real r = fast_rsqrt(Mpp);
         const Real l11 = Mpp * r;
         const Real l21 = Mpr * r;
-        const Real l22 = sqrt(det) * r;
+        const Real l22 = fast_sqrt(det) * r;
         const Real nP = nrm[MP - L::NC], nR = nrm[MR - L::NC];
         xi[MP - L::NC] = sc * l11 * nP;
         xi[MR - L::NC] = sc * (l21 * nP + l22 * nR);
