@@ -103,7 +103,14 @@ typedef struct {
  *               compiled variant, else LB_ERR_UNSUPPORTED.
  *   variant     if > 0, selects compiled step-kernel variant number
  *               variant - 1 of lb_kernel_variants() directly (overrides
- *               tile and occupancy); 0 = by tile / occupancy / default.      */
+ *               tile and occupancy); 0 = by tile / occupancy / default.
+ *   hist_bins   order-parameter histograms P_L(m) (Sec. II D): every
+ *               observable sample also bins each block value m of every
+ *               level into hist_bins equal bins on [-hist_range, hist_range)
+ *               (plus under/overflow counts); 0 disables, at most
+ *               LB_MAX_HIST_BINS.
+ *   hist_range  half-width of the histogram range (> 0 when hist_bins > 0). */
+#define LB_MAX_HIST_BINS 4096
 typedef struct {
     int32_t precision;
     int32_t obs_every;
@@ -112,6 +119,8 @@ typedef struct {
     int32_t tile[3];
     int32_t occupancy;
     int32_t variant;
+    int32_t hist_bins;
+    double hist_range;
 } lb_run_opts;
 
 /* FP64 accumulators of one block level (Eqs. 46-50).  Blocks have dims
@@ -181,6 +190,44 @@ lb_status lb_observables(lb_ctx* ctx, int sys, lb_obs_level* h_levels, int max_l
  * (Eq. 49), out[3] = c_H,L (Eq. 50), out[4] = Binder U_L = 1 - <m^4>/(3<m^2>^2),
  * out[5] = <m>.  Pure host arithmetic.  Errors: LB_ERR_ARG (n == 0, kT <= 0). */
 lb_status lb_derive(const lb_obs_level* level, double kT, double out[6]);
+
+/* Order-parameter histogram P_L(m) of level `level` of system `sys` (level
+ * order as in lb_observables), accumulated over the obs_every schedule: the
+ * histogram of the block values m_L^(b) (Eq. 46) over all blocks and samples
+ * (Sec. II D).  Writes nbins + 2 counts to h_counts: [0] values below lo,
+ * [1 + k] values in bin k, i.e. with floor((m - lo) * (nbins / (hi - lo))) = k
+ * evaluated in float64, [nbins + 1] values at or above hi or NaN; and the
+ * range lo = -hist_range, hi = hist_range (nullable).  n_counts must equal
+ * hist_bins + 2.  Synchronises.  Errors: LB_ERR_ARG (indices, n_counts),
+ * LB_ERR_UNSUPPORTED (hist_bins == 0), device errors, LB_ERR_CUDA. */
+lb_status lb_histogram(lb_ctx* ctx, int sys, int level, uint64_t* h_counts, int n_counts, double* lo,
+                       double* hi);
+
+/* Estimators of M_L and chi_L from one histogram (Sec. IV, order-parameter
+ * distribution), pure host arithmetic.  counts: nbins + 2 values as written by
+ * lb_histogram, on a range symmetric about 0 (lo = -hi); vol = L^d, the block
+ * volume; kT the noise temperature; bins whose centre has |m| < m_cut are set
+ * to zero, also in the normalisation (0 = keep all); frac in (0, 1) bounds the
+ * Gaussian-fit window (contiguous bins around the peak with count >= frac x
+ * the peak count).  With P_s the histogram symmetrised about m = 0 and k* the
+ * first maximum of P_s over bins with centre >= 0:
+ *   out[0] m_max  centre of bin k* (M_L as the position of the maximum)
+ *   out[1] P_max  P_s(k*) / (N w): N = kept counts + under + overflow, w = bin width
+ *   out[2] chi_L  from the peak height: vol / (2 pi kT P_max^2) for a peak in
+ *                 the innermost bin (one Gaussian about 0), else
+ *                 vol / (8 pi kT P_max^2) (two Gaussians of half weight)
+ *   out[3] M_fit  centre of a Gaussian fitted to the peak (weighted least
+ *                 squares of log P_s against a quadratic; NaN if the window
+ *                 has < 3 bins or is not concave)
+ *   out[4] sigma^2 of that Gaussian, out[5] chi_L = vol sigma^2 / kT
+ *   out[6] bins in the fit window, out[7] 1 if the peak is central else 0
+ *   out[8] <|m|> and out[9] <m^2> over the kept bins (bin centres)
+ *   out[10] N.
+ * Errors: LB_ERR_ARG (nbins < 2, asymmetric range, vol <= 0, kT <= 0, frac
+ * outside (0, 1), null pointers). */
+#define LB_HIST_EST 11
+lb_status lb_histogram_estimates(const uint64_t* counts, int nbins, double lo, double hi, double vol, double kT,
+                                 double m_cut, double frac, double out[LB_HIST_EST]);
 
 /* Structure factor of Eq. 80 accumulated over the sk_every schedule, binned in
  * shells j = 1..nbins (k = 2 pi n / S, shell j holds j(j-1) < |n|^2 <= j(j+1)):

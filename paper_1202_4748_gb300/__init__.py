@@ -31,6 +31,7 @@ LB_FP64, LB_FP32_DEVIATION = 0, 1
 LB_INIT_UNIFORM_NOISE, LB_INIT_FROM_RHO = 0, 1
 LB_MAX_Q = 19
 LB_MAX_LEVELS = 32
+LB_MAX_HIST_BINS = 4096
 LB_NOALLOC_MAX_SITES = 1 << 18
 Q_OF = {LB_D2Q9: 9, LB_D3Q19: 19}
 
@@ -47,7 +48,8 @@ class lb_system_desc(ctypes.Structure):
 class lb_run_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("obs_every", ctypes.c_int32),
                 ("sk_every", ctypes.c_int32), ("graph_chunk", ctypes.c_int32),
-                ("tile", ctypes.c_int32 * 3), ("occupancy", ctypes.c_int32), ("variant", ctypes.c_int32)]
+                ("tile", ctypes.c_int32 * 3), ("occupancy", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("hist_bins", ctypes.c_int32), ("hist_range", ctypes.c_double)]
 
 
 class lb_obs_level(ctypes.Structure):
@@ -76,6 +78,10 @@ _SIG = {
     "lb_observables": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(lb_obs_level), ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(lb_obs_global)]),
     "lb_derive": (ctypes.c_int, [ctypes.POINTER(lb_obs_level), ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "lb_histogram": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)]),
+    "lb_histogram_estimates": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_double, _P]),
     "lb_structure_factor": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
     "lb_read_fields": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "lb_write_fields": (ctypes.c_int, [_P, ctypes.c_int, _P]),
@@ -134,7 +140,8 @@ def make_desc(systems):
     return arr
 
 
-def make_opts(precision="fp64", obs_every=0, sk_every=0, graph_chunk=0, tile=(0, 0, 0), occupancy=0, variant=0):
+def make_opts(precision="fp64", obs_every=0, sk_every=0, graph_chunk=0, tile=(0, 0, 0), occupancy=0, variant=0,
+              hist_bins=0, hist_range=0.0):
     o = lb_run_opts()
     o.precision = {"fp64": LB_FP64, "fp32": LB_FP32_DEVIATION}.get(precision, precision)
     o.obs_every, o.sk_every, o.graph_chunk = int(obs_every), int(sk_every), int(graph_chunk)
@@ -142,7 +149,25 @@ def make_opts(precision="fp64", obs_every=0, sk_every=0, graph_chunk=0, tile=(0,
         o.tile[k] = int(tile[k])
     o.occupancy = int(occupancy)
     o.variant = int(variant)
+    o.hist_bins = int(hist_bins)
+    o.hist_range = float(hist_range)
     return o
+
+
+HIST_EST_FIELDS = ("m_max", "P_max", "chi_peak", "M_fit", "sigma2_fit", "chi_fit", "n_fit", "central",
+                   "hist_abs_m", "hist_m2", "n_total")
+
+
+def histogram_estimates(counts, lo, hi, vol, kT, m_cut=0.0, frac=0.2):
+    """M_L and chi_L estimators of one level's histogram (lb_histogram_estimates)."""
+    c = np.ascontiguousarray(counts, dtype=np.uint64)
+    out = (ctypes.c_double * len(HIST_EST_FIELDS))()
+    check(lb_histogram_estimates(c.ctypes.data_as(_P), c.size - 2, float(lo), float(hi), float(vol), float(kT),
+                                 float(m_cut), float(frac), out), "lb_histogram_estimates")
+    d = dict(zip(HIST_EST_FIELDS, list(out)))
+    d["n_fit"] = int(d["n_fit"])
+    d["central"] = bool(d["central"])
+    return d
 
 
 def kernel_variants(lattice):
@@ -231,6 +256,15 @@ class Ensemble:
         out = (ctypes.c_double * 6)()
         check(lb_derive(ctypes.byref(L), float(kT), out), "lb_derive")
         return dict(M_L=out[0], chi_L=out[1], chi_L_lowT=out[2], c_HL=out[3], U_L=out[4], mean_m=out[5])
+
+    def histogram(self, k, level):
+        """(counts [under, bins, over], lo, hi) of level ``level`` of system ``k``."""
+        n = int(self._opts.hist_bins) + 2
+        out = np.zeros(n, dtype=np.uint64)
+        lo, hi = ctypes.c_double(), ctypes.c_double()
+        check(lb_histogram(self.ctx, k, level, out.ctypes.data_as(_P), n, ctypes.byref(lo), ctypes.byref(hi)),
+              "lb_histogram")
+        return out, lo.value, hi.value
 
     def structure_factor(self, k, nbins):
         s = np.zeros(nbins)

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/lbfluct.h"
@@ -39,7 +40,9 @@ struct SysHost {
 // Byte offsets of every region inside the workspace.
 struct Plan {
     size_t sys, phys, tiles, pop0, pop1, step, status, d, dbar, site_items, site_partial, spans, red4, glob, levels,
-        S, E, bottom_items, up_items, rec, acc, field_tmp, sk_sys, sk_tw, sk_acc, sk_b0, sk_b1, sk_bins, total;
+        S, E, bottom_items, up_items, rec, acc, hist, field_tmp, sk_sys, sk_tw, sk_acc, sk_b0, sk_b1, sk_bins, total;
+    int hist_bins = 0;
+    double hist_range = 0.0;
     int n_tiles = 0, n_site_items = 0, n_levels = 0, n_bottom = 0, n_up = 0, n_rec = 0, max_depth = 0;
     int64_t n_sites = 0, n_blocks_pyr = 0, max_sites = 0;
     std::vector<int4> tiles_h, site_items_h;
@@ -60,6 +63,8 @@ lb_status validate(const lb_system_desc* s, int n, const lb_run_opts* o) {
     if (!s || n <= 0 || !o) return LB_ERR_ARG;
     if (o->precision != LB_FP64 && o->precision != LB_FP32_DEVIATION) return LB_ERR_ARG;
     if (o->obs_every < 0 || o->sk_every < 0 || o->graph_chunk < 0 || (o->graph_chunk & 1)) return LB_ERR_ARG;
+    if (o->hist_bins < 0 || o->hist_bins > LB_MAX_HIST_BINS) return LB_ERR_ARG;
+    if (o->hist_bins > 0 && !(o->hist_range > 0 && std::isfinite(o->hist_range))) return LB_ERR_ARG;
     for (int k = 0; k < n; ++k) {
         const lb_system_desc& d = s[k];
         if (d.lattice != s[0].lattice || d.coupling != s[0].coupling) return LB_ERR_ARG;
@@ -330,6 +335,9 @@ lb_status make_plan(const lb_system_desc* s, int n, const lb_run_opts* o, std::v
     P.up_items = take(sizeof(ObsItem) * P.n_up);
     P.rec = take(sizeof(double) * REC * P.n_rec);
     P.acc = take(sizeof(double) * 7 * P.n_levels);
+    P.hist_bins = o->hist_bins;
+    P.hist_range = o->hist_range;
+    P.hist = take(sizeof(uint64_t) * (P.hist_bins > 0 ? (P.hist_bins + 2) * int64_t(P.n_levels) : 0));
     P.field_tmp = take(sizeof(double) * P.max_sites);
     const int64_t skn = P.sk ? P.n_sites : 0;
     P.sk_sys = take(sizeof(SkSys) * (P.sk ? n : 0));
@@ -442,6 +450,10 @@ cudaError_t launch_step_any(lb_ctx* c, const StepLaunch& a) {
                                  : launch_step_d3q19(c->coupling, c->fp32, a, c->stream);
 }
 
+size_t hist_bytes(const Plan& P) {
+    return P.hist_bins > 0 ? sizeof(uint64_t) * (P.hist_bins + 2) * size_t(P.n_levels) : 0;
+}
+
 // Observable sample of the state held in population buffer `buf`.
 cudaError_t sample_obs(lb_ctx* c, int buf, bool set_mass0, bool count) {
     const Plan& P = c->P;
@@ -461,15 +473,20 @@ cudaError_t sample_obs(lb_ctx* c, int buf, bool set_mass0, bool count) {
     c->launches += 3;
     if (e != cudaSuccess || !count) return e;
     c->launches += 2 + P.max_depth;
+    HistDev H;
+    H.counts = c->at<unsigned long long>(P.hist);
+    H.nbins = P.hist_bins;
+    H.lo = -P.hist_range;
+    H.inv_w = P.hist_bins > 0 ? double(P.hist_bins) / (P.hist_range - (-P.hist_range)) : 0.0;
     e = launch_pyr_bottom(sys, c->at<LevelDev>(P.levels), c->at<ObsItem>(P.bottom_items), P.n_bottom,
                           c->at<double>(P.d), c->at<double>(P.dbar), c->at<double>(P.S), c->at<double>(P.E),
-                          c->at<double>(P.rec), c->stream);
+                          c->at<double>(P.rec), H, c->stream);
     if (e != cudaSuccess) return e;
     for (int u = 1; u <= P.max_depth; ++u) {
         const int first = P.up_first[u - 1], cnt = P.up_first[u] - first;
         e = launch_pyr_up(sys, c->at<LevelDev>(P.levels), c->at<ObsItem>(P.up_items) + first, cnt,
                           c->lattice == LB_D3Q19 ? 1 : 0, c->at<double>(P.S), c->at<double>(P.E),
-                          c->at<double>(P.rec), c->stream);
+                          c->at<double>(P.rec), H, c->stream);
         if (e != cudaSuccess) return e;
     }
     return launch_obs_accum(c->at<LevelDev>(P.levels), P.n_levels, c->at<double>(P.rec), c->at<double>(P.acc),
@@ -570,6 +587,7 @@ void drop_graphs(lb_ctx* c) {
 lb_status reset_accumulators(lb_ctx* c) {
     const Plan& P = c->P;
     LB_CHECK(cudaMemsetAsync(c->ws + P.acc, 0, sizeof(double) * 7 * P.n_levels, c->stream));
+    if (P.hist_bins > 0) LB_CHECK(cudaMemsetAsync(c->ws + P.hist, 0, hist_bytes(P), c->stream));
     LB_CHECK(cudaMemsetAsync(c->ws + P.glob, 0, sizeof(double) * 8 * c->n_sys, c->stream));
     LB_CHECK(cudaMemsetAsync(c->ws + P.status, 0, sizeof(int), c->stream));
     if (P.sk) LB_CHECK(cudaMemsetAsync(c->ws + P.sk_acc, 0, sizeof(double) * P.n_sites, c->stream));
@@ -843,6 +861,116 @@ lb_status lb_derive(const lb_obs_level* L, double kT, double out[6]) {
     return LB_OK;
 }
 
+lb_status lb_histogram(lb_ctx* c, int sys, int level, uint64_t* h_counts, int n_counts, double* lo, double* hi) {
+    if (!c || sys < 0 || sys >= c->n_sys) return LB_ERR_ARG;
+    const Plan& P = c->P;
+    if (P.hist_bins == 0) return LB_ERR_UNSUPPORTED;
+    const SysHost& h = c->sys[sys];
+    if (level < 0 || level >= int(h.lv.size()) || !h_counts || n_counts != P.hist_bins + 2) return LB_ERR_ARG;
+    const int nh = P.hist_bins + 2;
+    LB_CHECK(cudaMemcpyAsync(h_counts, c->at<uint64_t>(P.hist) + int64_t(h.lv_first + level) * nh,
+                             sizeof(uint64_t) * nh, cudaMemcpyDeviceToHost, c->stream));
+    if (lo) *lo = -P.hist_range;
+    if (hi) *hi = P.hist_range;
+    return sync_and_check(c);
+}
+
+lb_status lb_histogram_estimates(const uint64_t* counts, int nbins, double lo, double hi, double vol, double kT,
+                                 double m_cut, double frac, double out[LB_HIST_EST]) {
+    if (!counts || !out || nbins < 2 || !(hi > 0) || lo != -hi || !std::isfinite(hi) || !(vol > 0) || !(kT > 0) ||
+        !(frac > 0 && frac < 1) || !(m_cut >= 0))
+        return LB_ERR_ARG;
+    for (int k = 0; k < LB_HIST_EST; ++k) out[k] = NAN;
+    const double w = (hi - lo) / nbins;
+    std::vector<double> mc(nbins), cnt(nbins), ps(nbins);
+    double n_all = double(counts[0]) + double(counts[nbins + 1]);
+    for (int k = 0; k < nbins; ++k) {
+        mc[k] = lo + (k + 0.5) * w;
+        cnt[k] = std::fabs(mc[k]) < m_cut ? 0.0 : double(counts[1 + k]);
+        n_all += cnt[k];
+    }
+    for (int k = 0; k < nbins; ++k) ps[k] = 0.5 * (cnt[k] + cnt[nbins - 1 - k]);
+    out[6] = 0;
+    out[10] = n_all;
+    const int k_in = nbins / 2;       // innermost bin with centre >= 0
+    int ks = k_in;
+    for (int k = k_in + 1; k < nbins; ++k)
+        if (ps[k] > ps[ks]) ks = k;
+    double kept = 0, s_abs = 0, s_m2 = 0;
+    for (int k = 0; k < nbins; ++k) {
+        kept += cnt[k];
+        s_abs += std::fabs(mc[k]) * cnt[k];
+        s_m2 += mc[k] * mc[k] * cnt[k];
+    }
+    if (kept > 0) {
+        out[8] = s_abs / kept;
+        out[9] = s_m2 / kept;
+    }
+    if (!(n_all > 0) || !(ps[ks] > 0)) return LB_OK;
+    const bool central = ks == k_in;
+    out[0] = mc[ks];
+    out[1] = ps[ks] / (n_all * w);
+    constexpr double kPi = 3.14159265358979323846;
+    out[2] = vol / ((central ? 2.0 : 8.0) * kPi * kT * out[1] * out[1]);
+    out[7] = central ? 1.0 : 0.0;
+    // fit window: contiguous bins around k* at or above frac of the peak
+    const double floor_v = frac * ps[ks];
+    const int kmin = central ? 0 : k_in;
+    int a = ks, b = ks;
+    while (a - 1 >= kmin && ps[a - 1] >= floor_v) --a;
+    while (b + 1 < nbins && ps[b + 1] >= floor_v) ++b;
+    const int nfit = b - a + 1;
+    out[6] = nfit;
+    if (nfit >= 3) {
+        // weighted normal equations for y = c0 + c1 x + c2 x^2, x centred on the peak
+        // for conditioning (the fitted curve is the same)
+        const double x0 = mc[ks];
+        double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, r[3] = {0, 0, 0};
+        for (int k = a; k <= b; ++k) {
+            const double x = mc[k] - x0, y = std::log(ps[k]), wt = ps[k];
+            const double v[3] = {1.0, x, x * x};
+            for (int i = 0; i < 3; ++i) {
+                r[i] += wt * v[i] * y;
+                for (int j = 0; j < 3; ++j) A[i][j] += wt * v[i] * v[j];
+            }
+        }
+        // Gaussian elimination with partial pivoting on the 3 x 3 system
+        double M[3][4];
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) M[i][j] = A[i][j];
+            M[i][3] = r[i];
+        }
+        bool ok = true;
+        for (int col = 0; col < 3 && ok; ++col) {
+            int best = col;
+            for (int i = col + 1; i < 3; ++i)
+                if (std::fabs(M[i][col]) > std::fabs(M[best][col])) best = i;
+            if (!(std::fabs(M[best][col]) > 0)) ok = false;
+            if (!ok) break;
+            if (best != col)
+                for (int j = 0; j < 4; ++j) std::swap(M[col][j], M[best][j]);
+            for (int i = col + 1; i < 3; ++i) {
+                const double f = M[i][col] / M[col][col];
+                for (int j = col; j < 4; ++j) M[i][j] -= f * M[col][j];
+            }
+        }
+        if (ok) {
+            double cf[3];
+            for (int i = 2; i >= 0; --i) {
+                double t = M[i][3];
+                for (int j = i + 1; j < 3; ++j) t -= M[i][j] * cf[j];
+                cf[i] = t / M[i][i];
+            }
+            if (cf[2] < 0) {
+                out[4] = -0.5 / cf[2];
+                out[3] = x0 - cf[1] / (2.0 * cf[2]);
+                out[5] = vol * out[4] / kT;
+            }
+        }
+    }
+    return LB_OK;
+}
+
 lb_status lb_structure_factor(lb_ctx* c, int sys, double* h_sum, int64_t* h_count, int nbins, int64_t* n_samples) {
     if (!c || sys < 0 || sys >= c->n_sys || nbins < 0 || (nbins > 0 && (!h_sum || !h_count))) return LB_ERR_ARG;
     const Plan& P = c->P;
@@ -907,6 +1035,8 @@ struct CkptHeader {
     char magic[8];
     int32_t version, lattice, coupling, fp32, n_sys, q;
     int64_t step, n_sites, n_levels;
+    int32_t hist_bins, pad;
+    double hist_range;
 };
 
 lb_status lb_save(lb_ctx* c, const char* path) {
@@ -916,7 +1046,10 @@ lb_status lb_save(lb_ctx* c, const char* path) {
     const size_t es = c->fp32 ? 4 : 8;
     std::vector<char> pop(es * c->q * P.n_sites);
     std::vector<double> acc(7 * P.n_levels), glob(8 * c->n_sys);
+    std::vector<uint64_t> hist(hist_bytes(P) / sizeof(uint64_t));
     LB_CHECK(cudaMemcpyAsync(pop.data(), c->pop(int(c->step & 1)), pop.size(), cudaMemcpyDeviceToHost, c->stream));
+    if (!hist.empty())
+        LB_CHECK(cudaMemcpyAsync(hist.data(), c->ws + P.hist, hist_bytes(P), cudaMemcpyDeviceToHost, c->stream));
     LB_CHECK(cudaMemcpyAsync(acc.data(), c->ws + P.acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost,
                              c->stream));
     LB_CHECK(cudaMemcpyAsync(glob.data(), c->ws + P.glob, sizeof(double) * glob.size(), cudaMemcpyDeviceToHost,
@@ -926,8 +1059,10 @@ lb_status lb_save(lb_ctx* c, const char* path) {
     if (!fp) return LB_ERR_IO;
     CkptHeader hd;
     std::memset(&hd, 0, sizeof(hd));
-    std::memcpy(hd.magic, "LBFLUCT1", 8);
-    hd.version = 1;
+    std::memcpy(hd.magic, "LBFLUCT2", 8);
+    hd.version = 2;
+    hd.hist_bins = P.hist_bins;
+    hd.hist_range = P.hist_range;
     hd.lattice = c->lattice;
     hd.coupling = c->coupling;
     hd.fp32 = c->fp32;
@@ -941,6 +1076,7 @@ lb_status lb_save(lb_ctx* c, const char* path) {
     ok = ok && std::fwrite(pop.data(), 1, pop.size(), fp) == pop.size();
     ok = ok && std::fwrite(acc.data(), sizeof(double), acc.size(), fp) == acc.size();
     ok = ok && std::fwrite(glob.data(), sizeof(double), glob.size(), fp) == glob.size();
+    ok = ok && std::fwrite(hist.data(), sizeof(uint64_t), hist.size(), fp) == hist.size();
     ok = (std::fclose(fp) == 0) && ok;
     return ok ? LB_OK : LB_ERR_IO;
 }
@@ -951,9 +1087,10 @@ lb_status lb_load(lb_ctx* c, const char* path) {
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return LB_ERR_IO;
     CkptHeader hd;
-    bool ok = std::fread(&hd, sizeof(hd), 1, fp) == 1 && std::memcmp(hd.magic, "LBFLUCT1", 8) == 0 &&
-              hd.version == 1 && hd.lattice == c->lattice && hd.coupling == c->coupling && hd.fp32 == c->fp32 &&
-              hd.n_sys == c->n_sys && hd.q == c->q && hd.n_sites == P.n_sites && hd.n_levels == P.n_levels;
+    bool ok = std::fread(&hd, sizeof(hd), 1, fp) == 1 && std::memcmp(hd.magic, "LBFLUCT2", 8) == 0 &&
+              hd.version == 2 && hd.lattice == c->lattice && hd.coupling == c->coupling && hd.fp32 == c->fp32 &&
+              hd.n_sys == c->n_sys && hd.q == c->q && hd.n_sites == P.n_sites && hd.n_levels == P.n_levels &&
+              hd.hist_bins == P.hist_bins && hd.hist_range == P.hist_range;
     for (int k = 0; ok && k < c->n_sys; ++k) {
         lb_system_desc d;
         ok = std::fread(&d, sizeof(d), 1, fp) == 1 && std::memcmp(&d, &c->sys[k].d, sizeof(d)) == 0;
@@ -961,9 +1098,11 @@ lb_status lb_load(lb_ctx* c, const char* path) {
     const size_t es = c->fp32 ? 4 : 8;
     std::vector<char> pop(es * c->q * P.n_sites);
     std::vector<double> acc(7 * P.n_levels), glob(8 * c->n_sys);
+    std::vector<uint64_t> hist(hist_bytes(P) / sizeof(uint64_t));
     ok = ok && std::fread(pop.data(), 1, pop.size(), fp) == pop.size();
     ok = ok && std::fread(acc.data(), sizeof(double), acc.size(), fp) == acc.size();
     ok = ok && std::fread(glob.data(), sizeof(double), glob.size(), fp) == glob.size();
+    ok = ok && std::fread(hist.data(), sizeof(uint64_t), hist.size(), fp) == hist.size();
     std::fclose(fp);
     if (!ok) return LB_ERR_IO;
     drop_graphs(c);
@@ -973,6 +1112,8 @@ lb_status lb_load(lb_ctx* c, const char* path) {
                              c->stream));
     LB_CHECK(cudaMemcpyAsync(c->ws + P.glob, glob.data(), sizeof(double) * glob.size(), cudaMemcpyHostToDevice,
                              c->stream));
+    if (!hist.empty())
+        LB_CHECK(cudaMemcpyAsync(c->ws + P.hist, hist.data(), hist_bytes(P), cudaMemcpyHostToDevice, c->stream));
     LB_CHECK(cudaMemcpyAsync(c->ws + P.step, &c->step, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
     LB_CHECK(cudaMemsetAsync(c->ws + P.status, 0, sizeof(int), c->stream));
     LB_CHECK(cudaStreamSynchronize(c->stream));

@@ -75,6 +75,14 @@ struct ObsItem {            // a range of blocks of one level
     int32_t rec, rec2;      // partial records written (rec2 for the unit level)
 };
 
+// Order-parameter histograms: per level (nbins + 2) counts [under, bins, over]
+// at counts + level * (nbins + 2); nbins = 0 disables them.
+struct HistDev {
+    unsigned long long* counts;
+    int32_t nbins;
+    double lo, inv_w;       // bin of m: floor((m - lo) * inv_w), inv_w = nbins / (hi - lo)
+};
+
 cudaError_t launch_init_noise(const SysDev* sys, const int4* items, int n_items, double amp, double* d,
                               double* partial, cudaStream_t st);
 cudaError_t launch_reduce_sys(const SysSpan* spans, int n_sys, const double* partial, int K, double* out,
@@ -84,9 +92,9 @@ cudaError_t launch_obs_globals(const SysDev* sys, int n_sys, const double* red4,
 cudaError_t launch_set_dbar(const SysDev* sys, int n_sys, double* dbar, cudaStream_t st);
 cudaError_t launch_pyr_bottom(const SysDev* sys, const LevelDev* lv, const ObsItem* items, int n_items,
                               const double* d, const double* dbar, double* S, double* E, double* rec,
-                              cudaStream_t st);
+                              const HistDev& hist, cudaStream_t st);
 cudaError_t launch_pyr_up(const SysDev* sys, const LevelDev* lv, const ObsItem* items, int n_items, int dims3,
-                          double* S, double* E, double* rec, cudaStream_t st);
+                          double* S, double* E, double* rec, const HistDev& hist, cudaStream_t st);
 cudaError_t launch_obs_accum(const LevelDev* lv, int n_levels_total, const double* rec, double* acc,
                              int* status, cudaStream_t st);
 cudaError_t launch_advance(int64_t* step, int64_t n, cudaStream_t st);

@@ -239,12 +239,13 @@ extern "C" lb_status lb_block_moments_noalloc(const double* d_rho, int nx, int n
     NA_CHECK(cudaGetLastError());
     NA_CHECK(launch_reduce_sys(reinterpret_cast<const SysSpan*>(base + o_span), 1, part, 4, red4, st));
     NA_CHECK(launch_obs_globals(dsys, 1, red4, dbar, reinterpret_cast<double*>(base + o_glob), 1, 0, st));
+    const HistDev no_hist{nullptr, 0, 0.0, 0.0};
     NA_CHECK(launch_pyr_bottom(dsys, dlv, reinterpret_cast<const ObsItem*>(base + o_bot), n_bottom, d_rho, dbar, S,
-                               E, recs, st));
+                               E, recs, no_hist, st));
     for (int u = 1; u <= imax; ++u) {
         const int first = up_first[u - 1], cnt = up_first[u] - first;
         NA_CHECK(launch_pyr_up(dsys, dlv, reinterpret_cast<const ObsItem*>(base + o_up) + first, cnt, dims3 ? 1 : 0,
-                               S, E, recs, st));
+                               S, E, recs, no_hist, st));
     }
     NA_CHECK(launch_obs_accum(dlv, nl, recs, acc, reinterpret_cast<int*>(base + o_stat), st));
     NA_CHECK(cudaMemcpyAsync(d_out, acc, sizeof(double) * 7 * nl, cudaMemcpyDeviceToDevice, st));

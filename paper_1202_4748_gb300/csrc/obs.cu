@@ -92,14 +92,36 @@ __device__ __forceinline__ void add_terms(double (&t)[REC], double s, double e, 
     t[5] += E * E;
 }
 
+// Histogram bin of a block value m: 1 + floor(t), t = (m - lo) * inv_w, with
+// 0 below the range and nbins + 1 at or above it (and for NaN).  The product
+// is formed from the rounded difference, as in the plain definition.
+__device__ __forceinline__ int hist_bin(double m, const HistDev& H) {
+    const double t = __dmul_rn(__dsub_rn(m, H.lo), H.inv_w);
+    if (t >= 0.0) return t < double(H.nbins) ? 1 + int(t) : H.nbins + 1;
+    return t < 0.0 ? 0 : H.nbins + 1;
+}
+
+// Per-CTA histograms in shared memory (32-bit counts; a CTA sees far fewer
+// than 2^32 values), added to the 64-bit global counts at the end.
+__device__ __forceinline__ void hist_clear(unsigned* sh, int n) {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) sh[k] = 0u;
+}
+__device__ __forceinline__ void hist_flush(const unsigned* sh, int n, unsigned long long* g) {
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+        if (sh[k]) atomicAdd(g + k, (unsigned long long)sh[k]);
+}
+
 // Bottom pyramid level: block sums of phi, phi^2 straight from the sites; the
-// separate single-site level (if any) is fed from the same loop.
+// separate single-site level (if any) is fed from the same loop.  With
+// histograms on, each block value m (and each site value of the single-site
+// level) is also binned.
 __global__ void __launch_bounds__(OBS_THREADS)
     pyr_bottom_kernel(const SysDev* __restrict__ sysv, const LevelDev* __restrict__ lvv,
                       const ObsItem* __restrict__ items, const double* __restrict__ d,
                       const double* __restrict__ dbar, double* __restrict__ Sg, double* __restrict__ Eg,
-                      double* __restrict__ rec) {
+                      double* __restrict__ rec, const HistDev H) {
     __shared__ double sh[REC * OBS_THREADS];
+    extern __shared__ unsigned shist[];          // [block level | single-site level], nbins + 2 each
     const ObsItem it = items[blockIdx.x];
     const LevelDev lv = lvv[it.level];
     const SysDev& S = sysv[lv.sys];
@@ -107,6 +129,13 @@ __global__ void __launch_bounds__(OBS_THREADS)
     const double db = dbar[lv.sys];
     const double inv_rbar = 1.0 / (S.rho_c + db);
     const double inv_v = 1.0 / (double(lv.bx) * lv.by * lv.bz);
+    const int nh = H.nbins + 2;
+    const bool hist = H.nbins > 0;
+    const bool hist_u = hist && it.unit_level >= 0;
+    if (hist) {
+        hist_clear(shist, hist_u ? 2 * nh : nh);
+        __syncthreads();
+    }
     double tb[REC] = {0, 0, 0, 0, 0, 0};
     double tu[REC] = {0, 0, 0, 0, 0, 0};
     for (int j = 0; j < BLOCKS_PER_THREAD; ++j) {
@@ -123,11 +152,13 @@ __global__ void __launch_bounds__(OBS_THREADS)
                     s += phi;
                     e += phi * phi;
                     if (it.unit_level >= 0) add_terms(tu, phi, phi * phi, 1.0);
+                    if (hist_u) atomicAdd(shist + nh + hist_bin(phi, H), 1u);
                 }
             }
         Sg[lv.off + b] = s;
         Eg[lv.off + b] = e;
         add_terms(tb, s, e, inv_v);
+        if (hist) atomicAdd(shist + hist_bin(s * inv_v, H), 1u);
     }
     block_sum<REC, OBS_THREADS>(tb, sh);
     if (threadIdx.x == 0)
@@ -138,17 +169,29 @@ __global__ void __launch_bounds__(OBS_THREADS)
         if (threadIdx.x == 0)
             for (int k = 0; k < REC; ++k) rec[int64_t(it.rec2) * REC + k] = tu[k];
     }
+    if (hist) {
+        __syncthreads();
+        hist_flush(shist, nh, H.counts + int64_t(it.level) * nh);
+        if (hist_u) hist_flush(shist + nh, nh, H.counts + int64_t(it.unit_level) * nh);
+    }
 }
 
 // One coarser level: each block sums its 2^d children of the next finer level.
 __global__ void __launch_bounds__(OBS_THREADS)
     pyr_up_kernel(const LevelDev* __restrict__ lvv, const ObsItem* __restrict__ items, int dims3,
-                  double* __restrict__ Sg, double* __restrict__ Eg, double* __restrict__ rec) {
+                  double* __restrict__ Sg, double* __restrict__ Eg, double* __restrict__ rec, const HistDev H) {
     __shared__ double sh[REC * OBS_THREADS];
+    extern __shared__ unsigned shist[];
     const ObsItem it = items[blockIdx.x];
     const LevelDev lv = lvv[it.level];
     const LevelDev ch = lvv[lv.child];
     const double inv_v = 1.0 / (double(lv.bx) * lv.by * lv.bz);
+    const int nh = H.nbins + 2;
+    const bool hist = H.nbins > 0;
+    if (hist) {
+        hist_clear(shist, nh);
+        __syncthreads();
+    }
     double tb[REC] = {0, 0, 0, 0, 0, 0};
     for (int j = 0; j < BLOCKS_PER_THREAD; ++j) {
         const int64_t b = it.b0 + int64_t(j) * OBS_THREADS + threadIdx.x;
@@ -167,10 +210,15 @@ __global__ void __launch_bounds__(OBS_THREADS)
         Sg[lv.off + b] = s;
         Eg[lv.off + b] = e;
         add_terms(tb, s, e, inv_v);
+        if (hist) atomicAdd(shist + hist_bin(s * inv_v, H), 1u);
     }
     block_sum<REC, OBS_THREADS>(tb, sh);
     if (threadIdx.x == 0)
         for (int k = 0; k < REC; ++k) rec[int64_t(it.rec) * REC + k] = tb[k];
+    if (hist) {
+        __syncthreads();
+        hist_flush(shist, nh, H.counts + int64_t(it.level) * nh);
+    }
 }
 
 // acc layout per level (7 doubles): n, sum m, m^2, |m|, m^4, e, e^2
@@ -222,16 +270,18 @@ cudaError_t launch_set_dbar(const SysDev* sys, int n_sys, double* dbar, cudaStre
 
 cudaError_t launch_pyr_bottom(const SysDev* sys, const LevelDev* lv, const ObsItem* items, int n_items,
                               const double* d, const double* dbar, double* S, double* E, double* rec,
-                              cudaStream_t st) {
+                              const HistDev& hist, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
-    pyr_bottom_kernel<<<n_items, OBS_THREADS, 0, st>>>(sys, lv, items, d, dbar, S, E, rec);
+    const size_t shm = hist.nbins > 0 ? 2 * sizeof(unsigned) * (hist.nbins + 2) : 0;
+    pyr_bottom_kernel<<<n_items, OBS_THREADS, shm, st>>>(sys, lv, items, d, dbar, S, E, rec, hist);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pyr_up(const SysDev*, const LevelDev* lv, const ObsItem* items, int n_items, int dims3,
-                          double* S, double* E, double* rec, cudaStream_t st) {
+                          double* S, double* E, double* rec, const HistDev& hist, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
-    pyr_up_kernel<<<n_items, OBS_THREADS, 0, st>>>(lv, items, dims3, S, E, rec);
+    const size_t shm = hist.nbins > 0 ? sizeof(unsigned) * (hist.nbins + 2) : 0;
+    pyr_up_kernel<<<n_items, OBS_THREADS, shm, st>>>(lv, items, dims3, S, E, rec, hist);
     return cudaGetLastError();
 }
 

@@ -143,3 +143,57 @@ def test_kernel_variant_table():
         lb.workspace_bytes([s], precision="fp32", variant=n + 1)
     assert e.value.status == lb.LB_ERR_UNSUPPORTED
     assert lb.workspace_bytes([s], precision="fp32", variant=n) > 0
+
+
+def _mixture_counts(lo, hi, nb, parts, n_total):
+    from scipy.special import ndtr
+    edges = lo + (hi - lo) * np.arange(nb + 1) / nb
+    cdf = sum(wt * ndtr((edges - mu) / sg) for wt, mu, sg in parts)
+    c = np.rint(n_total * np.diff(cdf)).astype(np.int64)
+    return np.concatenate([[17], c, [5]]).astype(np.uint64)
+
+
+@pytest.mark.parametrize("case", ["two", "one", "cut", "flat"])
+def test_histogram_estimates_match_oracle(case):
+    import paper_1202_4748_gb300 as lb
+    from oracle import observables as ob
+    lo, hi = -0.4, 0.4
+    if case == "two":
+        c = _mixture_counts(lo, hi, 640, [(0.5, 0.21, 0.01), (0.5, -0.21, 0.012)], 10 ** 9)
+        kw = dict(vol=64.0, kT=1e-4)
+    elif case == "one":
+        c = _mixture_counts(lo, hi, 801, [(1.0, 0.001, 0.05)], 10 ** 8)
+        kw = dict(vol=1.0, kT=2e-4)
+    elif case == "cut":
+        c = _mixture_counts(lo, hi, 640, [(0.45, 0.2, 0.01), (0.45, -0.2, 0.01), (0.1, 0.0, 0.2)], 10 ** 9)
+        kw = dict(vol=8.0, kT=1e-4, m_cut=0.1, frac=0.3)
+    else:
+        c = np.ones(66, dtype=np.uint64)
+        kw = dict(vol=8.0, kT=1e-4)
+    got = lb.histogram_estimates(c, lo, hi, **kw)
+    want = ob.histogram_estimates(c.astype(np.int64), lo, hi, **kw)
+    for k in lb.HIST_EST_FIELDS:
+        g, w = got[k], want[k]
+        if isinstance(w, float) and np.isnan(w):
+            assert np.isnan(g), k
+        else:
+            assert g == pytest.approx(w, rel=1e-9, abs=1e-12), k
+
+
+def test_histogram_estimates_and_options_rejected():
+    import paper_1202_4748_gb300 as lb
+    c = np.ones(10, dtype=np.uint64)
+    for args in [(-0.5, 0.6, 1.0, 1e-4), (-0.5, 0.5, 0.0, 1e-4), (-0.5, 0.5, 1.0, 0.0)]:
+        with pytest.raises(lb.LBError):
+            lb.histogram_estimates(c, *args)
+    with pytest.raises(lb.LBError):
+        lb.histogram_estimates(c, -0.5, 0.5, 1.0, 1e-4, frac=1.5)
+    s = synth.system("D2Q9", n=16)
+    for kw in [dict(hist_bins=lb.LB_MAX_HIST_BINS + 1, hist_range=0.5), dict(hist_bins=8, hist_range=0.0),
+               dict(hist_bins=-1, hist_range=0.5), dict(hist_bins=8, hist_range=float("inf"))]:
+        with pytest.raises(lb.LBError) as e:
+            lb.workspace_bytes([s], **kw)
+        assert e.value.status == lb.LB_ERR_ARG
+    base = lb.workspace_bytes([s])
+    # 5 levels (16, 8, 4, 2, 1) of 102 64-bit counts, up to one alignment unit of slack
+    assert lb.workspace_bytes([s], hist_bins=100, hist_range=0.5) >= base + 8 * 102 * 5 - 256
