@@ -24,11 +24,28 @@ floor(t) with t = (m - lo) * (nbins / (hi - lo)) evaluated in FP64, below lo to
 an underflow count and at or above hi (or NaN) to an overflow count.  From a
 histogram symmetric about m = 0 the estimators of Sec. IV (order-parameter
 distribution results) are: M_L as the position of the maximum of P_L, chi_L
-from the peak height through the Gaussian forms of P_L (one central peak:
+from the peak height through the Gaussian forms of P_L (Eqs. 57 and 58; one central peak:
 chi_L = L^d / (2 pi kT P_max^2); two displaced peaks, each carrying half the
 weight: chi_L = L^d / (8 pi kT P_max^2)), and chi_L from the variance of a
 Gaussian fitted to the peak (chi_L = L^d sigma^2 / kT), after an optional
 central region |m| < m_cut is set to zero (also in the normalisation).
+
+Momentum spectra (Sec. III D, equilibration of momentum, and Eq. 69): the fluid
+momentum j = rho u of the collision (j = sum_i c_i f_i with the modified
+equilibrium; j + F/2 with the Guo force F = kappa rho grad lap rho), its DFT
+J_a(k) = sum_r j_a(r) e^{-i k.r}, and per k the three spectra |J_x|^2 / N,
+|khat . J|^2 / N (longitudinal) and (|J|^2 - |khat . J|^2) / (N (d - 1))
+(transverse, per component), with khat = n / |n| for k = 2 pi n / S (n wrapped
+as below; both projections are 0 at k = 0).  In equilibrium each equals
+rho_0 kT (Eq. 69).  They are accumulated on the structure-factor schedule and
+binned in the same shells.
+
+Ornstein-Zernike fit (Eq. 25 with the lattice Laplacian's symbol for k^2, as
+Sec. IV requires): on shells 1..kmax, 1 / C_j = a + b k2_j by weighted least
+squares, with C_j the shell mean of C, k2_j the shell mean of the symbol
+6 sum_i t_i (1 - cos k.c_i), and weights (points in shell) x C_j^2 (the inverse
+variance of 1 / C_j when C_j has relative error ~ 1/sqrt(points)); then
+chi = 1 / (kT a) and xi = sqrt(b / a).
 
 Structure factor (Eq. 80): C(k) = N^-1 |sum_r phi(r) exp(-i k.r)|^2, with the
 discrete Fourier transform taken by numpy's FFT (a library primitive).  Shell
@@ -231,6 +248,81 @@ def histogram_estimates(counts, lo, hi, vol, kT, m_cut=0.0, frac=0.2):
     return out
 
 
+def fluid_momentum(f, p):
+    """rho u as the collision defines it (see module docstring); shape (3, nz, ny, nx)."""
+    j = lbm.momentum(f, p.lat)
+    if p.coupling == "guo":
+        rho = lbm.density(f)
+        j = j + 0.5 * p.kappa * rho * lbm.gradient(lbm.laplacian(rho, p.lat), p.lat)
+    return j
+
+
+def wavevectors(shape):
+    """Integer wavevector components (n_x, n_y, n_z), each wrapped to [-S/2, S/2), on a (nz, ny, nx) grid."""
+    nz, ny, nx = shape
+    out = []
+    for ax, n in ((2, nx), (1, ny), (0, nz)):
+        idx = np.arange(n)
+        idx = np.where(2 * idx < n, idx, idx - n)
+        shp = [1, 1, 1]
+        shp[ax] = n
+        out.append(np.broadcast_to(idx.reshape(shp), shape).astype(np.float64))
+    return out
+
+
+def momentum_spectra(f, p):
+    """(3, nz, ny, nx): |J_x|^2 / N, longitudinal and transverse spectra per k (module docstring)."""
+    return spectra_of_momentum(fluid_momentum(f, p), p.lat.d)
+
+
+def spectra_of_momentum(j, d):
+    """The three spectra of a momentum field j (shape (3, nz, ny, nx)) in d dimensions."""
+    shape = j.shape[1:]
+    N = float(np.prod(shape))
+    J = [np.fft.fftn(j[a]) for a in range(d)]
+    nvec = wavevectors(shape)[:d]
+    nn = np.sqrt(sum(n * n for n in nvec))
+    safe = np.where(nn > 0, nn, 1.0)
+    par = sum((n / safe) * Ja for n, Ja in zip(nvec, J))
+    tot = sum(np.abs(Ja) ** 2 for Ja in J)
+    p2 = np.abs(par) ** 2
+    out = np.zeros((3,) + shape)
+    out[0] = np.abs(J[0]) ** 2 / N
+    out[1] = np.where(nn > 0, p2 / N, 0.0)
+    out[2] = np.where(nn > 0, (tot - p2) / (N * (d - 1)), 0.0)
+    return out
+
+
+def laplacian_symbol(shape, lat):
+    """k^2 of the lattice Laplacian: 6 sum_i t_i (1 - cos k.c_i), k = 2 pi n / S."""
+    nz, ny, nx = shape
+    nvec = wavevectors(shape)
+    k = [2.0 * np.pi * n / s for n, s in zip(nvec, (nx, ny, nz))]
+    out = np.zeros(shape)
+    for i in range(1, lat.q):
+        kc = sum(k[a] * float(lat.c[i][a]) for a in range(3))
+        out += 6.0 * lat.t[i] * (1.0 - np.cos(kc))
+    return out
+
+
+def oz_fit(sk_sum, counts, n_samples, shape, lat, kT, kmax):
+    """Ornstein-Zernike fit of a shell-binned C(k) (module docstring): dict(chi, xi, a, b, shells)."""
+    k2sum, k2cnt = bin_shells(laplacian_symbol(shape, lat), shape, kmax)
+    sk_sum = np.asarray(sk_sum, dtype=np.float64)[:kmax]
+    counts = np.asarray(counts, dtype=np.float64)[:kmax]
+    if not np.array_equal(counts, k2cnt):
+        raise ValueError("shell counts do not belong to this lattice")
+    use = counts > 0
+    C = sk_sum[use] / (counts[use] * n_samples)
+    x = k2sum[use] / counts[use]
+    y = 1.0 / C
+    wt = counts[use] * C * C
+    A = np.stack([np.ones_like(x), x], axis=1)
+    a, b = np.linalg.solve(A.T @ (wt[:, None] * A), A.T @ (wt * y))
+    xi = float(np.sqrt(b / a)) if a > 0 and b >= 0 else float("nan")
+    return dict(chi=1.0 / (kT * a), xi=xi, a=float(a), b=float(b), shells=int(use.sum()))
+
+
 class Recorder:
     """Accumulates block observables (and optionally C(k)) every ``every`` steps.
 
@@ -238,7 +330,7 @@ class Recorder:
     Also records the FP64 mass sum rho and momentum sum j at each sample.
     """
 
-    def __init__(self, p, every, sk_every=0, hist=None):
+    def __init__(self, p, every, sk_every=0, hist=None, jk=False):
         self.p = p
         self.lv = levels(p)
         self.every = every
@@ -247,6 +339,7 @@ class Recorder:
         self.hist = np.zeros((len(self.lv), hist[0] + 2), dtype=np.int64) if hist else None
         self.acc = np.zeros((len(self.lv), len(ACC_FIELDS)))
         self.ck = np.zeros(p.shape)
+        self.jk = np.zeros((3,) + p.shape) if jk else None
         self.n_sk = 0
         self.mass = []
         self.mom = []
@@ -262,4 +355,6 @@ class Recorder:
             self.mom.append(lbm.momentum(f, self.p.lat).reshape(3, -1).sum(axis=1))
         if self.sk_every > 0 and t > 0 and t % self.sk_every == 0:
             self.ck += structure_factor(order_parameter(f))
+            if self.jk is not None:
+                self.jk += momentum_spectra(f, self.p)
             self.n_sk += 1

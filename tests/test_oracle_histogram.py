@@ -1,9 +1,9 @@
 """Pins of the oracle's order-parameter histograms P_L(m) and their estimators.
 
 The estimators are checked against histograms built from the closed forms of
-P_L in Sec. II D: one Gaussian about m = 0 (Eq. for the disordered phase) and
-two displaced Gaussians of half weight each (Eq. for coexistence), both with
-known L^d, kT, chi_L and M_L.  Expected bin counts are exact integrals of
+P_L in Sec. II D: one Gaussian about m = 0 (Eq. 57, disordered phase) and two
+displaced Gaussians of half weight each (Eq. 58, coexistence), both with known
+L^d, kT, chi_L and M_L.  Expected bin counts are exact integrals of
 those densities (normal CDF differences), so the only errors left are the
 binning errors, which are estimated in each test.
 """
