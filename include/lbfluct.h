@@ -109,6 +109,9 @@ typedef struct {
  *               level into hist_bins equal bins on [-hist_range, hist_range)
  *               (plus under/overflow counts); 0 disables, at most
  *               LB_MAX_HIST_BINS.
+ *   jk_spectra  1: every structure-factor sample also accumulates the
+ *               momentum spectra of lb_momentum_spectra (needs sk_every > 0);
+ *               0: off.
  *   hist_range  half-width of the histogram range (> 0 when hist_bins > 0). */
 #define LB_MAX_HIST_BINS 4096
 typedef struct {
@@ -120,6 +123,7 @@ typedef struct {
     int32_t occupancy;
     int32_t variant;
     int32_t hist_bins;
+    int32_t jk_spectra;
     double hist_range;
 } lb_run_opts;
 
@@ -237,6 +241,36 @@ lb_status lb_histogram_estimates(const uint64_t* counts, int nbins, double lo, d
  * Errors: LB_ERR_ARG, LB_ERR_UNSUPPORTED (sk_every == 0). */
 lb_status lb_structure_factor(lb_ctx* ctx, int sys, double* h_sum, int64_t* h_count, int nbins,
                               int64_t* n_samples);
+
+/* Momentum spectra accumulated on the sk_every schedule when jk_spectra = 1
+ * (the equilibration check of Sec. III D against Eq. 69, <|j_a(k)|^2> =
+ * rho_0 kT): with j = rho u the fluid momentum of the collision (sum_i c_i f_i
+ * for LB_MODEQ; plus F/2, F = kappa rho grad lap rho, for LB_GUO), J_a(k) =
+ * sum_r j_a(r) exp(-i k.r), N the sites and khat = n / |n| for k = 2 pi n / S,
+ * shell j = 1..nbins (as lb_structure_factor) receives
+ *   h_sum[0 * nbins + j - 1]  sum of |J_x|^2 / N
+ *   h_sum[1 * nbins + j - 1]  sum of |khat . J|^2 / N            (longitudinal)
+ *   h_sum[2 * nbins + j - 1]  sum of (|J|^2 - |khat . J|^2) / (N (d - 1))
+ *                                                   (transverse, per component)
+ * over samples and shell points; h_count and *n_samples as in
+ * lb_structure_factor.  Synchronises.  Errors: LB_ERR_ARG, LB_ERR_UNSUPPORTED
+ * (jk_spectra == 0), device errors, LB_ERR_CUDA. */
+lb_status lb_momentum_spectra(lb_ctx* ctx, int sys, double* h_sum, int64_t* h_count, int nbins,
+                              int64_t* n_samples);
+
+/* Ornstein-Zernike fit of a shell-binned structure factor (Eq. 25 with k^2
+ * the symbol of the lattice Laplacian, 6 sum_i t_i (1 - cos k.c_i), as the
+ * text after Eq. 80 requires), pure host arithmetic.  Inputs: lattice
+ * (LB_D2Q9 / LB_D3Q19), side S of the square / cubic system, the shell sums and
+ * counts of lb_structure_factor for shells 1..kmax, the number of samples and
+ * kT.  With C_j = h_sum / (h_count n_samples) and k2_j the shell mean of the
+ * symbol, fits 1 / C_j = a + b k2_j by least squares weighted by
+ * h_count C_j^2, and writes out[0] chi = 1 / (kT a), out[1] xi = sqrt(b / a)
+ * (NaN unless a > 0 and b >= 0), out[2] a, out[3] b, out[4] shells used.
+ * Errors: LB_ERR_ARG (side < 2, kmax < 2, counts that do not match the
+ * lattice's shells, non-positive C_j, kT <= 0, fewer than 2 shells). */
+lb_status lb_oz_fit(int lattice, int side, const double* h_sum, const int64_t* h_count, int kmax,
+                    int64_t n_samples, double kT, double out[5]);
 
 /* Copy f_i(r, t) of system `sys` to h_f (float64 [q][nz][ny][nx]).  Synchronises.
  * Errors: LB_ERR_ARG, LB_ERR_CUDA. */

@@ -49,7 +49,7 @@ class lb_run_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("obs_every", ctypes.c_int32),
                 ("sk_every", ctypes.c_int32), ("graph_chunk", ctypes.c_int32),
                 ("tile", ctypes.c_int32 * 3), ("occupancy", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("hist_bins", ctypes.c_int32), ("hist_range", ctypes.c_double)]
+                ("hist_bins", ctypes.c_int32), ("jk_spectra", ctypes.c_int32), ("hist_range", ctypes.c_double)]
 
 
 class lb_obs_level(ctypes.Structure):
@@ -82,6 +82,9 @@ _SIG = {
                                     ctypes.POINTER(ctypes.c_double)]),
     "lb_histogram_estimates": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double, ctypes.c_double, _P]),
+    "lb_momentum_spectra": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+    "lb_oz_fit": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                                 _P]),
     "lb_structure_factor": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
     "lb_read_fields": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "lb_write_fields": (ctypes.c_int, [_P, ctypes.c_int, _P]),
@@ -141,7 +144,7 @@ def make_desc(systems):
 
 
 def make_opts(precision="fp64", obs_every=0, sk_every=0, graph_chunk=0, tile=(0, 0, 0), occupancy=0, variant=0,
-              hist_bins=0, hist_range=0.0):
+              hist_bins=0, hist_range=0.0, jk_spectra=False):
     o = lb_run_opts()
     o.precision = {"fp64": LB_FP64, "fp32": LB_FP32_DEVIATION}.get(precision, precision)
     o.obs_every, o.sk_every, o.graph_chunk = int(obs_every), int(sk_every), int(graph_chunk)
@@ -151,7 +154,19 @@ def make_opts(precision="fp64", obs_every=0, sk_every=0, graph_chunk=0, tile=(0,
     o.variant = int(variant)
     o.hist_bins = int(hist_bins)
     o.hist_range = float(hist_range)
+    o.jk_spectra = 1 if jk_spectra else 0
     return o
+
+
+def oz_fit(lattice, side, sums, counts, n_samples, kT, kmax):
+    """Ornstein-Zernike fit of shell-binned C(k) (lb_oz_fit): dict(chi, xi, a, b, shells)."""
+    code = _LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
+    s = np.ascontiguousarray(sums[:kmax], dtype=np.float64)
+    c = np.ascontiguousarray(counts[:kmax], dtype=np.int64)
+    out = (ctypes.c_double * 5)()
+    check(lb_oz_fit(code, int(side), s.ctypes.data_as(_P), c.ctypes.data_as(_P), int(kmax), int(n_samples),
+                    float(kT), out), "lb_oz_fit")
+    return dict(chi=out[0], xi=out[1], a=out[2], b=out[3], shells=int(out[4]))
 
 
 HIST_EST_FIELDS = ("m_max", "P_max", "chi_peak", "M_fit", "sigma2_fit", "chi_fit", "n_fit", "central",
@@ -273,6 +288,15 @@ class Ensemble:
         check(lb_structure_factor(self.ctx, k, s.ctypes.data_as(_P), c.ctypes.data_as(_P), nbins,
                                   ctypes.byref(ns)), "lb_structure_factor")
         return s, c, ns.value
+
+    def momentum_spectra(self, k, nbins):
+        """(sums (3, nbins): x, longitudinal, transverse; counts; samples) of system ``k``."""
+        s = np.zeros(3 * nbins)
+        c = np.zeros(nbins, dtype=np.int64)
+        ns = ctypes.c_int64()
+        check(lb_momentum_spectra(self.ctx, k, s.ctypes.data_as(_P), c.ctypes.data_as(_P), nbins,
+                                  ctypes.byref(ns)), "lb_momentum_spectra")
+        return s.reshape(3, nbins), c, ns.value
 
     def read_fields(self, k):
         out = np.empty((self.q,) + self.shape(k), dtype=np.float64)

@@ -5,6 +5,7 @@
 // items), order the launches on the caller's stream, optionally capture step
 // chunks in CUDA graphs, and move data between host and device for I/O.
 // Every arithmetic step of the method runs in the kernels.
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -40,7 +41,9 @@ struct SysHost {
 // Byte offsets of every region inside the workspace.
 struct Plan {
     size_t sys, phys, tiles, pop0, pop1, step, status, d, dbar, site_items, site_partial, spans, red4, glob, levels,
-        S, E, bottom_items, up_items, rec, acc, hist, field_tmp, sk_sys, sk_tw, sk_acc, sk_b0, sk_b1, sk_bins, total;
+        S, E, bottom_items, up_items, rec, acc, hist, field_tmp, sk_sys, sk_tw, sk_acc, sk_b0, sk_b1, sk_bins, jk_j,
+        jk_lap, jk_F, jk_acc, total;
+    bool jk = false;
     int hist_bins = 0;
     double hist_range = 0.0;
     int n_tiles = 0, n_site_items = 0, n_levels = 0, n_bottom = 0, n_up = 0, n_rec = 0, max_depth = 0;
@@ -64,6 +67,7 @@ lb_status validate(const lb_system_desc* s, int n, const lb_run_opts* o) {
     if (o->precision != LB_FP64 && o->precision != LB_FP32_DEVIATION) return LB_ERR_ARG;
     if (o->obs_every < 0 || o->sk_every < 0 || o->graph_chunk < 0 || (o->graph_chunk & 1)) return LB_ERR_ARG;
     if (o->hist_bins < 0 || o->hist_bins > LB_MAX_HIST_BINS) return LB_ERR_ARG;
+    if (o->jk_spectra != 0 && (o->jk_spectra != 1 || o->sk_every == 0)) return LB_ERR_ARG;
     if (o->hist_bins > 0 && !(o->hist_range > 0 && std::isfinite(o->hist_range))) return LB_ERR_ARG;
     for (int k = 0; k < n; ++k) {
         const lb_system_desc& d = s[k];
@@ -346,6 +350,13 @@ lb_status make_plan(const lb_system_desc* s, int n, const lb_run_opts* o, std::v
     P.sk_b0 = take(sizeof(double) * 2 * skn);
     P.sk_b1 = take(sizeof(double) * 2 * skn);
     P.sk_bins = take(sizeof(double) * 2 * P.sk_max_bins);
+    // momentum spectra: j (3 fields), Laplacian scratch (Guo), transforms (3 complex fields), accumulators
+    P.jk = P.sk && o->jk_spectra == 1;
+    const int64_t jkn = P.jk ? P.n_sites : 0;
+    P.jk_j = take(sizeof(double) * 3 * jkn);
+    P.jk_lap = take(sizeof(double) * jkn);
+    P.jk_F = take(sizeof(double) * 6 * jkn);
+    P.jk_acc = take(sizeof(double) * 3 * jkn);
     P.total = off;
     return LB_OK;
 }
@@ -455,15 +466,17 @@ size_t hist_bytes(const Plan& P) {
 }
 
 // Observable sample of the state held in population buffer `buf`.
-cudaError_t sample_obs(lb_ctx* c, int buf, bool set_mass0, bool count) {
+// With want_j the site pass also writes the momentum field (for the momentum spectra).
+cudaError_t sample_obs(lb_ctx* c, int buf, bool set_mass0, bool count, bool want_j = false) {
     const Plan& P = c->P;
     cudaError_t e;
     const SysDev* sys = c->at<SysDev>(P.sys);
+    double* jout = want_j && P.jk ? c->at<double>(P.jk_j) : nullptr;
     e = c->lattice == LB_D2Q9
             ? launch_obs_site_d2q9(c->fp32, sys, c->at<int4>(P.site_items), P.n_site_items, c->pop(buf),
-                                   c->at<double>(P.d), c->at<double>(P.site_partial), c->stream)
+                                   c->at<double>(P.d), c->at<double>(P.site_partial), jout, P.n_sites, c->stream)
             : launch_obs_site_d3q19(c->fp32, sys, c->at<int4>(P.site_items), P.n_site_items, c->pop(buf),
-                                    c->at<double>(P.d), c->at<double>(P.site_partial), c->stream);
+                                    c->at<double>(P.d), c->at<double>(P.site_partial), jout, P.n_sites, c->stream);
     if (e != cudaSuccess) return e;
     e = launch_reduce_sys(c->at<SysSpan>(P.spans), c->n_sys, c->at<double>(P.site_partial), 4, c->at<double>(P.red4),
                           c->stream);
@@ -493,13 +506,55 @@ cudaError_t sample_obs(lb_ctx* c, int buf, bool set_mass0, bool count) {
                             c->at<int>(P.status), c->stream);
 }
 
+// Momentum spectra of the momentum field the site pass just wrote: Guo
+// half-force, then per component x, y (and z) transforms, then accumulation.
+cudaError_t sample_jk(lb_ctx* c) {
+    const Plan& P = c->P;
+    cudaError_t e;
+    const SysDev* sys = c->at<SysDev>(P.sys);
+    const SkSys* sk = c->at<SkSys>(P.sk_sys);
+    const int4* items = c->at<int4>(P.site_items);
+    const int n_items = P.n_site_items;
+    const int64_t ns = P.n_sites;
+    double* j = c->at<double>(P.jk_j);
+    double* F = c->at<double>(P.jk_F);
+    double* b0 = c->at<double>(P.sk_b0);
+    double* b1 = c->at<double>(P.sk_b1);
+    const double* tw = c->at<double>(P.sk_tw);
+    const bool d3 = c->lattice == LB_D3Q19;
+    const int dims = d3 ? 3 : 2;
+    if (c->coupling == LB_GUO) {
+        e = launch_jk_guo_force(d3 ? 1 : 0, sys, items, n_items, c->at<double>(P.d), c->at<double>(P.jk_lap), j, ns,
+                                c->stream);
+        if (e != cudaSuccess) return e;
+        c->launches += 2;
+    }
+    for (int a = 0; a < dims; ++a) {
+        double* Fa = F + 2 * ns * a;
+        e = launch_sk_x(sys, sk, items, n_items, j + ns * a, nullptr, tw, b0, c->stream);
+        if (e != cudaSuccess) return e;
+        e = launch_sk_pass(sk, items, n_items, 1, tw, b0, d3 ? b1 : Fa, c->stream);
+        if (e != cudaSuccess) return e;
+        c->launches += 2;
+        if (d3) {
+            e = launch_sk_pass(sk, items, n_items, 2, tw, b1, Fa, c->stream);
+            if (e != cudaSuccess) return e;
+            c->launches += 1;
+        }
+    }
+    c->launches += 1;
+    return launch_jk_accum(sk, items, n_items, dims, F, F + 2 * ns, d3 ? F + 4 * ns : nullptr,
+                           c->at<double>(P.jk_acc), ns, c->stream);
+}
+
 // Structure-factor sample of the state in buffer `buf`; `have_d` when the
-// observable pass of the same step has already filled d and dbar.
+// observable pass of the same step has already filled d and dbar (and, with
+// momentum spectra on, the momentum field).
 cudaError_t sample_sk(lb_ctx* c, int buf, bool have_d) {
     const Plan& P = c->P;
     cudaError_t e;
     if (!have_d) {
-        e = sample_obs(c, buf, false, false);
+        e = sample_obs(c, buf, false, false, true);
         if (e != cudaSuccess) return e;
     }
     const SysDev* sys = c->at<SysDev>(P.sys);
@@ -521,7 +576,9 @@ cudaError_t sample_sk(lb_ctx* c, int buf, bool have_d) {
         c->launches += 1;
     }
     c->launches += 1;
-    return launch_sk_accum(sk, items, P.n_site_items, fin, c->at<double>(P.sk_acc), c->stream);
+    e = launch_sk_accum(sk, items, P.n_site_items, fin, c->at<double>(P.sk_acc), c->stream);
+    if (e != cudaSuccess || !P.jk) return e;
+    return sample_jk(c);
 }
 
 // Launch `n` steps starting at host step c->step (device counter must equal it).
@@ -546,11 +603,12 @@ cudaError_t launch_steps(lb_ctx* c, int64_t n) {
         c->launches += 1;
         const int64_t t1 = t + 1;
         const bool obs_due = c->opts.obs_every > 0 && t1 % c->opts.obs_every == 0;
+        const bool sk_due = c->opts.sk_every > 0 && t1 % c->opts.sk_every == 0;
         if (obs_due) {
-            e = sample_obs(c, int(t1 & 1), false, true);
+            e = sample_obs(c, int(t1 & 1), false, true, sk_due);
             if (e != cudaSuccess) return e;
         }
-        if (c->opts.sk_every > 0 && t1 % c->opts.sk_every == 0) {
+        if (sk_due) {
             e = sample_sk(c, int(t1 & 1), obs_due);
             if (e != cudaSuccess) return e;
         }
@@ -591,6 +649,7 @@ lb_status reset_accumulators(lb_ctx* c) {
     LB_CHECK(cudaMemsetAsync(c->ws + P.glob, 0, sizeof(double) * 8 * c->n_sys, c->stream));
     LB_CHECK(cudaMemsetAsync(c->ws + P.status, 0, sizeof(int), c->stream));
     if (P.sk) LB_CHECK(cudaMemsetAsync(c->ws + P.sk_acc, 0, sizeof(double) * P.n_sites, c->stream));
+    if (P.jk) LB_CHECK(cudaMemsetAsync(c->ws + P.jk_acc, 0, sizeof(double) * 3 * P.n_sites, c->stream));
     return LB_OK;
 }
 
@@ -992,6 +1051,107 @@ lb_status lb_structure_factor(lb_ctx* c, int sys, double* h_sum, int64_t* h_coun
     return s;
 }
 
+lb_status lb_momentum_spectra(lb_ctx* c, int sys, double* h_sum, int64_t* h_count, int nbins, int64_t* n_samples) {
+    if (!c || sys < 0 || sys >= c->n_sys || nbins < 0 || (nbins > 0 && (!h_sum || !h_count))) return LB_ERR_ARG;
+    const Plan& P = c->P;
+    if (!P.jk) return LB_ERR_UNSUPPORTED;
+    if (nbins > P.sk_max_bins) return LB_ERR_ARG;
+    double* bins = c->at<double>(P.sk_bins);
+    std::vector<double> hb(2 * size_t(P.sk_max_bins));
+    for (int comp = 0; comp < 3 && nbins > 0; ++comp) {
+        LB_CHECK(launch_sk_bin(c->at<SkSys>(P.sk_sys), sys, c->at<double>(P.jk_acc) + int64_t(comp) * P.n_sites,
+                               nbins, bins, bins + P.sk_max_bins, c->stream));
+        LB_CHECK(cudaMemcpyAsync(hb.data(), bins, sizeof(double) * 2 * P.sk_max_bins, cudaMemcpyDeviceToHost,
+                                 c->stream));
+        LB_CHECK(cudaStreamSynchronize(c->stream));
+        for (int j = 0; j < nbins; ++j) {
+            h_sum[int64_t(comp) * nbins + j] = hb[j];
+            h_count[j] = int64_t(hb[P.sk_max_bins + j]);
+        }
+    }
+    lb_status st = sync_and_check(c);
+    if (n_samples) *n_samples = c->step / c->opts.sk_every;
+    return st;
+}
+
+lb_status lb_oz_fit(int lattice, int side, const double* h_sum, const int64_t* h_count, int kmax, int64_t n_samples,
+                    double kT, double out[5]) {
+    if ((lattice != LB_D2Q9 && lattice != LB_D3Q19) || side < 2 || !h_sum || !h_count || !out || kmax < 2 ||
+        n_samples <= 0 || !(kT > 0))
+        return LB_ERR_ARG;
+    // shell means of the Laplacian symbol, enumerating the k grid of the lattice
+    const bool d3 = lattice == LB_D3Q19;
+    static const int c2[9][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
+                                 {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+    std::vector<std::array<int, 3>> vel;
+    std::vector<double> wt;
+    if (d3) {
+        for (int x = -1; x <= 1; ++x)
+            for (int y = -1; y <= 1; ++y)
+                for (int z = -1; z <= 1; ++z) {
+                    const int n2 = x * x + y * y + z * z;
+                    if (n2 == 1 || n2 == 2) {
+                        vel.push_back({x, y, z});
+                        wt.push_back(n2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+                    }
+                }
+    } else {
+        for (int i = 1; i < 9; ++i) {
+            vel.push_back({c2[i][0], c2[i][1], c2[i][2]});
+            wt.push_back(i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+        }
+    }
+    std::vector<double> ksum(kmax, 0.0);
+    std::vector<int64_t> kcnt(kmax, 0);
+    const int nzk = d3 ? side : 1;
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int kz = 0; kz < nzk; ++kz)
+        for (int ky = 0; ky < side; ++ky)
+            for (int kx = 0; kx < side; ++kx) {
+                const int64_t a = 2 * kx < side ? kx : kx - side, b = 2 * ky < side ? ky : ky - side,
+                              cz = d3 ? (2 * kz < side ? kz : kz - side) : 0;
+                const int64_t n2 = a * a + b * b + cz * cz;
+                if (n2 == 0) continue;
+                int64_t j = int64_t(std::floor(std::sqrt(double(n2))));
+                while (j * (j + 1) < n2) ++j;
+                while (j > 0 && j * (j - 1) >= n2) --j;
+                if (j < 1 || j > kmax) continue;
+                double sym = 0.0;
+                for (size_t i = 0; i < vel.size(); ++i) {
+                    const double kc = two_pi * (double(a) * vel[i][0] + double(b) * vel[i][1] + double(cz) * vel[i][2]) /
+                                      side;
+                    sym += 6.0 * wt[i] * (1.0 - std::cos(kc));
+                }
+                ksum[j - 1] += sym;
+                kcnt[j - 1] += 1;
+            }
+    double A00 = 0, A01 = 0, A11 = 0, r0 = 0, r1 = 0;
+    int used = 0;
+    for (int j = 0; j < kmax; ++j) {
+        if (h_count[j] != kcnt[j]) return LB_ERR_ARG;
+        if (kcnt[j] == 0) continue;
+        const double C = h_sum[j] / (double(h_count[j]) * double(n_samples));
+        if (!(C > 0)) return LB_ERR_ARG;
+        const double x = ksum[j] / double(kcnt[j]), y = 1.0 / C, w = double(h_count[j]) * C * C;
+        A00 += w;
+        A01 += w * x;
+        A11 += w * x * x;
+        r0 += w * y;
+        r1 += w * x * y;
+        ++used;
+    }
+    if (used < 2) return LB_ERR_ARG;
+    const double det = A00 * A11 - A01 * A01;
+    if (!(det != 0)) return LB_ERR_ARG;
+    const double a = (r0 * A11 - r1 * A01) / det, b = (A00 * r1 - A01 * r0) / det;
+    out[0] = 1.0 / (kT * a);
+    out[1] = (a > 0 && b >= 0) ? std::sqrt(b / a) : NAN;
+    out[2] = a;
+    out[3] = b;
+    out[4] = used;
+    return LB_OK;
+}
+
 lb_status lb_read_fields(lb_ctx* c, int sys, double* h_f) {
     if (!c || !h_f || sys < 0 || sys >= c->n_sys) return LB_ERR_ARG;
     if (!c->has_state) return LB_ERR_STATE;
@@ -1030,14 +1190,36 @@ lb_status lb_write_fields(lb_ctx* c, int sys, const double* h_f) {
     return LB_OK;
 }
 
-// Checkpoint file: header, descriptors, populations (raw), accumulators, globals.
+// Checkpoint file: header, descriptors, populations (raw), accumulators,
+// globals, histogram counts, C(k) and momentum-spectrum accumulators.
 struct CkptHeader {
     char magic[8];
     int32_t version, lattice, coupling, fp32, n_sys, q;
     int64_t step, n_sites, n_levels;
-    int32_t hist_bins, pad;
+    int32_t hist_bins, sk_every;
     double hist_range;
+    int32_t jk, pad;
 };
+
+namespace {
+
+size_t spectra_doubles(const Plan& P) { return (P.sk ? size_t(P.n_sites) : 0) + (P.jk ? 3 * size_t(P.n_sites) : 0); }
+
+// C(k) accumulators then momentum-spectrum accumulators, between host and device.
+cudaError_t copy_spectra(lb_ctx* c, double* h, bool to_device) {
+    const Plan& P = c->P;
+    const size_t nk = P.sk ? size_t(P.n_sites) : 0, nj = P.jk ? 3 * size_t(P.n_sites) : 0;
+    const auto kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaSuccess;
+    if (nk) e = to_device ? cudaMemcpyAsync(c->ws + P.sk_acc, h, sizeof(double) * nk, kind, c->stream)
+                          : cudaMemcpyAsync(h, c->ws + P.sk_acc, sizeof(double) * nk, kind, c->stream);
+    if (e == cudaSuccess && nj)
+        e = to_device ? cudaMemcpyAsync(c->ws + P.jk_acc, h + nk, sizeof(double) * nj, kind, c->stream)
+                      : cudaMemcpyAsync(h + nk, c->ws + P.jk_acc, sizeof(double) * nj, kind, c->stream);
+    return e;
+}
+
+}  // namespace
 
 lb_status lb_save(lb_ctx* c, const char* path) {
     if (!c || !path) return LB_ERR_ARG;
@@ -1047,7 +1229,9 @@ lb_status lb_save(lb_ctx* c, const char* path) {
     std::vector<char> pop(es * c->q * P.n_sites);
     std::vector<double> acc(7 * P.n_levels), glob(8 * c->n_sys);
     std::vector<uint64_t> hist(hist_bytes(P) / sizeof(uint64_t));
+    std::vector<double> spec(spectra_doubles(P));
     LB_CHECK(cudaMemcpyAsync(pop.data(), c->pop(int(c->step & 1)), pop.size(), cudaMemcpyDeviceToHost, c->stream));
+    LB_CHECK(copy_spectra(c, spec.data(), false));
     if (!hist.empty())
         LB_CHECK(cudaMemcpyAsync(hist.data(), c->ws + P.hist, hist_bytes(P), cudaMemcpyDeviceToHost, c->stream));
     LB_CHECK(cudaMemcpyAsync(acc.data(), c->ws + P.acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost,
@@ -1063,6 +1247,8 @@ lb_status lb_save(lb_ctx* c, const char* path) {
     hd.version = 2;
     hd.hist_bins = P.hist_bins;
     hd.hist_range = P.hist_range;
+    hd.sk_every = c->opts.sk_every;
+    hd.jk = P.jk ? 1 : 0;
     hd.lattice = c->lattice;
     hd.coupling = c->coupling;
     hd.fp32 = c->fp32;
@@ -1077,6 +1263,7 @@ lb_status lb_save(lb_ctx* c, const char* path) {
     ok = ok && std::fwrite(acc.data(), sizeof(double), acc.size(), fp) == acc.size();
     ok = ok && std::fwrite(glob.data(), sizeof(double), glob.size(), fp) == glob.size();
     ok = ok && std::fwrite(hist.data(), sizeof(uint64_t), hist.size(), fp) == hist.size();
+    ok = ok && std::fwrite(spec.data(), sizeof(double), spec.size(), fp) == spec.size();
     ok = (std::fclose(fp) == 0) && ok;
     return ok ? LB_OK : LB_ERR_IO;
 }
@@ -1090,7 +1277,8 @@ lb_status lb_load(lb_ctx* c, const char* path) {
     bool ok = std::fread(&hd, sizeof(hd), 1, fp) == 1 && std::memcmp(hd.magic, "LBFLUCT2", 8) == 0 &&
               hd.version == 2 && hd.lattice == c->lattice && hd.coupling == c->coupling && hd.fp32 == c->fp32 &&
               hd.n_sys == c->n_sys && hd.q == c->q && hd.n_sites == P.n_sites && hd.n_levels == P.n_levels &&
-              hd.hist_bins == P.hist_bins && hd.hist_range == P.hist_range;
+              hd.hist_bins == P.hist_bins && hd.hist_range == P.hist_range && hd.sk_every == c->opts.sk_every &&
+              hd.jk == (P.jk ? 1 : 0);
     for (int k = 0; ok && k < c->n_sys; ++k) {
         lb_system_desc d;
         ok = std::fread(&d, sizeof(d), 1, fp) == 1 && std::memcmp(&d, &c->sys[k].d, sizeof(d)) == 0;
@@ -1103,6 +1291,8 @@ lb_status lb_load(lb_ctx* c, const char* path) {
     ok = ok && std::fread(acc.data(), sizeof(double), acc.size(), fp) == acc.size();
     ok = ok && std::fread(glob.data(), sizeof(double), glob.size(), fp) == glob.size();
     ok = ok && std::fread(hist.data(), sizeof(uint64_t), hist.size(), fp) == hist.size();
+    std::vector<double> spec(spectra_doubles(P));
+    ok = ok && std::fread(spec.data(), sizeof(double), spec.size(), fp) == spec.size();
     std::fclose(fp);
     if (!ok) return LB_ERR_IO;
     drop_graphs(c);
@@ -1114,6 +1304,7 @@ lb_status lb_load(lb_ctx* c, const char* path) {
                              c->stream));
     if (!hist.empty())
         LB_CHECK(cudaMemcpyAsync(c->ws + P.hist, hist.data(), hist_bytes(P), cudaMemcpyHostToDevice, c->stream));
+    LB_CHECK(copy_spectra(c, spec.data(), true));
     LB_CHECK(cudaMemcpyAsync(c->ws + P.step, &c->step, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
     LB_CHECK(cudaMemsetAsync(c->ws + P.status, 0, sizeof(int), c->stream));
     LB_CHECK(cudaStreamSynchronize(c->stream));

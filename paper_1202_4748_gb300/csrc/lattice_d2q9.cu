@@ -48,9 +48,9 @@ cudaError_t launch_scatter_d2q9(int fp32, const SysDev* sys, int s, int i, int64
                 : scatter_any<D2Q9, double>(sys, s, i, n, in, fbuf, st);
 }
 cudaError_t launch_obs_site_d2q9(int fp32, const SysDev* sys, const int4* items, int n_items, const void* fbuf,
-                                 double* d, double* partial, cudaStream_t st) {
-    return fp32 ? obs_site_any<D2Q9, float>(sys, items, n_items, fbuf, d, partial, st)
-                : obs_site_any<D2Q9, double>(sys, items, n_items, fbuf, d, partial, st);
+                                 double* d, double* partial, double* jout, int64_t jstride, cudaStream_t st) {
+    return fp32 ? obs_site_any<D2Q9, float>(sys, items, n_items, fbuf, d, partial, jout, jstride, st)
+                : obs_site_any<D2Q9, double>(sys, items, n_items, fbuf, d, partial, jout, jstride, st);
 }
 
 }  // namespace lbf

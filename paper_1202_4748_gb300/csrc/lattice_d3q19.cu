@@ -61,9 +61,9 @@ cudaError_t launch_scatter_d3q19(int fp32, const SysDev* sys, int s, int i, int6
                 : scatter_any<D3Q19, double>(sys, s, i, n, in, fbuf, st);
 }
 cudaError_t launch_obs_site_d3q19(int fp32, const SysDev* sys, const int4* items, int n_items, const void* fbuf,
-                                 double* d, double* partial, cudaStream_t st) {
-    return fp32 ? obs_site_any<D3Q19, float>(sys, items, n_items, fbuf, d, partial, st)
-                : obs_site_any<D3Q19, double>(sys, items, n_items, fbuf, d, partial, st);
+                                 double* d, double* partial, double* jout, int64_t jstride, cudaStream_t st) {
+    return fp32 ? obs_site_any<D3Q19, float>(sys, items, n_items, fbuf, d, partial, jout, jstride, st)
+                : obs_site_any<D3Q19, double>(sys, items, n_items, fbuf, d, partial, jout, jstride, st);
 }
 
 }  // namespace lbf

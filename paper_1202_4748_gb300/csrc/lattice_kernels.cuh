@@ -163,11 +163,13 @@ struct CompSum {
 // j(r) = sum_i c_i f_i(r - c_i), to FP64 accuracy (FP64 sums for FP64 storage;
 // compensated FP32 sums for FP32 storage, which keeps the per-population work
 // off the FP64 pipe).  Writes d and per-item partial sums (sum d, sum jx,
-// sum jy, sum jz) in FP64.
+// sum jy, sum jz) in FP64, and, when jout is not null, the momentum field
+// j_a(r) at jout + a * jstride (D components).
 template <class L, class Real>
 __global__ void __launch_bounds__(AUX_THREADS)
     obs_site_kernel(const SysDev* __restrict__ sysv, const int4* __restrict__ items, const Real* __restrict__ fbuf,
-                    double* __restrict__ d, double* __restrict__ partial) {
+                    double* __restrict__ d, double* __restrict__ partial, double* __restrict__ jout,
+                    int64_t jstride) {
     __shared__ double sh[4 * AUX_THREADS];
     const int4 it = items[blockIdx.x];
     const SysDev& S = sysv[it.x];
@@ -194,6 +196,10 @@ __global__ void __launch_bounds__(AUX_THREADS)
         }
         const double rv = r.value();
         d[S.site_offset + site] = rv;
+        if (jout) {
+#pragma unroll
+            for (int a = 0; a < L::D; ++a) jout[a * jstride + S.site_offset + site] = m[a].value();
+        }
         acc[0] += rv;
         acc[1] += m[0].value();
         acc[2] += m[1].value();

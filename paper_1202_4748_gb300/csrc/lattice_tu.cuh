@@ -86,9 +86,10 @@ cudaError_t scatter_any(const SysDev* sys, int s, int i, int64_t n, const double
 
 template <class L, class Real>
 cudaError_t obs_site_any(const SysDev* sys, const int4* items, int n_items, const void* fbuf, double* d,
-                         double* partial, cudaStream_t st) {
+                         double* partial, double* jout, int64_t jstride, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
-    obs_site_kernel<L, Real><<<n_items, AUX_THREADS, 0, st>>>(sys, items, static_cast<const Real*>(fbuf), d, partial);
+    obs_site_kernel<L, Real><<<n_items, AUX_THREADS, 0, st>>>(sys, items, static_cast<const Real*>(fbuf), d, partial,
+                                                              jout, jstride);
     return cudaGetLastError();
 }
 

@@ -46,10 +46,11 @@ cudaError_t launch_scatter_d2q9(int fp32, const SysDev* sys, int s, int i, int64
                                 cudaStream_t st);
 cudaError_t launch_scatter_d3q19(int fp32, const SysDev* sys, int s, int i, int64_t n, const double* in, void* fbuf,
                                  cudaStream_t st);
+// jout (nullable): momentum field j_a at jout + a * jstride.
 cudaError_t launch_obs_site_d2q9(int fp32, const SysDev* sys, const int4* items, int n_items, const void* fbuf,
-                                 double* d, double* partial, cudaStream_t st);
+                                 double* d, double* partial, double* jout, int64_t jstride, cudaStream_t st);
 cudaError_t launch_obs_site_d3q19(int fp32, const SysDev* sys, const int4* items, int n_items, const void* fbuf,
-                                  double* d, double* partial, cudaStream_t st);
+                                  double* d, double* partial, double* jout, int64_t jstride, cudaStream_t st);
 
 // ---- lattice-independent (obs.cu) ----------------------------------------
 struct SysSpan {            // items [first, first + count) of one system
@@ -125,6 +126,13 @@ cudaError_t launch_sk_pass(const SkSys* sk, const int4* items, int n_items, int 
 cudaError_t launch_sk_accum(const SkSys* sk, const int4* items, int n_items, const double* F, double* acc,
                             cudaStream_t st);
 // per-shell sums of the accumulated C(k) of one system (one CTA per shell)
+// Momentum spectra (see sk.cu): accumulate the x, longitudinal and transverse
+// spectra of the transforms F0..F2 (F2 unused in 2-D) into acc + c * stride.
+cudaError_t launch_jk_accum(const SkSys* sk, const int4* items, int n_items, int dims, const double* F0,
+                            const double* F1, const double* F2, double* acc, int64_t stride, cudaStream_t st);
+// Guo variant: lap = Laplacian of d, then j_a += kappa rho d_a(lap) / 2 (j at jf + a * stride).
+cudaError_t launch_jk_guo_force(int lattice, const SysDev* sys, const int4* items, int n_items, const double* d,
+                                double* lap, double* jf, int64_t stride, cudaStream_t st);
 cudaError_t launch_sk_bin(const SkSys* sk, int sys, const double* acc, int nbins, double* sums, double* counts,
                           cudaStream_t st);
 

@@ -26,6 +26,8 @@ __global__ void sk_twiddle_kernel(double* __restrict__ tw, const int* __restrict
 
 // item: (system, first element, end element, unused); element e of a system
 // enumerates its sites in [z][y][x] order, and names the output (k_x, y, z) etc.
+// With dbar the input is phi = (d - dbar) / (rho_c + dbar); without (null) it
+// is the field d itself.
 __global__ void __launch_bounds__(AUX_THREADS)
     sk_x_kernel(const SysDev* __restrict__ sysv, const SkSys* __restrict__ skv, const int4* __restrict__ items,
                 const double* __restrict__ d, const double* __restrict__ dbar, const double* __restrict__ tw,
@@ -33,8 +35,8 @@ __global__ void __launch_bounds__(AUX_THREADS)
     const int4 it = items[blockIdx.x];
     const SkSys K = skv[it.x];
     const SysDev& S = sysv[it.x];
-    const double db = dbar[it.x];
-    const double inv_rbar = 1.0 / (S.rho_c + db);
+    const double db = dbar ? dbar[it.x] : 0.0;
+    const double inv_rbar = dbar ? 1.0 / (S.rho_c + db) : 1.0;
     for (int j = 0; j < SITES_PER_THREAD; ++j) {
         const int e = it.y + j * AUX_THREADS + threadIdx.x;
         if (e >= it.z) break;
@@ -100,6 +102,99 @@ __global__ void __launch_bounds__(AUX_THREADS)
 
 __device__ __forceinline__ int wrapk(int k, int n) { return 2 * k < n ? k : k - n; }
 
+// Momentum spectra of one sample (Eq. 69 diagnostics): from the transforms
+// J_a(k) (complex, one field per component) accumulate per k
+//   acc[0][k] += |J_x|^2 / N
+//   acc[1][k] += |khat . J|^2 / N                       (0 at k = 0)
+//   acc[2][k] += (|J|^2 - |khat . J|^2) / (N (d - 1))    (0 at k = 0)
+// with khat = n / |n|, n the wrapped integer wavevector; acc[c] = acc + c * stride.
+__global__ void __launch_bounds__(AUX_THREADS)
+    jk_accum_kernel(const SkSys* __restrict__ skv, const int4* __restrict__ items, int dims,
+                    const double* __restrict__ F0, const double* __restrict__ F1, const double* __restrict__ F2,
+                    double* __restrict__ acc, int64_t stride) {
+    const int4 it = items[blockIdx.x];
+    const SkSys K = skv[it.x];
+    for (int j = 0; j < SITES_PER_THREAD; ++j) {
+        const int e = it.y + j * AUX_THREADS + threadIdx.x;
+        if (e >= it.z) break;
+        const int64_t g = K.site_offset + e;
+        const int kx = e % K.nx, ky = (e / K.nx) % K.ny, kz = e / (K.nx * K.ny);
+        const double a = wrapk(kx, K.nx), b = wrapk(ky, K.ny), c = dims == 3 ? wrapk(kz, K.nz) : 0;
+        const double xr = F0[2 * g], xi = F0[2 * g + 1];
+        const double yr = F1[2 * g], yi = F1[2 * g + 1];
+        const double zr = dims == 3 ? F2[2 * g] : 0.0, zi = dims == 3 ? F2[2 * g + 1] : 0.0;
+        const double jx2 = xr * xr + xi * xi;
+        acc[g] += jx2 * K.inv_n;
+        const double nn2 = a * a + b * b + c * c;
+        if (nn2 > 0.0) {
+            const double inv = 1.0 / sqrt(nn2);
+            const double pr = (a * xr + b * yr + c * zr) * inv, pi = (a * xi + b * yi + c * zi) * inv;
+            const double p2 = pr * pr + pi * pi;
+            const double tot = jx2 + yr * yr + yi * yi + zr * zr + zi * zi;
+            acc[stride + g] += p2 * K.inv_n;
+            acc[2 * stride + g] += (tot - p2) * K.inv_n / double(dims - 1);
+        }
+    }
+}
+
+// Laplacian of the density deviation d (FP64): lap(r) = 6 sum_i t_i (d(r + c_i) - d(r)).
+template <class L>
+__global__ void __launch_bounds__(AUX_THREADS)
+    jk_lap_kernel(const SysDev* __restrict__ sysv, const int4* __restrict__ items, const double* __restrict__ d,
+                  double* __restrict__ lap) {
+    const int4 it = items[blockIdx.x];
+    const SysDev& S = sysv[it.x];
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const double* ds = d + S.site_offset;
+    for (int j = 0; j < SITES_PER_THREAD; ++j) {
+        const int site = it.y + j * AUX_THREADS + threadIdx.x;
+        if (site >= it.z) break;
+        int x, y, z;
+        site_coords(site, nx, ny, x, y, z);
+        const double c0 = ds[site];
+        double v = 0.0;
+#pragma unroll
+        for (int i = 1; i < L::Q; ++i) {
+            const int sx = wrap1(x + L::c(i, 0), nx), sy = wrap1(y + L::c(i, 1), ny);
+            const int sz = L::D == 3 ? wrap1(z + L::c(i, 2), nz) : 0;
+            v += 6.0 * L::w(i) * (ds[sx + nx * (sy + ny * sz)] - c0);
+        }
+        lap[S.site_offset + site] = v;
+    }
+}
+
+// Guo half-force: j_a(r) += (1/2) kappa rho(r) d_a lap(r), d_a X = 3 sum_i t_i c_ia X(r + c_i),
+// rho = rho_c + d; the three components at j + a * stride.
+template <class L>
+__global__ void __launch_bounds__(AUX_THREADS)
+    jk_force_kernel(const SysDev* __restrict__ sysv, const int4* __restrict__ items, const double* __restrict__ d,
+                    const double* __restrict__ lap, double* __restrict__ jf, int64_t stride) {
+    const int4 it = items[blockIdx.x];
+    const SysDev& S = sysv[it.x];
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const double* ls = lap + S.site_offset;
+    for (int j = 0; j < SITES_PER_THREAD; ++j) {
+        const int site = it.y + j * AUX_THREADS + threadIdx.x;
+        if (site >= it.z) break;
+        int x, y, z;
+        site_coords(site, nx, ny, x, y, z);
+        double g[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int i = 1; i < L::Q; ++i) {
+            const int sx = wrap1(x + L::c(i, 0), nx), sy = wrap1(y + L::c(i, 1), ny);
+            const int sz = L::D == 3 ? wrap1(z + L::c(i, 2), nz) : 0;
+            const double v = ls[sx + nx * (sy + ny * sz)];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (L::c(i, a) != 0) g[a] += 3.0 * L::w(i) * double(L::c(i, a)) * v;
+        }
+        const int64_t gi = S.site_offset + site;
+        const double half = 0.5 * S.kappa * (S.rho_c + d[gi]);
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) jf[a * stride + gi] += half * g[a];
+    }
+}
+
 __global__ void __launch_bounds__(AUX_THREADS)
     sk_bin_kernel(const SkSys* __restrict__ skv, int sys, const double* __restrict__ acc, double* __restrict__ sums,
                   double* __restrict__ counts) {
@@ -153,6 +248,26 @@ cudaError_t launch_sk_accum(const SkSys* sk, const int4* items, int n_items, con
                             cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     sk_accum_kernel<<<n_items, AUX_THREADS, 0, st>>>(sk, items, F, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jk_accum(const SkSys* sk, const int4* items, int n_items, int dims, const double* F0,
+                            const double* F1, const double* F2, double* acc, int64_t stride, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    jk_accum_kernel<<<n_items, AUX_THREADS, 0, st>>>(sk, items, dims, F0, F1, F2, acc, stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jk_guo_force(int lattice, const SysDev* sys, const int4* items, int n_items, const double* d,
+                                double* lap, double* jf, int64_t stride, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    if (lattice == 0) {
+        jk_lap_kernel<D2Q9><<<n_items, AUX_THREADS, 0, st>>>(sys, items, d, lap);
+        jk_force_kernel<D2Q9><<<n_items, AUX_THREADS, 0, st>>>(sys, items, d, lap, jf, stride);
+    } else {
+        jk_lap_kernel<D3Q19><<<n_items, AUX_THREADS, 0, st>>>(sys, items, d, lap);
+        jk_force_kernel<D3Q19><<<n_items, AUX_THREADS, 0, st>>>(sys, items, d, lap, jf, stride);
+    }
     return cudaGetLastError();
 }
 

@@ -197,3 +197,41 @@ def test_histogram_estimates_and_options_rejected():
     base = lb.workspace_bytes([s])
     # 5 levels (16, 8, 4, 2, 1) of 102 64-bit counts, up to one alignment unit of slack
     assert lb.workspace_bytes([s], hist_bins=100, hist_range=0.5) >= base + 8 * 102 * 5 - 256
+
+
+@pytest.mark.parametrize("lattice,side,xi", [("D3Q19", 24, 1.2), ("D2Q9", 48, 2.0), ("D3Q19", 16, 0.0)])
+def test_oz_fit_matches_oracle(lattice, side, xi):
+    import paper_1202_4748_gb300 as lb
+    from oracle import observables as ob
+    from oracle.lattice import d2q9, d3q19
+    lat = d3q19() if lattice == "D3Q19" else d2q9()
+    shape = (side, side, side) if lattice == "D3Q19" else (1, side, side)
+    kT, chi, kmax, ns = 1e-4, 9.0, 7, 4
+    C = kT * chi / (1.0 + xi * xi * ob.laplacian_symbol(shape, lat))
+    sums, counts = ob.bin_shells(ns * C, shape, kmax + 2)
+    got = lb.oz_fit(lattice, side, sums, counts, ns, kT, kmax)
+    want = ob.oz_fit(sums, counts, ns, shape, lat, kT, kmax)
+    assert got["shells"] == want["shells"] == kmax
+    for k in ("chi", "a"):
+        assert got[k] == pytest.approx(want[k], rel=1e-9), k
+    # b is a difference of large sums: compare it on the scale of a
+    assert abs(got["b"] - want["b"]) <= 1e-9 * abs(want["a"])
+    if xi > 0:
+        assert got["xi"] == pytest.approx(want["xi"], rel=1e-6)
+    else:                        # b = 0 up to rounding: xi is 0 or NaN (b slightly negative)
+        assert all(np.isnan(v) or v < 1e-5 for v in (got["xi"], want["xi"]))
+    bad = counts.copy()
+    bad[2] += 1
+    with pytest.raises(lb.LBError):
+        lb.oz_fit(lattice, side, sums, bad, ns, kT, kmax)
+
+
+def test_momentum_spectra_option_needs_structure_factor():
+    import paper_1202_4748_gb300 as lb
+    s = synth.system("D2Q9", n=16)
+    with pytest.raises(lb.LBError) as e:
+        lb.workspace_bytes([s], jk_spectra=True)
+    assert e.value.status == lb.LB_ERR_ARG
+    a = lb.workspace_bytes([s], sk_every=5)
+    b = lb.workspace_bytes([s], sk_every=5, jk_spectra=True)
+    assert b >= a + 13 * 8 * 256 - 4 * 256        # j, Laplacian, three transforms, three accumulators
