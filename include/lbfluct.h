@@ -57,7 +57,8 @@ typedef enum {
     LB_ERR_NONFINITE = -6,           /* NaN/Inf met in the observables              */
     LB_ERR_UNSUPPORTED = -7,         /* valid but not supported combination         */
     LB_ERR_STATE = -8,               /* sticky error or call out of order           */
-    LB_ERR_IO = -9                   /* checkpoint file error                       */
+    LB_ERR_IO = -9,                  /* checkpoint file error                       */
+    LB_ERR_NO_ROOT = -10             /* a self-consistency equation has no solution  */
 } lb_status;
 
 enum { LB_D2Q9 = 0, LB_D3Q19 = 1 };
@@ -271,6 +272,43 @@ lb_status lb_momentum_spectra(lb_ctx* ctx, int sys, double* h_sum, int64_t* h_co
  * lattice's shells, non-positive C_j, kT <= 0, fewer than 2 shells). */
 lb_status lb_oz_fit(int lattice, int side, const double* h_sum, const int64_t* h_count, int kmax,
                     int64_t n_samples, double kT, double out[5]);
+
+/* ---- Perturbation-theory comparator (Sec. II C) ------------------------------
+ * Lattice sums over the wavevectors q != 0 of an S^d periodic lattice (S^2 for
+ * LB_D2Q9, S^3 for LB_D3Q19; the momentum integrals of Eqs. 31-32 and 40-42
+ * become such sums, the zero mode excluded because the order parameter is
+ * conserved), with G(q) = 1 / (m + kappa q^2) and q^2 the symbol of the lattice
+ * Laplacian of the simulated model, 6 sum_i t_i (1 - cos q.c_i):
+ *   S1 = N^-1 sum_q G,  S1sq = N^-1 sum_q G^2,
+ *   S2 = N^-2 sum_{q1, q2} G(q1) G(q2) G(q1 + q2), terms at the zero mode dropped.
+ * Evaluated on the device on the caller's stream in a caller-owned device
+ * workspace (256-byte aligned, lb_pt_workspace_bytes() long); each call
+ * synchronises that stream.  Results are written to host arrays.
+ * Errors: LB_ERR_ARG (lattice, S < 2 or N > 2^28, parameters),
+ * LB_ERR_WORKSPACE, LB_ERR_CUDA, LB_ERR_NO_ROOT. */
+lb_status lb_pt_workspace_bytes(int lattice, int side, size_t* bytes);
+
+/* out[0] S1, out[1] S1sq, out[2] S2 at mass m > 0. */
+lb_status lb_pt_sums(int lattice, int side, double m, double kappa, void* d_workspace, size_t bytes,
+                     void* cuda_stream, double out[3]);
+
+/* Symmetric phase, Eq. 36: r' = r + 3 u kT S1(r') - 6 u^2 kT^2 S2(r'), the
+ * largest root r' > 0 (the branch that tends to r as u -> 0), found by halving
+ * from an upper bound where the right side is below r' and bisecting.
+ * out[0] r', out[1] chi = 1/r', out[2] xi = sqrt(kappa/r'), out[3] S1(r'),
+ * out[4] S2(r').  LB_ERR_NO_ROOT when no r' > 0 solves it. */
+lb_status lb_pt_symmetric(int lattice, int side, double r, double u, double kappa, double kT, void* d_workspace,
+                          size_t bytes, void* cuda_stream, double out[5]);
+
+/* Broken phase (r < 0, u > 0), Eqs. 40, 42, 43: v from
+ * 0 = r + u v^2 + 3 u kT S1(r_sigma), r_sigma = r + 3 u v^2, the root next
+ * below the mean-field v^2 = -r/u; then
+ * r'_sigma = r_sigma + kT (3 u S1(r_sigma) - 18 u^2 v^2 kT S1sq(r_sigma)).
+ * out[0] v, out[1] r_sigma, out[2] r'_sigma, out[3] chi = 1/r'_sigma,
+ * out[4] xi = sqrt(kappa/r'_sigma), out[5] S1, out[6] S1sq (at r_sigma).
+ * LB_ERR_NO_ROOT when fluctuations leave no ordered solution. */
+lb_status lb_pt_broken(int lattice, int side, double r, double u, double kappa, double kT, void* d_workspace,
+                       size_t bytes, void* cuda_stream, double out[7]);
 
 /* Copy f_i(r, t) of system `sys` to h_f (float64 [q][nz][ny][nx]).  Synchronises.
  * Errors: LB_ERR_ARG, LB_ERR_CUDA. */

@@ -24,7 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 LB_OK = 0
 LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_WORKSPACE = -1, -2, -3
 LB_ERR_NONPOSITIVE_DENSITY, LB_ERR_NOISE_NOT_PD, LB_ERR_NONFINITE = -4, -5, -6
-LB_ERR_UNSUPPORTED, LB_ERR_STATE, LB_ERR_IO = -7, -8, -9
+LB_ERR_UNSUPPORTED, LB_ERR_STATE, LB_ERR_IO, LB_ERR_NO_ROOT = -7, -8, -9, -10
 LB_D2Q9, LB_D3Q19 = 0, 1
 LB_MODEQ, LB_GUO = 0, 1
 LB_FP64, LB_FP32_DEVIATION = 0, 1
@@ -85,6 +85,13 @@ _SIG = {
     "lb_momentum_spectra": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
     "lb_oz_fit": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
                                  _P]),
+    "lb_pt_workspace_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "lb_pt_sums": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, ctypes.c_size_t,
+                                  _P, _P]),
+    "lb_pt_symmetric": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, _P, ctypes.c_size_t, _P, _P]),
+    "lb_pt_broken": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, _P, ctypes.c_size_t, _P, _P]),
     "lb_structure_factor": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
     "lb_read_fields": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "lb_write_fields": (ctypes.c_int, [_P, ctypes.c_int, _P]),
@@ -156,6 +163,38 @@ def make_opts(precision="fp64", obs_every=0, sk_every=0, graph_chunk=0, tile=(0,
     o.hist_range = float(hist_range)
     o.jk_spectra = 1 if jk_spectra else 0
     return o
+
+
+def _pt_call(fn, nout, lattice, side, *args, device=None):
+    """Run a perturbation-theory call in a torch-allocated workspace on the current stream."""
+    import torch
+    code = _LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
+    n = ctypes.c_size_t()
+    check(lb_pt_workspace_bytes(code, int(side), ctypes.byref(n)), "lb_pt_workspace_bytes")
+    dev = torch.device("cuda" if device is None else device)
+    ws = torch.empty(n.value, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = (ctypes.c_double * nout)()
+    check(fn(code, int(side), *[float(a) for a in args], _P(ws.data_ptr()), n.value, _P(stream.cuda_stream), out),
+          fn.__name__)
+    return list(out)
+
+
+def pt_sums(lattice, side, m, kappa, device=None):
+    """Lattice sums S1, S1sq, S2 at propagator mass m (lb_pt_sums)."""
+    return dict(zip(("S1", "S1sq", "S2"), _pt_call(lb_pt_sums, 3, lattice, side, m, kappa, device=device)))
+
+
+def pt_symmetric(lattice, side, r, u, kappa, kT, device=None):
+    """Self-consistent r' of Eq. 36 (lb_pt_symmetric)."""
+    out = _pt_call(lb_pt_symmetric, 5, lattice, side, r, u, kappa, kT, device=device)
+    return dict(zip(("r_prime", "chi", "xi", "S1", "S2"), out))
+
+
+def pt_broken(lattice, side, r, u, kappa, kT, device=None):
+    """v, r_sigma and r'_sigma of Eqs. 40, 42, 43 (lb_pt_broken)."""
+    out = _pt_call(lb_pt_broken, 7, lattice, side, r, u, kappa, kT, device=device)
+    return dict(zip(("v", "r_sigma", "r_prime_sigma", "chi", "xi", "S1", "S1sq"), out))
 
 
 def oz_fit(lattice, side, sums, counts, n_samples, kT, kmax):

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbfluct.so")
-SOURCES = ["api.cu", "obs.cu", "sk.cu", "noalloc.cu", "lattice_d2q9.cu", "lattice_d3q19.cu"]
+SOURCES = ["api.cu", "obs.cu", "sk.cu", "noalloc.cu", "lattice_d2q9.cu", "lattice_d3q19.cu", "pt.cu"]
 HEADERS = ["lb_device.cuh", "lb_launch.h", "step_kernels.cuh", "lattice_kernels.cuh", "lattice_tu.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -671,6 +671,7 @@ const char* lb_status_string(lb_status s) {
         case LB_ERR_UNSUPPORTED: return "unsupported combination";
         case LB_ERR_STATE: return "invalid state (sticky error or missing initialisation)";
         case LB_ERR_IO: return "checkpoint I/O error";
+        case LB_ERR_NO_ROOT: return "no solution of the self-consistency equation";
     }
     return "unknown status";
 }

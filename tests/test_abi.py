@@ -32,7 +32,7 @@ def test_every_declared_symbol_is_exported():
 def test_status_strings_and_version():
     import paper_1202_4748_gb300 as lb
     assert lb.lb_status_string(0) == b"ok"
-    for code in range(-9, 0):
+    for code in range(-10, 0):
         assert lb.lb_status_string(code) != b"unknown status"
     assert b"sm_103a" in lb.lb_version()
 
@@ -235,3 +235,20 @@ def test_momentum_spectra_option_needs_structure_factor():
     a = lb.workspace_bytes([s], sk_every=5)
     b = lb.workspace_bytes([s], sk_every=5, jk_spectra=True)
     assert b >= a + 13 * 8 * 256 - 4 * 256        # j, Laplacian, three transforms, three accumulators
+
+
+def test_pt_workspace_sizes_and_validation():
+    import paper_1202_4748_gb300 as lb
+    n = ctypes.c_size_t()
+    assert lb.lb_pt_workspace_bytes(lb.LB_D3Q19, 16, ctypes.byref(n)) == lb.LB_OK
+    assert n.value >= 8 * 5 * 16 ** 3                 # G plus two complex transform buffers
+    assert lb.lb_pt_workspace_bytes(lb.LB_D2Q9, 64, ctypes.byref(n)) == lb.LB_OK
+    assert n.value >= 8 * 5 * 64 ** 2
+    for lat, side in [(lb.LB_D3Q19, 1), (5, 16), (lb.LB_D3Q19, 1024)]:
+        assert lb.lb_pt_workspace_bytes(lat, side, ctypes.byref(n)) == lb.LB_ERR_ARG
+    out = (ctypes.c_double * 7)()
+    # argument checks come before any device work
+    assert lb.lb_pt_broken(lb.LB_D2Q9, 8, 1e-3, 0.1, 0.01, 1e-4, None, 0, None, out) == lb.LB_ERR_ARG
+    assert lb.lb_pt_symmetric(lb.LB_D2Q9, 8, 1e-3, -0.1, 0.01, 1e-4, None, 0, None, out) == lb.LB_ERR_ARG
+    assert lb.lb_pt_sums(lb.LB_D2Q9, 8, 0.0, 0.01, None, 0, None, out) == lb.LB_ERR_ARG
+    assert lb.lb_pt_sums(lb.LB_D2Q9, 8, 1.0, 0.01, None, 0, None, out) == lb.LB_ERR_WORKSPACE
