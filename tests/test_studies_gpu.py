@@ -1,0 +1,64 @@
+"""The studies through the CUDA library.
+
+- Sound damping: the library's trajectory of a standing wave decays at the
+  Chapman-Enskog rate with the bulk-viscosity factor (2/d + 1 - 3 c_s^2), in
+  FP64 and FP32 storage, for both couplings (tolerance as on the oracle: the
+  O(k^2) lattice correction, < 0.3%).
+- Coupling comparison of the statics at the paper's 2-D parameters (u = 2.8e-2,
+  kappa = 9.6e-5, kT = 1e-7, as in the captions of the finite-size figures of
+  Sec. IV) in the disordered phase
+  (r = 1e-3): both couplings equilibrate the momentum (<|j(k)|^2> = rho_0 kT,
+  Eq. 69) and give the same Ornstein-Zernike susceptibility, close to the
+  perturbation-theory r' (Eq. 36), within the statistical error of the run.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("GPU tests need CUDA; the library has no CPU fallback")
+    import paper_1202_4748_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("lattice,coupling,nx,tau,steps,shape,precision", [
+    ("D2Q9", "modeq", 64, [1] * 3 + [0.8] * 6, 1200, (2, 1), "fp64"),
+    ("D2Q9", "guo", 64, [1] * 3 + [1.2] + [0.8] * 5, 1200, (2, 1), "fp64"),
+    ("D3Q19", "guo", 32, [1] * 4 + [0.8] * 15, 800, (2, 2), "fp64"),
+    ("D3Q19", "guo", 32, [1] * 4 + [0.8] * 15, 800, (2, 2), "fp32"),
+])
+def test_sound_damping_through_the_library(lb, lattice, coupling, nx, tau, steps, shape, precision):
+    from paper_1202_4748_gb300 import studies
+    s = synth.system(lattice, coupling, n=nx, a=0.1, kT=0.0, kappa=0.01, tau=tau)
+    s.update(nx=nx, ny=shape[0], nz=shape[1])
+    res = studies.sound_decay(s, steps=steps, every=4, precision=precision)
+    assert res["Gamma"] == pytest.approx(res["Gamma_theory"], rel=3e-3)
+    assert res["Gamma"] / res["Gamma_ideal"] > 1.3
+    assert res["omega"] == pytest.approx(math.sqrt(res["c_s2"] * res["k2"]), rel=3e-3)
+
+
+@pytest.mark.parametrize("coupling", ["modeq", "guo"])
+def test_coupling_statics_at_the_papers_2d_parameters(lb, coupling):
+    from paper_1202_4748_gb300 import studies
+    r, u, kappa, kT = 1e-3, 2.8e-2, 9.6e-5, 1e-7
+    systems = []
+    for rep in range(16):
+        s = synth.system("D2Q9", coupling, n=64, a=r, b=u, kappa=kappa, kT=kT, seed=100 + rep, system_id=rep)
+        systems.append(s)
+    res = studies.statics(systems, steps=20000, every=20, precision="fp32", kmax=8, warmup=2000,
+                          graph_chunk=100)
+    # momentum equipartition per shell and projection (shells 2..8: k >~ 0.2)
+    ratio = res["jk_ratio"][:, 1:]
+    assert np.all(np.abs(ratio - 1.0) < 0.06), ratio
+    # susceptibility: the perturbative r' barely moves from r at this kT
+    rp = lb.pt_symmetric("D2Q9", 64, r, u, kappa, kT)["r_prime"]
+    assert res["chi"] == pytest.approx(1.0 / rp, rel=0.06), (res["chi"], 1.0 / rp)
