@@ -331,7 +331,7 @@ lb_status lb_load(lb_ctx* ctx, const char* path);
 
 /* Step-kernel variants compiled for a lattice (LB_D2Q9 or LB_D3Q19): writes up
  * to max_rows rows of 5 int32 (tile x, tile y, tile z or z-chunk, resident CTAs
- * per SM of the register budget (0 = default), prefetch flag) into out
+ * per SM of the register budget (0 = default), flags (0, reserved)) into out
  * (nullable) and returns the number of variants (negative lb_status on error).
  * Row 0 is the default.  Used by the autotuner; no device call. */
 int lb_kernel_variants(int lattice, int32_t* out, int max_rows);

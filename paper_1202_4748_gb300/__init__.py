@@ -225,7 +225,7 @@ def histogram_estimates(counts, lo, hi, vol, kT, m_cut=0.0, frac=0.2):
 
 
 def kernel_variants(lattice):
-    """Compiled step-kernel variants of a lattice: list of (x, y, z, occupancy, prefetch)."""
+    """Compiled step-kernel variants of a lattice: list of (x, y, z, occupancy, flags)."""
     code = _LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
     n = lb_kernel_variants(code, None, 0)
     if n < 0:

@@ -7,16 +7,15 @@
 namespace lbf {
 
 namespace {
-// (x, y, z-chunk, resident CTAs per SM, prefetch of the collided site) of the
-// z-marching kernel; the first entry is the default (fastest on the 160-system
-// ensemble by the autotuner)
-constexpr int kTiles[][5] = {{16, 16, 16, 4, 0}, {16, 16, 32, 4, 0}, {16, 16, 8, 4, 0}, {16, 8, 16, 6, 0},
-                             {16, 16, 16, 4, 1}, {16, 16, 16, 3, 1}, {16, 8, 16, 6, 1}, {16, 16, 32, 3, 1}};
+// (x, y, z-chunk, resident CTAs per SM, unused) of the z-marching kernel; the
+// first entry is the default (fastest on the 160-system ensemble by the autotuner)
+constexpr int kTiles[][5] = {{16, 8, 16, 6, 0}, {16, 8, 32, 6, 0}, {16, 8, 16, 5, 0}, {16, 8, 16, 8, 0},
+                             {16, 16, 16, 4, 0}, {16, 16, 32, 4, 0}, {16, 16, 8, 4, 0}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
 
 template <int CP, class Real, int I>
 cudaError_t step_variant(const StepLaunch& a, cudaStream_t st) {
-    return step_z<D3Q19, CP, Real, kTiles[I][0], kTiles[I][1], kTiles[I][2], kTiles[I][3], kTiles[I][4] != 0>(a, st);
+    return step_z<D3Q19, CP, Real, kTiles[I][0], kTiles[I][1], kTiles[I][2], kTiles[I][3]>(a, st);
 }
 
 template <int CP, class Real, int... I>

@@ -23,7 +23,7 @@ cudaError_t step_one_mode(const StepLaunch& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB, int MODE, bool PREF>
+template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB, int MODE>
 cudaError_t step_z_mode(const StepLaunch& a, cudaStream_t st) {
     StepArgs<Real> A;
     A.sys = a.sys;
@@ -34,18 +34,18 @@ cudaError_t step_z_mode(const StepLaunch& a, cudaStream_t st) {
     A.step_ptr = a.step_ptr;
     A.k = a.k;
     A.status = a.status;
-    step_kernel_z<L, CP, Real, TX, TY, ZC, MINB, MODE, PREF><<<a.n_tiles, TX * TY, 0, st>>>(A);
+    step_kernel_z<L, CP, Real, TX, TY, ZC, MINB, MODE><<<a.n_tiles, TX * TY, 0, st>>>(A);
     return cudaGetLastError();
 }
 
 // z-marching launch: tile = (TX, TY, z-chunk), register budget for MINB resident
-// CTAs per SM (applied to the FP32 kernel; FP64 keeps the default budget)
-template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB, bool PREF = false>
+// CTAs per SM (the FP64 instances use the natural register count).
+template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB>
 cudaError_t step_z(const StepLaunch& a, cudaStream_t st) {
     constexpr int MB = sizeof(Real) == 4 ? MINB : 1;
-    if (a.bgk_only == 2) return step_z_mode<L, CP, Real, TX, TY, ZC, MB, 2, PREF>(a, st);
-    if (a.bgk_only == 1) return step_z_mode<L, CP, Real, TX, TY, ZC, MB, 1, PREF>(a, st);
-    return step_z_mode<L, CP, Real, TX, TY, ZC, MB, 0, PREF>(a, st);
+    if (a.bgk_only == 2) return step_z_mode<L, CP, Real, TX, TY, ZC, MB, 2>(a, st);
+    if (a.bgk_only == 1) return step_z_mode<L, CP, Real, TX, TY, ZC, MB, 1>(a, st);
+    return step_z_mode<L, CP, Real, TX, TY, ZC, MB, 0>(a, st);
 }
 
 template <class L, int CP, class Real, int TX, int TY, int TZ>

@@ -27,7 +27,7 @@ struct StepLaunch {
 };
 
 // Step-kernel variants compiled for each lattice: (x, y, z, resident CTAs per
-// SM, prefetch); index = tile_id.
+// SM, flags (0)); index = tile_id.
 int tile_shapes_d2q9(int (*out)[5], int max);
 int tile_shapes_d3q19(int (*out)[5], int max);
 

@@ -95,7 +95,10 @@ __device__ __forceinline__ void pull_site(const Real* __restrict__ fb, int N, co
 }
 
 // Moment-space noise of Eq. 68 on the non-conserved modes: xi[a - NC].
-template <class L, class Real>
+// TAU1: every non-conserved mode fully relaxed (tau = 1), so g_ab = 1 and the
+// amplitudes are the lattice constants sqrt(N_a); the per-system tables are
+// not read.
+template <class L, class Real, bool TAU1 = false>
 __device__ __forceinline__ void noise_modes(const SysDev& S, const SysPhys<Real>& P, uint32_t site, int64_t step,
                                             Real rho, Real cs2, Real (&xi)[L::Q - L::NC], int* status) {
     constexpr int Q = L::Q;
@@ -114,9 +117,10 @@ __device__ __forceinline__ void noise_modes(const SysDev& S, const SysPhys<Real>
     constexpr double vP = double(L::T(MP, 0)), vR = double(L::T(MR, 0));
     constexpr double NP = norm2<L>(MP), NR = norm2<L>(MR);
     const Real om = Real(1) - Real(3) * cs2;
-    const Real Mpp = (Real(NP) + om * Real(vP * vP)) * P.g_diag[MP];
-    const Real Mrr = (Real(NR) + om * Real(vR * vR)) * P.g_diag[MR];
-    const Real Mpr = om * Real(vP * vR) * P.g_pair;
+    const Real gP = TAU1 ? Real(1) : P.g_diag[MP], gR = TAU1 ? Real(1) : P.g_diag[MR];
+    const Real Mpp = (Real(NP) + om * Real(vP * vP)) * gP;
+    const Real Mrr = (Real(NR) + om * Real(vR * vR)) * gR;
+    const Real Mpr = om * Real(vP * vR) * (TAU1 ? Real(1) : P.g_pair);
     const Real det = Mpp * Mrr - Mpr * Mpr;
     if (Mpp > Real(0) && det > Real(0)) {
         const Real r = fast_rsqrt(Mpp);
@@ -133,7 +137,10 @@ __device__ __forceinline__ void noise_modes(const SysDev& S, const SysPhys<Real>
     }
     sfor<L::NC, Q>([&](auto A) {
         constexpr int a = A;
-        if constexpr (a != MP && a != MR) xi[a - L::NC] = sc * P.namp[a] * nrm[a - L::NC];
+        if constexpr (a != MP && a != MR) {
+            const Real amp = TAU1 ? Real(sqrt(norm2<L>(a))) : P.namp[a];
+            xi[a - L::NC] = sc * amp * nrm[a - L::NC];
+        }
     });
 }
 
@@ -216,7 +223,7 @@ __device__ __forceinline__ void collide_guo_bgk(Real (&f)[L::Q], const Real drho
     });
     Real xi[K];
     sfor<0, K>([&](auto A) { xi[decltype(A)::value] = Real(0); });
-    if (P.kT > Real(0)) noise_modes<L, Real>(S, P, site, step, rho, cs2, xi, status);
+    if (P.kT > Real(0)) noise_modes<L, Real, TAU1>(S, P, site, step, rho, cs2, xi, status);
 
     const Real lam = TAU1 ? Real(1) : P.lam_bgk;
     const Real fs = Real(1) - Real(0.5) * lam;
@@ -600,7 +607,7 @@ struct ZLayout {
     static constexpr size_t bytes = 0;     // static shared memory only
 };
 
-template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB, int MODE, bool PREF>
+template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB, int MODE>
 __global__ void __launch_bounds__(TX* TY, MINB)
     step_kernel_z(const StepArgs<Real> A) {
     static_assert(L::D == 3, "z-marching is for 3-D lattices");
@@ -630,26 +637,29 @@ __global__ void __launch_bounds__(TX* TY, MINB)
     const int x = tl.y + tx, y = tl.z + ty;
     const bool valid_xy = x < nx && y < ny;
 
+    // footprint of plane zz: the density at the tile + halo H sites, from the
+    // populations pulled to them; thread tid handles footprint sites tid + s NT
+    const bool sm = S.small != 0;
+    auto foot_site = [&](int idx, int zz, int& gxw, int& gyw, int& wz) {
+        const int px = idx % SX, py = idx / SX;
+        const int gx = tl.y + px - H, gy = tl.z + py - H;
+        if (!(gx < nx + H && gy < ny + H)) return false;
+        gxw = sm ? wrapm(gx, nx) : wrap2(gx, nx);
+        gyw = sm ? wrapm(gy, ny) : wrap2(gy, ny);
+        wz = sm ? wrapm(zz, nz) : wrap2(zz, nz);
+        return true;
+    };
+
     // planes of rho needed: z0 - H .. z1 - 1 + H; collision of plane zc trails rho by H
     for (int zz = z0 - H; zz < z1 + H; ++zz) {
         const int zc = zz - H;
         const bool collide = zc >= z0 && valid_xy;
-        // PREF: the collided site's populations are requested before the footprint
-        // and Laplacian phases, so their latency overlaps that work
-        Real f[Q];
-        if constexpr (PREF) {
-            if (collide) pull_site<L, Real>(fb, N, Nbr(x, y, zc, nx, ny, nz, true), f);
-        }
         const int slot = (zz - z0 + 2 * NR) % NR;
-        const bool sm = S.small != 0;
-        const int wz = sm ? wrapm(zz, nz) : wrap2(zz, nz);
         for (int idx = tid; idx < SP; idx += NT) {
-            const int px = idx % SX, py = idx / SX;
-            const int gx = tl.y + px - H, gy = tl.z + py - H;
+            int gxw, gyw, wz;
             Real v = Real(0);
-            if (gx < nx + H && gy < ny + H) {
-                const Nbr nb(sm ? wrapm(gx, nx) : wrap2(gx, nx), sm ? wrapm(gy, ny) : wrap2(gy, ny), wz, nx, ny, nz,
-                             true);
+            if (foot_site(idx, zz, gxw, gyw, wz)) {
+                const Nbr nb(gxw, gyw, wz, nx, ny, nz, true);
                 Real g[Q];
                 pull_site<L, Real>(fb, N, nb, g);
                 sfor<0, Q>([&](auto I) { v += g[decltype(I)::value]; });
@@ -684,7 +694,8 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         }
         // collision of plane zc = zz - H
         if (collide) {
-            if constexpr (!PREF) pull_site<L, Real>(fb, N, Nbr(x, y, zc, nx, ny, nz, true), f);
+            Real f[Q];
+            pull_site<L, Real>(fb, N, Nbr(x, y, zc, nx, ny, nz, true), f);
             Real drho = Real(0);
             sfor<0, Q>([&](auto I) { drho += f[decltype(I)::value]; });
             const int site = site_index(x, y, zc, nx, ny);

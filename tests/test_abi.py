@@ -130,8 +130,8 @@ def test_kernel_variant_table():
     for lat in ("D2Q9", "D3Q19"):
         rows = lb.kernel_variants(lat)
         assert len(rows) >= 3 and len(set(rows)) == len(rows)
-        for x, y, z, occ, pref in rows:
-            assert x > 0 and y > 0 and z > 0 and occ >= 0 and pref in (0, 1)
+        for x, y, z, occ, flags in rows:
+            assert x > 0 and y > 0 and z > 0 and occ >= 0 and flags == 0
             assert x * y <= 1024 and x % 16 == 0
         if lat == "D2Q9":
             assert all(r[2] == 1 for r in rows)
