@@ -611,14 +611,20 @@ template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB, int MOD
 __global__ void __launch_bounds__(TX* TY, MINB)
     step_kernel_z(const StepArgs<Real> A) {
     static_assert(L::D == 3, "z-marching is for 3-D lattices");
+    static_assert(CP == GUO, "the z-marching kernel implements the Guo-forced coupling");
     constexpr bool BGK_ONLY = MODE >= 1;
     constexpr bool TAU1 = MODE == 2;
     constexpr int Q = L::Q;
     constexpr int H = HaloOf<L, CP>::H;
     constexpr int SX = TX + 2 * H, SY = TY + 2 * H, SP = SX * SY;     // rho footprint plane
-    constexpr int NR = 2 * H + 1;                                     // rho ring planes
-    constexpr int LX = TX + 2, LY = TY + 2, LP = LX * LY;             // Laplacian plane (Guo)
-    constexpr int NL = CP == GUO ? 3 : 1;
+    // One barrier per plane: the collision trails the density by H + 1 planes,
+    // so the Laplacian planes it reads were written before the iteration's
+    // barrier.  Ring sizes: rho planes zz-2..zz are read by the Laplacian while a
+    // thread past the barrier may already write plane zz+1 (4 slots); Laplacian
+    // planes zz-4..zz-2 are read by the collision while plane zz-1 is written (4).
+    constexpr int NR = 4;                                             // rho ring planes
+    constexpr int LX = TX + 2, LY = TY + 2, LP = LX * LY;             // Laplacian plane
+    constexpr int NL = 4;
     constexpr int NT = TX * TY;
     __shared__ Real srho[NR * SP];
     __shared__ Real slap[NL * LP];
@@ -650,61 +656,59 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         return true;
     };
 
-    // planes of rho needed: z0 - H .. z1 - 1 + H; collision of plane zc trails rho by H
-    for (int zz = z0 - H; zz < z1 + H; ++zz) {
-        const int zc = zz - H;
+    // rho planes z0 - H .. z1 + H - 1, Laplacian planes z0 - 1 .. z1, collisions z0 .. z1 - 1
+    for (int zz = z0 - H; zz <= z1 + H; ++zz) {
+        const int zc = zz - H - 1;
         const bool collide = zc >= z0 && valid_xy;
-        const int slot = (zz - z0 + 2 * NR) % NR;
-        for (int idx = tid; idx < SP; idx += NT) {
-            int gxw, gyw, wz;
-            Real v = Real(0);
-            if (foot_site(idx, zz, gxw, gyw, wz)) {
-                const Nbr nb(gxw, gyw, wz, nx, ny, nz, true);
-                Real g[Q];
-                pull_site<L, Real>(fb, N, nb, g);
-                sfor<0, Q>([&](auto I) { v += g[decltype(I)::value]; });
+        if (zz < z1 + H) {
+            const int slot = (zz - z0 + 2 * NR) % NR;
+            for (int idx = tid; idx < SP; idx += NT) {
+                int gxw, gyw, wz;
+                Real v = Real(0);
+                if (foot_site(idx, zz, gxw, gyw, wz)) {
+                    const Nbr nb(gxw, gyw, wz, nx, ny, nz, true);
+                    Real g[Q];
+                    pull_site<L, Real>(fb, N, nb, g);
+                    sfor<0, Q>([&](auto I) { v += g[decltype(I)::value]; });
+                }
+                srho[slot * SP + idx] = v;
             }
-            srho[slot * SP + idx] = v;
         }
         __syncthreads();
-        if constexpr (CP == GUO) {
-            // Laplacian of plane zl = zz - 1 on the column + 1 (needs rho planes zl-1 .. zl+1)
-            const int zl = zz - 1;
-            if (zl >= z0 - 1) {
-                const int lslot = (zl - z0 + 6) % 3;
-                const int r0 = (zl - z0 + 2 * NR) % NR;
-                const int rm = (zl - 1 - z0 + 2 * NR) % NR;
-                const int rp = (zl + 1 - z0 + 2 * NR) % NR;
-                for (int idx = tid; idx < LP; idx += NT) {
-                    const int px = idx % LX, py = idx / LX;
-                    const int c = (py + H - 1) * SX + (px + H - 1);
-                    const Real rc = srho[r0 * SP + c];
-                    Real lap = Real(0);
-                    sfor<1, Q>([&](auto I) {
-                        constexpr int i = I;
-                        constexpr int cz = L::c(i, 2);
-                        constexpr int off = L::c(i, 0) + SX * L::c(i, 1);
-                        const int pl = cz == 0 ? r0 : (cz > 0 ? rp : rm);
-                        lap += Real(6.0 * L::w(i)) * (srho[pl * SP + c + off] - rc);
-                    });
-                    slap[lslot * LP + idx] = lap;
-                }
+        // Laplacian of plane zl = zz - 1 on the column + 1 (needs rho planes zl-1 .. zl+1)
+        const int zl = zz - 1;
+        if (zl >= z0 - 1 && zl <= z1) {
+            const int lslot = (zl - z0 + 2 * NL) % NL;
+            const int r0 = (zl - z0 + 2 * NR) % NR;
+            const int rm = (zl - 1 - z0 + 2 * NR) % NR;
+            const int rp = (zl + 1 - z0 + 2 * NR) % NR;
+            for (int idx = tid; idx < LP; idx += NT) {
+                const int px = idx % LX, py = idx / LX;
+                const int c = (py + H - 1) * SX + (px + H - 1);
+                const Real rc = srho[r0 * SP + c];
+                Real lap = Real(0);
+                sfor<1, Q>([&](auto I) {
+                    constexpr int i = I;
+                    constexpr int cz = L::c(i, 2);
+                    constexpr int off = L::c(i, 0) + SX * L::c(i, 1);
+                    const int pl = cz == 0 ? r0 : (cz > 0 ? rp : rm);
+                    lap += Real(6.0 * L::w(i)) * (srho[pl * SP + c + off] - rc);
+                });
+                slap[lslot * LP + idx] = lap;
             }
-            __syncthreads();
         }
-        // collision of plane zc = zz - H
+        // collision of plane zc = zz - H - 1
         if (collide) {
             Real f[Q];
             pull_site<L, Real>(fb, N, Nbr(x, y, zc, nx, ny, nz, true), f);
             Real drho = Real(0);
             sfor<0, Q>([&](auto I) { drho += f[decltype(I)::value]; });
             const int site = site_index(x, y, zc, nx, ny);
-            // the collision reads rho (MODEQ) or the Laplacian (GUO) around the site;
-            // GUO needs only lap planes zc-1..zc+1, addressed through a 3-plane view
-            const RingView<Real, SX> rv{srho, ((zc - 1 - z0 + 2 * NR) % NR) * SP, ((zc - z0 + 2 * NR) % NR) * SP,
-                                        ((zc + 1 - z0 + 2 * NR) % NR) * SP, (ty + H) * SX + (tx + H)};
-            const RingView<Real, LX> lv{slap, ((zc - 1 - z0 + 6) % 3) * LP, ((zc - z0 + 6) % 3) * LP,
-                                        ((zc + 1 - z0 + 6) % 3) * LP, (ty + 1) * LX + (tx + 1)};
+            // the Guo collision reads only the Laplacian planes zc-1..zc+1 around the
+            // site (a 3-plane view); the density view is unused by this coupling
+            const RingView<Real, SX> rv{srho, 0, 0, 0, (ty + H) * SX + (tx + H)};
+            const RingView<Real, LX> lv{slap, ((zc - 1 - z0 + 2 * NL) % NL) * LP, ((zc - z0 + 2 * NL) % NL) * LP,
+                                        ((zc + 1 - z0 + 2 * NL) % NL) * LP, (ty + 1) * LX + (tx + 1)};
             if constexpr (CP == GUO && BGK_ONLY)
                 collide_guo_bgk<L, Real, TAU1>(f, drho, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
             else
@@ -714,10 +718,9 @@ __global__ void __launch_bounds__(TX* TY, MINB)
                 fo[i * N + site] = f[i];
             });
         }
-        // no barrier needed here: the next writes to the rho ring (slot of plane
-        // zz + 1) and to the Laplacian ring (plane zz) come after the next
-        // iteration's first barrier, and the collision above reads neither
-        // (it reads rho planes zz - 3 .. zz - 1 and Laplacian planes zz - 3 .. zz - 1)
+        // no second barrier: the next iteration writes rho plane zz + 1 (a slot
+        // none of this iteration's reads use) before its barrier, and Laplacian
+        // plane zz only after it
     }
 }
 
