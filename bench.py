@@ -37,6 +37,8 @@ WORKLOADS = {
     "single_64": dict(ensemble="single_64", lattice="D3Q19", precision="fp32"),
     "large_256": dict(ensemble="large_256", lattice="D3Q19", precision="fp32"),
     "fss_160_fp64": dict(ensemble="fss_160", lattice="D3Q19", precision="fp64"),
+    "fss_160_64": dict(ensemble="fss_160_64", lattice="D3Q19", precision="fp32"),
+    "fss_60": dict(ensemble="fss_60", lattice="D3Q19", precision="fp32"),
 }
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
@@ -204,6 +206,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fss_160", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", default="default",
+                    help="step-kernel variant: 'default', 'auto' (autotuner, timed on this ensemble) or a row index")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
 
@@ -241,8 +245,17 @@ def main():
     es = 4 if wl["precision"] == "fp32" else 8
 
     stream = torch.cuda.current_stream()
+    rows = lb.kernel_variants(wl["lattice"])
+    if args.variant == "auto":
+        from paper_1202_4748_gb300 import autotune
+        best, _ = autotune.tune(systems, wl["precision"], cache=None)
+        vindex = rows.index(best)
+    elif args.variant == "default":
+        vindex = 0
+    else:
+        vindex = int(args.variant)
     ens = lb.Ensemble(systems, precision=wl["precision"], obs_every=LB_STEPS_PER_STEP,
-                      graph_chunk=LB_STEPS_PER_STEP)
+                      graph_chunk=LB_STEPS_PER_STEP, variant=vindex + 1)
     ens.init(amplitude=0.01)
     for _ in range(args.warmup):
         ens.step(LB_STEPS_PER_STEP)
@@ -335,7 +348,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if wl["precision"] == "fp32" else "f64", "data": "synthetic",
-            "config": describe(wl, systems),
+            "config": dict(describe(wl, systems), step_kernel_variant=list(rows[vindex]),
+                           variant_choice=args.variant if args.variant in ("auto", "default") else "row"),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
                          "traffic": traffic,

@@ -28,6 +28,7 @@ SIDES_3D = {
     "single_16": [16],
     "single_64": [64],
     "fss_160": [16, 24, 32, 48, 64],
+    "fss_160_64": [64],          # the 64^3 members of fss_160 (a profiling case larger than L2)
     "fss_60": [32, 48, 64, 96, 128],
     "large_256": [256],
 }
@@ -40,7 +41,7 @@ def _a_values(name):
         return [0.0]
     if name == "single_64":
         return [-0.002]
-    if name == "fss_160":
+    if name in ("fss_160", "fss_160_64"):
         return list(np.linspace(-0.004, 0.004, 8))
     if name == "fss_60":
         return list(np.linspace(-0.004, 0.004, 6))
@@ -48,7 +49,7 @@ def _a_values(name):
 
 
 def _replicas(name):
-    return {"fss_160": 4, "fss_60": 2}.get(name, 1)
+    return {"fss_160": 4, "fss_160_64": 4, "fss_60": 2}.get(name, 1)
 
 
 def system(lattice="D2Q9", coupling=None, n=64, a=0.0, b=0.1, kappa=0.01, kT=1e-4,
