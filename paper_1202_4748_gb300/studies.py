@@ -172,3 +172,49 @@ def statics(systems, steps, every, precision="fp32", kmax=6, warmup=0, graph_chu
     C = sk / (cnt * ns_tot)
     J = jk / (cnt[None, :] * ns_tot) / (s0["rho_c"] * s0["kT"])
     return dict(chi=fit["chi"], xi=fit["xi"], oz=fit, sk=C, jk_ratio=J, samples=ns_tot)
+
+
+def binder_cumulants(systems, steps, precision, obs_every=10, graph_chunk=0, amplitude=0.01):
+    """U_L = 1 - <m^4>/(3 <m^2>^2) per system and level after ``steps`` steps,
+    with the block sizes: (list of lists of (block side, U_L))."""
+    ens = Ensemble(systems, precision=precision, obs_every=obs_every, graph_chunk=graph_chunk)
+    try:
+        ens.init(amplitude=amplitude)
+        ens.step(steps)
+        out = []
+        for k, s in enumerate(systems):
+            levels, _ = ens.observables(k)
+            row = []
+            for L in levels:
+                if L["n"] <= 0:
+                    continue
+                d = ens.derive(L, s["kT"])
+                row.append((L["block"][0], d["U_L"]))
+            out.append(row)
+    finally:
+        ens.close()
+    return out
+
+
+def precision_accuracy(systems, steps, obs_every=10, max_block_fraction=1.0 / 8.0):
+    """Binder cumulants of the same systems and seeds in FP32 and FP64.
+
+    Systems are grouped by (side, a); within a group the replicas (different
+    seeds) give the statistical error sigma of the FP64 mean.  For every group
+    and every block size L <= max_block_fraction * S (the finite-size-scaling
+    range of the analysis) returns (side, a, L, mean U fp32, mean U fp64, sigma)."""
+    u32 = binder_cumulants(systems, steps, "fp32", obs_every)
+    u64 = binder_cumulants(systems, steps, "fp64", obs_every)
+    groups = {}
+    for k, s in enumerate(systems):
+        groups.setdefault((s["nx"], round(s["a"], 12)), []).append(k)
+    rows = []
+    for (side, a), ks in sorted(groups.items()):
+        for li, (L, _) in enumerate(u64[ks[0]]):
+            if L > max_block_fraction * side or L == side:
+                continue
+            v32 = np.array([u32[k][li][1] for k in ks])
+            v64 = np.array([u64[k][li][1] for k in ks])
+            sigma = float(np.std(v64, ddof=1) / math.sqrt(len(ks))) if len(ks) > 1 else float("nan")
+            rows.append((side, a, L, float(v32.mean()), float(v64.mean()), sigma))
+    return rows
