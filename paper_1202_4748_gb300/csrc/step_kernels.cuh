@@ -180,16 +180,11 @@ __device__ __forceinline__ void from_moments(const Real (&w)[L::Q], Real (&out)[
 //   m^eq_a - T_a(0) rho_c = T_a(0) (drho - 3 p0) + 9/2 rho u.M_a.u,
 //   (T F_i)_a = 9 u.M_a.F,   M_a,bc = sum_i t_i T_ai c_ib c_ic,
 // and f <- (1 - lam) f + T^-1 w with w = (lam drho, lam j + F, lam m^eq + (1 - lam/2) F^ + xi).
-template <class L, class Real, bool TAU1, class LapV>
-__device__ __forceinline__ void collide_guo_bgk(Real (&f)[L::Q], const Real drho, const LapV& lv, const SysDev& S,
-                                                const SysPhys<Real>& P, const uint32_t site, const int64_t step,
-                                                int* status) {
-    constexpr int Q = L::Q;
-    constexpr int K = Q - L::NC;
-    const Real rho = P.rho_c + drho;
-    if (!(rho > Real(0))) atomicOr(status, ST_RHO);
-    Real j[3] = {Real(0), Real(0), Real(0)};
-    sfor<1, Q>([&](auto I) {
+// j = sum_i c_i f_i (Eq. 62), summed in population order.
+template <class L, class Real>
+__device__ __forceinline__ void momentum_of(const Real (&f)[L::Q], Real (&j)[3]) {
+    j[0] = j[1] = j[2] = Real(0);
+    sfor<1, L::Q>([&](auto I) {
         constexpr int i = I;
         sfor<0, L::D>([&](auto A) {
             constexpr int a = A;
@@ -197,6 +192,19 @@ __device__ __forceinline__ void collide_guo_bgk(Real (&f)[L::Q], const Real drho
             if constexpr (L::c(i, a) == -1) j[a] -= f[i];
         });
     });
+}
+
+// Single-rate Guo collision from the conserved moments (drho, j) of the site;
+// f holds the pre-collision populations on entry unless TAU1 (fully relaxed:
+// the update does not read them) and the post-collision ones on exit.
+template <class L, class Real, bool TAU1, class LapV>
+__device__ __forceinline__ void collide_guo_bgk_m(Real (&f)[L::Q], const Real drho, const Real (&j)[3], const LapV& lv,
+                                                  const SysDev& S, const SysPhys<Real>& P, const uint32_t site,
+                                                  const int64_t step, int* status) {
+    constexpr int Q = L::Q;
+    constexpr int K = Q - L::NC;
+    const Real rho = P.rho_c + drho;
+    if (!(rho > Real(0))) atomicOr(status, ST_RHO);
     const Real irc = P.inv_rho_c;
     const Real phi = drho * irc;
     const Real A_ = P.a, B_ = P.b, kap = P.kappa;
@@ -264,6 +272,15 @@ __device__ __forceinline__ void collide_guo_bgk(Real (&f)[L::Q], const Real drho
             f[i] = keep * f[i] + out[i];
         });
     }
+}
+
+template <class L, class Real, bool TAU1, class LapV>
+__device__ __forceinline__ void collide_guo_bgk(Real (&f)[L::Q], const Real drho, const LapV& lv, const SysDev& S,
+                                                const SysPhys<Real>& P, const uint32_t site, const int64_t step,
+                                                int* status) {
+    Real j[3];
+    momentum_of<L, Real>(f, j);
+    collide_guo_bgk_m<L, Real, TAU1>(f, drho, j, lv, S, P, site, step, status);
 }
 
 // Collision of one site given its pulled deviations f[], the density halo and
@@ -622,12 +639,18 @@ __global__ void __launch_bounds__(TX* TY, MINB)
     // barrier.  Ring sizes: rho planes zz-2..zz are read by the Laplacian while a
     // thread past the barrier may already write plane zz+1 (4 slots); Laplacian
     // planes zz-4..zz-2 are read by the collision while plane zz-1 is written (4).
-    constexpr int NR = 4;                                             // rho ring planes
+    // PULLFREE (every mode fully relaxed): the collision needs only the conserved
+    // moments of the site, which the footprint pass already sums; they are kept
+    // in a ring (sj, with the density in srho) instead of pulling the site again.
+    // The collided plane zz - 3 then stays live while plane zz + 1 is written: 5 slots.
+    constexpr bool PULLFREE = MODE == 2;
+    constexpr int NR = PULLFREE ? 5 : 4;                              // rho ring planes
     constexpr int LX = TX + 2, LY = TY + 2, LP = LX * LY;             // Laplacian plane
     constexpr int NL = 4;
     constexpr int NT = TX * TY;
     __shared__ Real srho[NR * SP];
     __shared__ Real slap[NL * LP];
+    __shared__ Real sj[PULLFREE ? NR * 3 * NT : 1];
 
     const int4 tl = A.tiles[blockIdx.x];
     const SysDev& S = A.sys[tl.x];
@@ -670,6 +693,16 @@ __global__ void __launch_bounds__(TX* TY, MINB)
                     Real g[Q];
                     pull_site<L, Real>(fb, N, nb, g);
                     sfor<0, Q>([&](auto I) { v += g[decltype(I)::value]; });
+                    if constexpr (PULLFREE) {
+                        const int px = idx % SX - H, py = idx / SX - H;
+                        if (px >= 0 && px < TX && py >= 0 && py < TY) {
+                            Real jm[3];
+                            momentum_of<L, Real>(g, jm);
+                            sfor<0, 3>([&](auto A) {
+                                sj[(slot * 3 + int(A)) * NT + py * TX + px] = jm[decltype(A)::value];
+                            });
+                        }
+                    }
                 }
                 srho[slot * SP + idx] = v;
             }
@@ -700,16 +733,25 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         // collision of plane zc = zz - H - 1
         if (collide) {
             Real f[Q];
-            pull_site<L, Real>(fb, N, Nbr(x, y, zc, nx, ny, nz, true), f);
             Real drho = Real(0);
-            sfor<0, Q>([&](auto I) { drho += f[decltype(I)::value]; });
+            Real jc[3];
+            const int cslot = (zc - z0 + 2 * NR) % NR;
+            if constexpr (PULLFREE) {
+                drho = srho[cslot * SP + (ty + H) * SX + (tx + H)];
+                sfor<0, 3>([&](auto A) { jc[decltype(A)::value] = sj[(cslot * 3 + int(A)) * NT + tid]; });
+            } else {
+                pull_site<L, Real>(fb, N, Nbr(x, y, zc, nx, ny, nz, true), f);
+                sfor<0, Q>([&](auto I) { drho += f[decltype(I)::value]; });
+            }
             const int site = site_index(x, y, zc, nx, ny);
             // the Guo collision reads only the Laplacian planes zc-1..zc+1 around the
             // site (a 3-plane view); the density view is unused by this coupling
             const RingView<Real, SX> rv{srho, 0, 0, 0, (ty + H) * SX + (tx + H)};
             const RingView<Real, LX> lv{slap, ((zc - 1 - z0 + 2 * NL) % NL) * LP, ((zc - z0 + 2 * NL) % NL) * LP,
                                         ((zc + 1 - z0 + 2 * NL) % NL) * LP, (ty + 1) * LX + (tx + 1)};
-            if constexpr (CP == GUO && BGK_ONLY)
+            if constexpr (PULLFREE)
+                collide_guo_bgk_m<L, Real, true>(f, drho, jc, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
+            else if constexpr (BGK_ONLY)
                 collide_guo_bgk<L, Real, TAU1>(f, drho, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
             else
                 collide_site<L, CP, Real, BGK_ONLY>(f, drho, rv, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
