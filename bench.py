@@ -322,8 +322,7 @@ def main():
     for _ in range(k_e2e):
         ens.init(rho=rho_np)                     # H2D of the step's input density field
         ens.step(LB_STEPS_PER_STEP)
-        for k in range(n_sys):                   # D2H of the step's result (observables)
-            levels, _ = ens.observables(k)
+        for levels, _ in ens.observables_all():  # D2H of the step's result (observables)
             d2h += 64 * len(levels) + 64
     barrier()
     e2e_s = time.perf_counter() - t0

@@ -190,6 +190,18 @@ lb_status lb_sync(lb_ctx* ctx);
 lb_status lb_observables(lb_ctx* ctx, int sys, lb_obs_level* h_levels, int max_levels,
                          int* n_levels, lb_obs_global* h_global);
 
+/* The accumulators of every system at once (one device-to-host copy of each
+ * array and one synchronisation; same content as lb_observables per system).
+ * h_levels receives the levels of system 0, then system 1, ... (at most
+ * max_levels entries in total); level_first[k] is the index of system k's
+ * first level and level_first[n_systems] the total (array of n_systems + 1,
+ * filled even when h_levels is too short); h_globals (nullable) receives
+ * n_systems entries.  Errors: LB_ERR_ARG (null level_first, or max_levels
+ * smaller than the total while h_levels is not null), device errors,
+ * LB_ERR_CUDA. */
+lb_status lb_observables_all(lb_ctx* ctx, lb_obs_level* h_levels, int max_levels, int* level_first,
+                             lb_obs_global* h_globals);
+
 /* Derived quantities of one level at noise temperature kT (Eqs. 47-50):
  * out[0] = M_L = <|m|>, out[1] = chi_L (Eq. 48), out[2] = chi_L low-T form
  * (Eq. 49), out[3] = c_H,L (Eq. 50), out[4] = Binder U_L = 1 - <m^4>/(3<m^2>^2),

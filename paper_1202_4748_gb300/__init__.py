@@ -77,6 +77,8 @@ _SIG = {
     "lb_sync": (ctypes.c_int, [_P]),
     "lb_observables": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(lb_obs_level), ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(lb_obs_global)]),
+    "lb_observables_all": (ctypes.c_int, [_P, ctypes.POINTER(lb_obs_level), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(lb_obs_global)]),
     "lb_derive": (ctypes.c_int, [ctypes.POINTER(lb_obs_level), ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "lb_histogram": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double)]),
@@ -301,6 +303,27 @@ class Ensemble:
         glob = dict(step=g.step, n_samples=g.n_samples, mass0=g.mass0, mass=g.mass,
                     momentum=tuple(g.momentum), rho_mean=g.rho_mean)
         return levels, glob
+
+    def observables_all(self):
+        """[(levels, global)] for every system, read with one copy and one synchronisation."""
+        n = len(self.systems)
+        first = (ctypes.c_int * (n + 1))()
+        check(lb_observables_all(self.ctx, None, 0, first, None), "lb_observables_all")
+        total = first[n]
+        lv = (lb_obs_level * max(total, 1))()
+        gl = (lb_obs_global * n)()
+        check(lb_observables_all(self.ctx, lv, total, first, gl), "lb_observables_all")
+        out = []
+        for k in range(n):
+            levels = []
+            for l in range(first[k], first[k + 1]):
+                L = lv[l]
+                levels.append(dict(block=(L.bx, L.by, L.bz), n=L.n, sum_m=L.sum_m, sum_m2=L.sum_m2,
+                                   sum_abs_m=L.sum_abs_m, sum_m4=L.sum_m4, sum_e=L.sum_e, sum_e2=L.sum_e2))
+            g = gl[k]
+            out.append((levels, dict(step=g.step, n_samples=g.n_samples, mass0=g.mass0, mass=g.mass,
+                                     momentum=tuple(g.momentum), rho_mean=g.rho_mean)))
+        return out
 
     def derive(self, level, kT):
         L = lb_obs_level()

@@ -907,6 +907,56 @@ lb_status lb_observables(lb_ctx* c, int sys, lb_obs_level* h_levels, int max_lev
     return s;
 }
 
+lb_status lb_observables_all(lb_ctx* c, lb_obs_level* h_levels, int max_levels, int* level_first,
+                             lb_obs_global* h_globals) {
+    if (!c || !level_first) return LB_ERR_ARG;
+    const Plan& P = c->P;
+    int total = 0;
+    for (int k = 0; k < c->n_sys; ++k) {
+        level_first[k] = total;
+        total += int(c->sys[k].lv.size());
+    }
+    level_first[c->n_sys] = total;
+    if (h_levels && max_levels < total) return LB_ERR_ARG;
+    std::vector<double> acc(7 * size_t(P.n_levels)), glob(8 * size_t(c->n_sys));
+    LB_CHECK(cudaMemcpyAsync(acc.data(), c->ws + P.acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost,
+                             c->stream));
+    LB_CHECK(cudaMemcpyAsync(glob.data(), c->ws + P.glob, sizeof(double) * glob.size(), cudaMemcpyDeviceToHost,
+                             c->stream));
+    lb_status s = sync_and_check(c);
+    for (int k = 0; k < c->n_sys && h_levels; ++k) {
+        const SysHost& h = c->sys[k];
+        for (size_t l = 0; l < h.lv.size(); ++l) {
+            const double* a = acc.data() + 7 * (size_t(h.lv_first) + l);
+            lb_obs_level& o = h_levels[level_first[k] + int(l)];
+            o.bx = h.lv[l].bx;
+            o.by = h.lv[l].by;
+            o.bz = h.lv[l].bz;
+            o.pad = 0;
+            o.n = a[0];
+            o.sum_m = a[1];
+            o.sum_m2 = a[2];
+            o.sum_abs_m = a[3];
+            o.sum_m4 = a[4];
+            o.sum_e = a[5];
+            o.sum_e2 = a[6];
+        }
+    }
+    for (int k = 0; k < c->n_sys && h_globals; ++k) {
+        const double* g = glob.data() + 8 * size_t(k);
+        lb_obs_global& o = h_globals[k];
+        o.step = c->step;
+        o.n_samples = int64_t(g[0]);
+        o.mass0 = g[1];
+        o.mass = g[2];
+        o.momentum[0] = g[3];
+        o.momentum[1] = g[4];
+        o.momentum[2] = g[5];
+        o.rho_mean = g[6];
+    }
+    return s;
+}
+
 lb_status lb_derive(const lb_obs_level* L, double kT, double out[6]) {
     if (!L || !out || !(L->n > 0) || !(kT > 0)) return LB_ERR_ARG;
     const double n = L->n, v = double(L->bx) * L->by * L->bz;

@@ -29,6 +29,11 @@ def test_every_declared_symbol_is_exported():
     assert sorted(lb.EXPORTED) == names
 
 
+def test_observables_all_rejects_missing_arguments():
+    import paper_1202_4748_gb300 as lb
+    assert lb.lb_observables_all(None, None, 0, None, None) == lb.LB_ERR_ARG
+
+
 def test_status_strings_and_version():
     import paper_1202_4748_gb300 as lb
     assert lb.lb_status_string(0) == b"ok"

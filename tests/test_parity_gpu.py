@@ -343,3 +343,21 @@ def test_autotuner_times_every_variant_and_caches(lb, tmp_path):
         e.close()
     for r in runs[1:]:
         assert all(np.array_equal(a, b) for a, b in zip(runs[0], r))
+
+
+def test_observables_of_all_systems_in_one_read(lb):
+    systems = synth.ensemble("fss_160", "D3Q19")[::16]
+    ens = lb.Ensemble(systems, precision="fp32", obs_every=5)
+    ens.init()
+    ens.step(20)
+    both = ens.observables_all()
+    assert len(both) == len(systems)
+    for k in range(len(systems)):
+        assert both[k] == ens.observables(k)
+    # a level array shorter than the total is rejected, the counts still come back
+    import ctypes
+    first = (ctypes.c_int * (len(systems) + 1))()
+    short = (lb.lb_obs_level * 1)()
+    assert lb.lb_observables_all(ens.ctx, short, 1, first, None) == lb.LB_ERR_ARG
+    assert first[len(systems)] == sum(len(b[0]) for b in both)
+    ens.close()
