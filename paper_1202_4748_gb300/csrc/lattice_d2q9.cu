@@ -6,7 +6,8 @@ namespace lbf {
 
 namespace {
 // (x, y, 1, resident CTAs per SM (0 = default), flags (0))
-constexpr int kTiles[][5] = {{32, 8, 1, 0, 0}, {64, 4, 1, 0, 0}, {128, 2, 1, 0, 0}};
+constexpr int kTiles[][5] = {{32, 8, 1, 0, 0}, {64, 4, 1, 0, 0}, {128, 2, 1, 0, 0},
+                             {32, 4, 1, 0, 0}, {32, 16, 1, 0, 0}, {64, 8, 1, 0, 0}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
 
 template <int CP, class Real>
@@ -15,6 +16,9 @@ cudaError_t step_tile(const StepLaunch& a, cudaStream_t st) {
         case 0: return step_one<D2Q9, CP, Real, 32, 8, 1>(a, st);
         case 1: return step_one<D2Q9, CP, Real, 64, 4, 1>(a, st);
         case 2: return step_one<D2Q9, CP, Real, 128, 2, 1>(a, st);
+        case 3: return step_one<D2Q9, CP, Real, 32, 4, 1>(a, st);
+        case 4: return step_one<D2Q9, CP, Real, 32, 16, 1>(a, st);
+        case 5: return step_one<D2Q9, CP, Real, 64, 8, 1>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }
