@@ -58,7 +58,8 @@ typedef enum {
     LB_ERR_UNSUPPORTED = -7,         /* valid but not supported combination         */
     LB_ERR_STATE = -8,               /* sticky error or call out of order           */
     LB_ERR_IO = -9,                  /* checkpoint file error                       */
-    LB_ERR_NO_ROOT = -10             /* a self-consistency equation has no solution  */
+    LB_ERR_NO_ROOT = -10,            /* a self-consistency equation has no solution  */
+    LB_ERR_TIMEOUT = -11             /* a bounded device-side wait ran out            */
 } lb_status;
 
 enum { LB_D2Q9 = 0, LB_D3Q19 = 1 };
@@ -343,10 +344,21 @@ lb_status lb_load(lb_ctx* ctx, const char* path);
 
 /* Step-kernel variants compiled for a lattice (LB_D2Q9 or LB_D3Q19): writes up
  * to max_rows rows of 5 int32 (tile x, tile y, tile z or z-chunk, resident CTAs
- * per SM of the register budget (0 = default), flags (0, reserved)) into out
+ * per SM of the register budget (0 = default), producer warps: 0 = every thread
+ * stages and collides its own column, > 0 = warp-specialised kernel with that
+ * many staging warps, used on the fully relaxed FP32 path) into out
  * (nullable) and returns the number of variants (negative lb_status on error).
  * Row 0 is the default.  Used by the autotuner; no device call. */
 int lb_kernel_variants(int lattice, int32_t* out, int max_rows);
+
+/* Self-test of the bounded device-side waits (the warp-specialised step
+ * kernel's hand-offs give up after about 0.3 s instead of hanging): launches one
+ * CTA on `cuda_stream` that waits on a shared-memory barrier nothing arrives
+ * at, and reads back the status word d_status (one int of caller-owned device
+ * memory, zeroed here).  Returns LB_ERR_TIMEOUT when the wait gave up and
+ * reported it, as it must; LB_ERR_STATE if the wait completed; LB_ERR_CUDA on
+ * a launch or copy error.  The paper has no counterpart. */
+lb_status lb_selftest_wait_timeout(int* d_status, void* cuda_stream);
 
 /* Number of kernels this context has launched so far (graph replays count
  * every kernel node).  Instrumentation for benchmarks; no device call. */

@@ -24,7 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 LB_OK = 0
 LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_WORKSPACE = -1, -2, -3
 LB_ERR_NONPOSITIVE_DENSITY, LB_ERR_NOISE_NOT_PD, LB_ERR_NONFINITE = -4, -5, -6
-LB_ERR_UNSUPPORTED, LB_ERR_STATE, LB_ERR_IO, LB_ERR_NO_ROOT = -7, -8, -9, -10
+LB_ERR_UNSUPPORTED, LB_ERR_STATE, LB_ERR_IO, LB_ERR_NO_ROOT, LB_ERR_TIMEOUT = -7, -8, -9, -10, -11
 LB_D2Q9, LB_D3Q19 = 0, 1
 LB_MODEQ, LB_GUO = 0, 1
 LB_FP64, LB_FP32_DEVIATION = 0, 1
@@ -101,6 +101,7 @@ _SIG = {
     "lb_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "lb_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "lb_kernel_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "lb_selftest_wait_timeout": (ctypes.c_int, [_P, _P]),
     "lb_kernel_variants": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int]),
     "lb_block_moments_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
                                                 ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P]),
@@ -227,7 +228,7 @@ def histogram_estimates(counts, lo, hi, vol, kT, m_cut=0.0, frac=0.2):
 
 
 def kernel_variants(lattice):
-    """Compiled step-kernel variants of a lattice: list of (x, y, z, occupancy, flags)."""
+    """Compiled step-kernel variants of a lattice: list of (x, y, z, occupancy, producer warps)."""
     code = _LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
     n = lb_kernel_variants(code, None, 0)
     if n < 0:

@@ -1,13 +1,13 @@
 """Step-kernel variant autotuner.
 
 For a given ensemble, every step-kernel variant compiled into the library for
-its lattice (tile shape and register budget; listed by
+its lattice (tile shape, register budget, producer warps; listed by
 ``lb_kernel_variants``) is timed on the device (CUDA events around a plain run
 of step launches, after a warm-up) through the public API, and the fastest is
 returned.  Results are cached in a JSON file keyed by lattice, coupling,
 precision and the multiset of system sizes, so a later run of the same ensemble
 picks its variant without re-timing.  A variant is named by its row
-``(x, y, z, occupancy, flags)``; ``Ensemble(..., variant=variant_index(...))``
+``(x, y, z, occupancy, producer warps)``; ``Ensemble(..., variant=variant_index(...))``
 selects it.
 """
 import json

@@ -625,6 +625,7 @@ lb_status read_status(lb_ctx* c) {
     if (st & ST_RHO) return LB_ERR_NONPOSITIVE_DENSITY;
     if (st & ST_NOISE) return LB_ERR_NOISE_NOT_PD;
     if (st & ST_NONFINITE) return LB_ERR_NONFINITE;
+    if (st & ST_TIMEOUT) return LB_ERR_TIMEOUT;
     return LB_OK;
 }
 
@@ -672,6 +673,7 @@ const char* lb_status_string(lb_status s) {
         case LB_ERR_STATE: return "invalid state (sticky error or missing initialisation)";
         case LB_ERR_IO: return "checkpoint I/O error";
         case LB_ERR_NO_ROOT: return "no solution of the self-consistency equation";
+        case LB_ERR_TIMEOUT: return "a bounded device-side wait timed out";
     }
     return "unknown status";
 }
@@ -1362,6 +1364,18 @@ lb_status lb_load(lb_ctx* c, const char* path) {
     c->sticky = LB_OK;
     c->has_state = true;
     return LB_OK;
+}
+
+lb_status lb_selftest_wait_timeout(int* d_status, void* stream) {
+    if (!d_status) return LB_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int h = 0;
+    if (cudaMemsetAsync(d_status, 0, sizeof(int), st) != cudaSuccess) return LB_ERR_CUDA;
+    if (launch_selftest_wait(d_status, st) != cudaSuccess) return LB_ERR_CUDA;
+    if (cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LB_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return LB_ERR_CUDA;
+    if (h & (1 << 30)) return LB_ERR_STATE;
+    return (h & ST_TIMEOUT) ? LB_ERR_TIMEOUT : LB_ERR_STATE;
 }
 
 int lb_kernel_variants(int lattice, int32_t* out, int max_rows) {

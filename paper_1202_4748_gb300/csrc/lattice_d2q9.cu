@@ -5,7 +5,7 @@
 namespace lbf {
 
 namespace {
-// (x, y, 1, resident CTAs per SM (0 = default), flags (0))
+// (x, y, 1, resident CTAs per SM (0 = default), producer warps (0: none))
 constexpr int kTiles[][5] = {{32, 8, 1, 0, 0}, {64, 4, 1, 0, 0}, {128, 2, 1, 0, 0},
                              {32, 4, 1, 0, 0}, {32, 16, 1, 0, 0}, {64, 8, 1, 0, 0}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));

@@ -1,5 +1,6 @@
 // D3Q19 instantiations (3-D variant): Guo-forced form with the Landau
 // pressure in the equilibrium, FP64 and FP32-deviation storage.
+#include <type_traits>
 #include <utility>
 
 #include "lattice_tu.cuh"
@@ -7,14 +8,22 @@
 namespace lbf {
 
 namespace {
-// (x, y, z-chunk, resident CTAs per SM, unused) of the z-marching kernel; the
-// first entry is the default (fastest on the 160-system ensemble by the autotuner)
-constexpr int kTiles[][5] = {{16, 8, 16, 6, 0}, {16, 8, 32, 6, 0}, {16, 8, 16, 5, 0}, {16, 8, 16, 8, 0},
-                             {16, 16, 16, 4, 0}, {16, 16, 32, 4, 0}, {16, 16, 8, 4, 0}};
+// (x, y, z-chunk, resident CTAs per SM, producer warps) of the z-marching
+// kernel: producer warps 0 = every thread stages and collides its own column;
+// > 0 = warp-specialised kernel (used on the fully relaxed FP32 path; the other
+// paths run the plain kernel with the same tile).  The first entry is the
+// default (fastest on the 160-system ensemble by the autotuner).
+constexpr int kTiles[][5] = {{16, 8, 32, 3, 4}, {16, 8, 64, 3, 4}, {16, 8, 16, 3, 4}, {16, 8, 16, 6, 0},
+                             {16, 8, 32, 6, 0}, {16, 16, 16, 4, 0}, {16, 16, 32, 4, 0}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
 
 template <int CP, class Real, int I>
 cudaError_t step_variant(const StepLaunch& a, cudaStream_t st) {
+    constexpr int PW = kTiles[I][4];
+    if constexpr (PW > 0 && std::is_same<Real, float>::value) {
+        if (a.bgk_only == 2)
+            return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3]>(a, st);
+    }
     return step_z<D3Q19, CP, Real, kTiles[I][0], kTiles[I][1], kTiles[I][2], kTiles[I][3]>(a, st);
 }
 

@@ -48,6 +48,23 @@ cudaError_t step_z(const StepLaunch& a, cudaStream_t st) {
     return step_z_mode<L, CP, Real, TX, TY, ZC, MB, 0>(a, st);
 }
 
+// Warp-specialised launch (fully relaxed Guo path, FP32): TX x TY consumer
+// threads and PW producer warps per CTA.
+template <class L, int TX, int TY, int ZC, int PW, int MINB>
+cudaError_t step_ws(const StepLaunch& a, cudaStream_t st) {
+    StepArgs<float> A;
+    A.sys = a.sys;
+    A.phys = static_cast<const SysPhys<float>*>(a.phys);
+    A.tiles = a.tiles;
+    A.fin = static_cast<const float*>(a.fin);
+    A.fout = static_cast<float*>(a.fout);
+    A.step_ptr = a.step_ptr;
+    A.k = a.k;
+    A.status = a.status;
+    step_kernel_ws<L, TX, TY, ZC, PW, MINB><<<a.n_tiles, TX * TY + 32 * PW, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
 template <class L, int CP, class Real, int TX, int TY, int TZ>
 cudaError_t step_one(const StepLaunch& a, cudaStream_t st) {
     if (a.bgk_only == 2) return step_one_mode<L, CP, Real, TX, TY, TZ, 2>(a, st);

@@ -266,6 +266,47 @@ __device__ __forceinline__ int wrapm(int x, int n) {
 }
 
 // Device status bits (OR-ed by kernels, mapped to lb_status on the host).
-enum : int { ST_RHO = 1, ST_NOISE = 2, ST_NONFINITE = 4 };
+enum : int { ST_RHO = 1, ST_NOISE = 2, ST_NONFINITE = 4, ST_TIMEOUT = 8 };
+
+// ---- mbarrier (shared-memory arrival barrier) helpers ----------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+// arrive (release semantics at CTA scope: the caller's earlier shared-memory
+// accesses are ordered before the phase can complete)
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(b))
+                 : "memory");
+}
+// non-blocking test (acquire semantics) of the completion of the phase with this parity
+__device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after about 0.3 s, or at once when *abort is set,
+// sets *abort and the status bit, and returns false; control flow then
+// continues (results are flagged invalid), so no thread hangs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* abort, int* status) {
+    for (int i = 0; i < (1 << 22); ++i) {
+        if (mbar_test(b, parity)) return true;
+        if (*abort) return false;
+        if (i >= 32) __nanosleep(64);
+    }
+    *abort = 1;
+    atomicOr(status, ST_TIMEOUT);
+    return false;
+}
+// Named barrier over `count` threads (a multiple of 32) of the CTA.
+__device__ __forceinline__ void named_barrier(int id, int count) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
+}
 
 }  // namespace lbf

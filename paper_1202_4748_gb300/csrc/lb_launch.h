@@ -27,7 +27,7 @@ struct StepLaunch {
 };
 
 // Step-kernel variants compiled for each lattice: (x, y, z, resident CTAs per
-// SM, flags (0)); index = tile_id.
+// SM, producer warps); index = tile_id.
 int tile_shapes_d2q9(int (*out)[5], int max);
 int tile_shapes_d3q19(int (*out)[5], int max);
 
@@ -83,6 +83,9 @@ struct HistDev {
     int32_t nbins;
     double lo, inv_w;       // bin of m: floor((m - lo) * inv_w), inv_w = nbins / (hi - lo)
 };
+
+// One CTA whose bounded wait on a barrier nothing arrives at must time out.
+cudaError_t launch_selftest_wait(int* status, cudaStream_t st);
 
 cudaError_t launch_init_noise(const SysDev* sys, const int4* items, int n_items, double amp, double* d,
                               double* partial, cudaStream_t st);

@@ -242,6 +242,19 @@ __global__ void obs_accum_kernel(const LevelDev* __restrict__ lvv, int n_levels,
 
 __global__ void advance_kernel(int64_t* step, int64_t n) { *step += n; }
 
+// Self-test of the bounded waits: one CTA waits on an mbarrier that nothing
+// arrives at; every thread must give up and the status must record it.
+__global__ void selftest_wait_kernel(int* status) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+    }
+    __syncthreads();
+    if (mbar_wait(&bar, 0u, &abort_flag, status)) atomicOr(status, 1 << 30);   // cannot complete
+}
+
 }  // namespace
 
 cudaError_t launch_init_noise(const SysDev* sys, const int4* items, int n_items, double amp, double* d,
@@ -293,6 +306,11 @@ cudaError_t launch_obs_accum(const LevelDev* lv, int n_levels_total, const doubl
 
 cudaError_t launch_advance(int64_t* step, int64_t n, cudaStream_t st) {
     advance_kernel<<<1, 1, 0, st>>>(step, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_wait(int* status, cudaStream_t st) {
+    selftest_wait_kernel<<<1, 64, 0, st>>>(status);
     return cudaGetLastError();
 }
 

@@ -766,4 +766,156 @@ __global__ void __launch_bounds__(TX* TY, MINB)
     }
 }
 
+// Warp-specialised z-marching step for the fully relaxed Guo path (every mode
+// at tau = 1, FP32): PW producer warps stage each plane -- the footprint pulls,
+// the density on the tile + halo, the momentum of the tile sites and the
+// Laplacian on the tile + 1 -- into shared-memory rings; TX x TY consumer
+// threads collide one site each from those rings and store.  The consumers
+// read no global memory, so their arithmetic overlaps the producers' loads.
+//
+// Rings (R planes, data slot of plane z: (z - z0 + H) % R): density and
+// momentum of footprint planes z0 - H .. z1 + H - 1, Laplacian planes
+// z0 - 1 .. z1.  mbarriers: full[(zl - z0 + 1) % R] completes when all
+// producers have written Laplacian plane zl (and so every plane the collision
+// of zl - 1 reads); empty[(zc - z0) % R] completes when all consumers have
+// collided plane zc.  Before writing footprint plane zz (slot of zz - R) the
+// producers wait for the collision of plane zz - R; that also frees the
+// Laplacian slot written next.  A phase of one slot cannot complete twice
+// before its waiter looks (each side runs at most R - 2 planes ahead), so the
+// parity of the use count identifies the phase.  Every wait is bounded
+// (mbar_wait): a timeout flags the CTA and the status, and all threads keep
+// the same control flow, so the producers' named barrier is always reached.
+template <class L, int TX, int TY, int ZC, int PW, int MINB>
+__global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const StepArgs<float> A) {
+    using Real = float;
+    static_assert(L::D == 3, "z-marching is for 3-D lattices");
+    constexpr int Q = L::Q;
+    constexpr int H = HaloOf<L, GUO>::H;
+    constexpr int SX = TX + 2 * H, SY = TY + 2 * H, SP = SX * SY;     // rho footprint plane
+    constexpr int LX = TX + 2, LY = TY + 2, LP = LX * LY;             // Laplacian plane
+    constexpr int NC = TX * TY;                                       // consumer threads
+    constexpr int NP = 32 * PW;                                       // producer threads
+    constexpr int R = 6;                                              // ring planes
+    static_assert(R >= 4, "ring too short for the plane lags");
+    __shared__ Real srho[R * SP];
+    __shared__ Real slap[R * LP];
+    __shared__ Real sj[R * 3 * NC];
+    __shared__ uint64_t full[R], empty[R];
+    __shared__ int abort_flag;
+
+    const int4 tl = A.tiles[blockIdx.x];
+    const SysDev& S = A.sys[tl.x];
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const int N = S.ns;
+    const int z0 = tl.w, z1 = min(z0 + ZC, nz);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int r = 0; r < R; ++r) {
+            mbar_init(&full[r], NP);
+            mbar_init(&empty[r], NC);
+        }
+        abort_flag = 0;
+    }
+    __syncthreads();
+    auto dslot = [&](int z) { return (z - z0 + H) % R; };
+
+    if (tid >= NC) {
+        // ---------------- producers ----------------
+        const Real* __restrict__ fb = A.fin + S.pop_offset;
+        const int ptid = tid - NC;
+        const bool sm = S.small != 0;
+        for (int zz = z0 - H; zz < z1 + H; ++zz) {
+            const int zw = zz - R;                       // plane whose slots this iteration reuses
+            if (zw >= z0) mbar_wait(&empty[(zw - z0) % R], unsigned(((zw - z0) / R) & 1), &abort_flag, A.status);
+            const int slot = dslot(zz);
+            const int wz = sm ? wrapm(zz, nz) : wrap2(zz, nz);
+            // every footprint site of this producer thread is requested before any
+            // is summed (FS sites per thread, FS x Q loads in flight)
+            constexpr int FS = (SP + NP - 1) / NP;
+            Real g[FS][Q];
+            bool inb[FS];
+            sfor<0, FS>([&](auto SI) {
+                constexpr int si = SI;
+                const int idx = ptid + si * NP;
+                const int px = idx % SX, py = idx / SX;
+                const int gx = tl.y + px - H, gy = tl.z + py - H;
+                inb[si] = idx < SP && gx < nx + H && gy < ny + H;
+                if (inb[si]) {
+                    const Nbr nb(sm ? wrapm(gx, nx) : wrap2(gx, nx), sm ? wrapm(gy, ny) : wrap2(gy, ny), wz, nx, ny,
+                                 nz, true);
+                    pull_site<L, Real>(fb, N, nb, g[si]);
+                }
+            });
+            sfor<0, FS>([&](auto SI) {
+                constexpr int si = SI;
+                const int idx = ptid + si * NP;
+                if (idx < SP) {
+                    Real v = Real(0);
+                    if (inb[si]) {
+                        sfor<0, Q>([&](auto I) { v += g[si][decltype(I)::value]; });
+                        const int ix = idx % SX - H, iy = idx / SX - H;
+                        if (ix >= 0 && ix < TX && iy >= 0 && iy < TY) {
+                            Real jm[3];
+                            momentum_of<L, Real>(g[si], jm);
+                            sfor<0, 3>([&](auto C) {
+                                sj[(slot * 3 + int(C)) * NC + iy * TX + ix] = jm[decltype(C)::value];
+                            });
+                        }
+                    }
+                    srho[slot * SP + idx] = v;
+                }
+            });
+            named_barrier(1, NP);                        // density plane zz complete (producers)
+            const int zl = zz - 1;                       // Laplacian plane (needs density zl-1 .. zl+1)
+            if (zl >= z0 - 1) {
+                const int r0 = dslot(zl) * SP, rm = dslot(zl - 1) * SP, rp = dslot(zl + 1) * SP;
+                const int lslot = dslot(zl);
+                for (int idx = ptid; idx < LP; idx += NP) {
+                    const int px = idx % LX, py = idx / LX;
+                    const int c = (py + H - 1) * SX + (px + H - 1);
+                    const Real rc = srho[r0 + c];
+                    Real lap = Real(0);
+                    sfor<1, Q>([&](auto I) {
+                        constexpr int i = I;
+                        constexpr int cz = L::c(i, 2);
+                        constexpr int off = L::c(i, 0) + SX * L::c(i, 1);
+                        const int pl = cz == 0 ? r0 : (cz > 0 ? rp : rm);
+                        lap += Real(6.0 * L::w(i)) * (srho[pl + c + off] - rc);
+                    });
+                    slap[lslot * LP + idx] = lap;
+                }
+                mbar_arrive(&full[(zl - z0 + 1) % R]);
+            }
+        }
+    } else {
+        // ---------------- consumers ----------------
+        Real* __restrict__ fo = A.fout + S.pop_offset;
+        const int64_t step = *A.step_ptr + A.k;
+        const int tx = tid % TX, ty = tid / TX;
+        const int x = tl.y + tx, y = tl.z + ty;
+        const bool valid_xy = x < nx && y < ny;
+        for (int zc = z0; zc < z1; ++zc) {
+            const int zl = zc + 1;                       // the last Laplacian plane the collision reads
+            const bool ok = mbar_wait(&full[(zl - z0 + 1) % R], unsigned(((zl - z0 + 1) / R) & 1), &abort_flag,
+                                      A.status);
+            if (valid_xy && ok) {
+                const int cs = dslot(zc);
+                const Real drho = srho[cs * SP + (ty + H) * SX + (tx + H)];
+                Real jc[3];
+                sfor<0, 3>([&](auto C) { jc[decltype(C)::value] = sj[(cs * 3 + int(C)) * NC + tid]; });
+                const RingView<Real, LX> lv{slap, dslot(zc - 1) * LP, cs * LP, dslot(zc + 1) * LP,
+                                            (ty + 1) * LX + (tx + 1)};
+                const int site = site_index(x, y, zc, nx, ny);
+                Real f[Q];
+                collide_guo_bgk_m<L, Real, true>(f, drho, jc, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
+                sfor<0, Q>([&](auto I) {
+                    constexpr int i = I;
+                    fo[i * N + site] = f[i];
+                });
+            }
+            mbar_arrive(&empty[(zc - z0) % R]);
+        }
+    }
+}
+
 }  // namespace lbf

@@ -37,7 +37,7 @@ def test_observables_all_rejects_missing_arguments():
 def test_status_strings_and_version():
     import paper_1202_4748_gb300 as lb
     assert lb.lb_status_string(0) == b"ok"
-    for code in range(-10, 0):
+    for code in range(-11, 0):
         assert lb.lb_status_string(code) != b"unknown status"
     assert b"sm_103a" in lb.lb_version()
 
@@ -135,9 +135,11 @@ def test_kernel_variant_table():
     for lat in ("D2Q9", "D3Q19"):
         rows = lb.kernel_variants(lat)
         assert len(rows) >= 3 and len(set(rows)) == len(rows)
-        for x, y, z, occ, flags in rows:
-            assert x > 0 and y > 0 and z > 0 and occ >= 0 and flags == 0
-            assert x * y <= 1024 and x % 16 == 0
+        for x, y, z, occ, pw in rows:
+            assert x > 0 and y > 0 and z > 0 and occ >= 0 and pw >= 0
+            assert x * y + 32 * pw <= 1024 and x % 16 == 0
+            if lat == "D2Q9":
+                assert pw == 0                           # producer warps only on the 3-D kernel
         if lat == "D2Q9":
             assert all(r[2] == 1 for r in rows)
     assert lb.lb_kernel_variants(7, None, 0) == lb.LB_ERR_ARG

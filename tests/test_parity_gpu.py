@@ -361,3 +361,20 @@ def test_observables_of_all_systems_in_one_read(lb):
     assert lb.lb_observables_all(ens.ctx, short, 1, first, None) == lb.LB_ERR_ARG
     assert first[len(systems)] == sum(len(b[0]) for b in both)
     ens.close()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(lb):
+    """The warp-specialised kernel's waits are bounded: a wait on a barrier that
+    nothing arrives at gives up (about 0.3 s), reports LB_ERR_TIMEOUT through the
+    status word, and the context keeps working afterwards."""
+    import torch
+    d = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream()
+    assert lb.lb_selftest_wait_timeout(d.data_ptr(), st.cuda_stream) == lb.LB_ERR_TIMEOUT
+    s = synth.ensemble("single_16", "D3Q19")
+    e = lb.Ensemble(s, precision="fp32")
+    e.init()
+    e.step(3)
+    e.sync()
+    assert e.get_step() == 3
+    e.close()
