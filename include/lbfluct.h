@@ -351,6 +351,25 @@ lb_status lb_load(lb_ctx* ctx, const char* path);
  * Row 0 is the default.  Used by the autotuner; no device call. */
 int lb_kernel_variants(int lattice, int32_t* out, int max_rows);
 
+/* Host-armed fault injection for testing the error paths without faulting a
+ * GPU (the paper has no counterpart).  kind:
+ *   LB_FAULT_NONE        disarm;
+ *   LB_FAULT_DENSITY, LB_FAULT_NOISE, LB_FAULT_NONFINITE, LB_FAULT_TIMEOUT
+ *                        after the step that ends at time at_step, the device
+ *                        status word receives the bit a kernel sets on that
+ *                        condition (non-positive density, noise covariance not
+ *                        positive definite, non-finite observable, timed-out
+ *                        wait); lb_sync then reports LB_ERR_NONPOSITIVE_DENSITY,
+ *                        LB_ERR_NOISE_NOT_PD, LB_ERR_NONFINITE or LB_ERR_TIMEOUT,
+ *                        and the error is sticky as a real one;
+ *   LB_FAULT_LAUNCH      lb_step returns LB_ERR_CUDA without launching the step
+ *                        that would end at at_step (steps before it run).
+ * The fault fires once.  While one is armed, lb_step uses plain launches (no
+ * graph replay), so the step is seen on the host.  Errors: LB_ERR_ARG. */
+enum { LB_FAULT_NONE = 0, LB_FAULT_DENSITY = 1, LB_FAULT_NOISE = 2, LB_FAULT_NONFINITE = 3, LB_FAULT_TIMEOUT = 4,
+       LB_FAULT_LAUNCH = 5 };
+lb_status lb_inject_fault(lb_ctx* ctx, int kind, int64_t at_step);
+
 /* Self-test of the bounded device-side waits (the warp-specialised step
  * kernel's hand-offs give up after about 0.3 s instead of hanging): launches one
  * CTA on `cuda_stream` that waits on a shared-memory barrier nothing arrives

@@ -32,6 +32,7 @@ LB_INIT_UNIFORM_NOISE, LB_INIT_FROM_RHO = 0, 1
 LB_MAX_Q = 19
 LB_MAX_LEVELS = 32
 LB_MAX_HIST_BINS = 4096
+LB_FAULT_NONE, LB_FAULT_DENSITY, LB_FAULT_NOISE, LB_FAULT_NONFINITE, LB_FAULT_TIMEOUT, LB_FAULT_LAUNCH = range(6)
 LB_NOALLOC_MAX_SITES = 1 << 18
 Q_OF = {LB_D2Q9: 9, LB_D3Q19: 19}
 
@@ -101,6 +102,7 @@ _SIG = {
     "lb_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "lb_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "lb_kernel_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "lb_inject_fault": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
     "lb_selftest_wait_timeout": (ctypes.c_int, [_P, _P]),
     "lb_kernel_variants": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int]),
     "lb_block_moments_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,

@@ -13,6 +13,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbfluct.h"
 #include "lb_launch.h"
 
@@ -442,6 +444,8 @@ struct lb_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_kernels[2] = {0, 0};
     int64_t launches = 0;       // kernels launched (host-side count)
+    int fault_kind = 0;         // armed fault (lb_inject_fault), fires once
+    int64_t fault_step = -1;
 
     template <class T>
     T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
@@ -603,6 +607,12 @@ cudaError_t launch_steps(lb_ctx* c, int64_t n) {
         c->launches += 1;
         const int64_t t1 = t + 1;
         const bool obs_due = c->opts.obs_every > 0 && t1 % c->opts.obs_every == 0;
+        if (c->fault_kind != 0 && t1 == c->fault_step) {
+            static const int bits[5] = {0, ST_RHO, ST_NOISE, ST_NONFINITE, ST_TIMEOUT};
+            e = launch_set_status(c->at<int>(P.status), bits[c->fault_kind], c->stream);
+            c->fault_kind = 0;
+            if (e != cudaSuccess) return e;
+        }
         const bool sk_due = c->opts.sk_every > 0 && t1 % c->opts.sk_every == 0;
         if (obs_due) {
             e = sample_obs(c, int(t1 & 1), false, true, sk_due);
@@ -815,8 +825,12 @@ lb_status lb_step(lb_ctx* c, int64_t nsteps) {
     if (nsteps == 0) return LB_OK;
     const int C = c->opts.graph_chunk;
     int64_t left = nsteps;
+    struct Range {   // NVTX range over the enqueue of these steps (profiler timelines)
+        Range() { nvtxRangePushA("lb_step"); }
+        ~Range() { nvtxRangePop(); }
+    } range;
     while (left > 0) {
-        const bool aligned = C > 0 && c->step % C == 0 && left >= C &&
+        const bool aligned = C > 0 && c->fault_kind == 0 && c->step % C == 0 && left >= C &&
                              (c->opts.obs_every == 0 || C % c->opts.obs_every == 0) &&
                              (c->opts.sk_every == 0 || C % c->opts.sk_every == 0);
         if (!aligned) {
@@ -826,6 +840,14 @@ lb_status lb_step(lb_ctx* c, int64_t nsteps) {
                 const int64_t to_boundary = (C - c->step % C) % C;
                 n = to_boundary > 0 ? std::min(left, to_boundary) : left;
                 if (n >= C) n = left;   // never reached: aligned handles it
+            }
+            if (c->fault_kind == LB_FAULT_LAUNCH && c->fault_step <= c->step + n) {
+                // the step that would end at fault_step is not launched
+                n = c->fault_step - 1 - c->step;
+                if (n == 0) {
+                    c->fault_kind = 0;
+                    return LB_ERR_CUDA;
+                }
             }
             if (launch_steps(c, n) != cudaSuccess) return LB_ERR_CUDA;
             c->step += n;
@@ -1363,6 +1385,14 @@ lb_status lb_load(lb_ctx* c, const char* path) {
     LB_CHECK(cudaStreamSynchronize(c->stream));
     c->sticky = LB_OK;
     c->has_state = true;
+    return LB_OK;
+}
+
+lb_status lb_inject_fault(lb_ctx* c, int kind, int64_t at_step) {
+    if (!c || kind < LB_FAULT_NONE || kind > LB_FAULT_LAUNCH || (kind != LB_FAULT_NONE && at_step <= c->step))
+        return LB_ERR_ARG;
+    c->fault_kind = kind;
+    c->fault_step = kind == LB_FAULT_NONE ? -1 : at_step;
     return LB_OK;
 }
 

@@ -84,6 +84,8 @@ struct HistDev {
     double lo, inv_w;       // bin of m: floor((m - lo) * inv_w), inv_w = nbins / (hi - lo)
 };
 
+// OR status bits into the device status word (fault injection).
+cudaError_t launch_set_status(int* status, int bits, cudaStream_t st);
 // One CTA whose bounded wait on a barrier nothing arrives at must time out.
 cudaError_t launch_selftest_wait(int* status, cudaStream_t st);
 

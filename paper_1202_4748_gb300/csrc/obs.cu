@@ -242,6 +242,10 @@ __global__ void obs_accum_kernel(const LevelDev* __restrict__ lvv, int n_levels,
 
 __global__ void advance_kernel(int64_t* step, int64_t n) { *step += n; }
 
+// Fault injection: OR bits into the device status word (as a kernel would on
+// detecting the condition).
+__global__ void set_status_kernel(int* status, int bits) { atomicOr(status, bits); }
+
 // Self-test of the bounded waits: one CTA waits on an mbarrier that nothing
 // arrives at; every thread must give up and the status must record it.
 __global__ void selftest_wait_kernel(int* status) {
@@ -311,6 +315,11 @@ cudaError_t launch_advance(int64_t* step, int64_t n, cudaStream_t st) {
 
 cudaError_t launch_selftest_wait(int* status, cudaStream_t st) {
     selftest_wait_kernel<<<1, 64, 0, st>>>(status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_status(int* status, int bits, cudaStream_t st) {
+    set_status_kernel<<<1, 1, 0, st>>>(status, bits);
     return cudaGetLastError();
 }
 

@@ -412,3 +412,55 @@ def test_fp32_fully_relaxed_path_on_odd_and_tiny_shapes(lb):
         e.close()
     for r in runs[1:]:
         assert all(np.array_equal(a, b) for a, b in zip(runs[0], r))
+
+
+@pytest.mark.parametrize("kind,code", [("DENSITY", "NONPOSITIVE_DENSITY"), ("NOISE", "NOISE_NOT_PD"),
+                                       ("NONFINITE", "NONFINITE"), ("TIMEOUT", "TIMEOUT")])
+def test_injected_device_errors_are_reported_sticky_and_cleared(lb, tmp_path, kind, code):
+    """Failure detection without a GPU fault: a host-armed fault sets the status bit
+    a kernel would set; lb_sync reports it, later steps are refused, and a
+    checkpoint load clears it and the run continues as if nothing happened."""
+    systems = synth.ensemble("single_16", "D3Q19")
+    ens = lb.Ensemble(systems, precision="fp32", obs_every=5, graph_chunk=10)
+    ens.init()
+    ens.step(10)
+    path = os.path.join(tmp_path, "ck.bin")
+    ens.save(path)
+    ref = lb.Ensemble(systems, precision="fp32", obs_every=5, graph_chunk=10)
+    ref.init()
+    ref.step(30)
+    want = ref.read_fields(0)
+    ref.close()
+    assert lb.lb_inject_fault(ens.ctx, getattr(lb, "LB_FAULT_" + kind), 17) == lb.LB_OK
+    ens.step(10)                                  # the fault fires after the step ending at 17
+    with pytest.raises(lb.LBError) as e:
+        ens.sync()
+    assert e.value.status == getattr(lb, "LB_ERR_" + code)
+    with pytest.raises(lb.LBError) as e:
+        ens.step(1)
+    assert e.value.status == lb.LB_ERR_STATE
+    ens.load(path)                                # clears the sticky error
+    ens.step(20)
+    ens.sync()
+    assert np.array_equal(ens.read_fields(0), want)
+    ens.close()
+
+
+def test_injected_launch_failure_leaves_a_consistent_context(lb):
+    systems = synth.ensemble("single_16", "D2Q9")
+    ens = lb.Ensemble(systems, precision="fp32", graph_chunk=10)
+    ens.init()
+    assert lb.lb_inject_fault(ens.ctx, lb.LB_FAULT_LAUNCH, 7) == lb.LB_OK
+    assert lb.lb_inject_fault(ens.ctx, lb.LB_FAULT_LAUNCH, 0) == lb.LB_ERR_ARG     # not in the future
+    with pytest.raises(lb.LBError) as e:
+        ens.step(20)
+    assert e.value.status == lb.LB_ERR_CUDA
+    assert ens.get_step() == 6                    # the steps before the failed one ran
+    ens.step(14)                                  # the fault fired once; the run carries on
+    ens.sync()
+    ref = lb.Ensemble(systems, precision="fp32", graph_chunk=10)
+    ref.init()
+    ref.step(20)
+    assert np.array_equal(ens.read_fields(0), ref.read_fields(0))
+    ref.close()
+    ens.close()
