@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 LB_STEPS_PER_STEP = 100
+METRIC = "MLUPS and % of HBM roofline (batched FP32 vs plain FP64) at stated Binder-cumulant error"
 WORKLOADS = {
     "fss_160": dict(ensemble="fss_160", lattice="D3Q19", precision="fp32"),
     "fss_160_d2q9": dict(ensemble="fss_160", lattice="D2Q9", precision="fp32"),
@@ -342,7 +343,7 @@ def main():
     ens.close()
     if rank == 0:
         out = {
-            "metric": "MLUPS of the batched FP32 fused fluctuating LB step (HBM-roofline fraction in roofline)",
+            "metric": METRIC,
             "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -393,7 +394,7 @@ def run_reference(args, wl, rank, world):
     sample = ("FP64 numpy oracle on %d systems of the %s workload (one per size class, %d sites); "
               "one step = one LB step of the sample" % (len(ps), wl["ensemble"], sites))
     out = {
-        "metric": "MLUPS of the batched FP32 fused fluctuating LB step (HBM-roofline fraction in roofline)",
+        "metric": METRIC,
         "value": round(mlups, 4), "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",

@@ -1,7 +1,7 @@
 // Lattice-dependent auxiliary kernels: initial equilibrium, population
 // gather/scatter for host I/O, and the per-site pass of the observables.
-// All reductions are fixed-order (per thread sequential, then a shared-memory
-// tree), so results are bitwise reproducible run to run.
+// All reductions are fixed-order (per thread sequential, then a warp-shuffle
+// tree and a cross-warp stage), so results are bitwise reproducible run to run.
 #pragma once
 
 #include "lb_device.cuh"
@@ -12,21 +12,31 @@ namespace lbf {
 // Work item of a site pass: (system, first site, end site, unused).
 // Deterministic sum of K doubles over the CTA; result valid in thread 0.
 template <int K, int NT>
-__device__ __forceinline__ void block_sum(double (&v)[K], double* sh /* K * NT */) {
-    const int t = threadIdx.x;
+__device__ __forceinline__ void block_sum(double (&v)[K], double* sh /* >= K * NT / 32 */) {
+    static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // within each warp: shuffle-down tree (fixed order, so the sum is reproducible)
 #pragma unroll
-    for (int k = 0; k < K; ++k) sh[k * NT + t] = v[k];
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int s = NT / 2; s > 0; s >>= 1) {
-        if (t < s) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) sh[k * NT + t] += sh[k * NT + t + s];
-        }
-        __syncthreads();
+        for (int k = 0; k < K; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     }
+    if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = sh[k * NT];
+        for (int k = 0; k < K; ++k) sh[k * NW + w] = v[k];
+    }
+    __syncthreads();
+    // across warps: warp 0 reduces the NW partial sums the same way
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = lane < NW ? sh[k * NW + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        }
+    }
 }
 
 __device__ __forceinline__ void site_coords(int site, int nx, int ny, int& x, int& y, int& z) {
