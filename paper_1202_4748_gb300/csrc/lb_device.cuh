@@ -281,29 +281,40 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(b))
                  : "memory");
 }
-// non-blocking test (acquire semantics) of the completion of the phase with this parity
-__device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity) {
+// Wait (acquire semantics) for the completion of the phase with this parity;
+// the thread may be suspended in hardware for up to about suspend_ns before the
+// call returns false, so a waiting warp issues almost nothing.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity, unsigned suspend_ns) {
     unsigned ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
+        : "r"(smem_u32(b)), "r"(parity), "r"(suspend_ns)
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after about 0.3 s, or at once when *abort is set,
-// sets *abort and the status bit, and returns false; control flow then
-// continues (results are flagged invalid), so no thread hangs.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: gives up after about 0.3 s of wall time (global timer; also
+// after 2^20 attempts), or at once when *abort is set, sets *abort and the
+// status bit, and returns false; control flow then continues (results are
+// flagged invalid), so no thread hangs.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* abort, int* status) {
-    for (int i = 0; i < (1 << 22); ++i) {
-        if (mbar_test(b, parity)) return true;
+    if (mbar_try_wait(b, parity, 10000u)) return true;
+    const uint64_t t0 = global_ns();
+    for (int i = 0; i < (1 << 20); ++i) {
+        if (mbar_try_wait(b, parity, 10000u)) return true;
         if (*abort) return false;
-        if (i >= 32) __nanosleep(64);
+        if (global_ns() - t0 > 300000000ull) break;
     }
     *abort = 1;
     atomicOr(status, ST_TIMEOUT);
     return false;
 }
+
 // Named barrier over `count` threads (a multiple of 32) of the CTA.
 __device__ __forceinline__ void named_barrier(int id, int count) {
     asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
