@@ -174,14 +174,16 @@ def statics(systems, steps, every, precision="fp32", kmax=6, warmup=0, graph_chu
     return dict(chi=fit["chi"], xi=fit["xi"], oz=fit, sk=C, jk_ratio=J, samples=ns_tot)
 
 
-def binder_cumulants(systems, steps, precision, obs_every=10, graph_chunk=0, amplitude=0.01):
-    """U_L = 1 - <m^4>/(3 <m^2>^2) per system and level after ``steps`` steps,
-    with the block sizes: (list of lists of (block side, U_L))."""
-    ens = Ensemble(systems, precision=precision, obs_every=obs_every, graph_chunk=graph_chunk)
+def level_observables(systems, steps, precision, obs_every=10, sk_every=0, sk_bins=0, graph_chunk=0,
+                      amplitude=0.01):
+    """Per system: [(block side, U_L, chi_L, c_H,L)] after ``steps`` steps, and the
+    shell-binned C(k) (sums, counts, samples) when sk_every > 0."""
+    ens = Ensemble(systems, precision=precision, obs_every=obs_every, sk_every=sk_every,
+                   graph_chunk=graph_chunk)
     try:
         ens.init(amplitude=amplitude)
         ens.step(steps)
-        out = []
+        out, sk = [], []
         for k, s in enumerate(systems):
             levels, _ = ens.observables(k)
             row = []
@@ -189,32 +191,50 @@ def binder_cumulants(systems, steps, precision, obs_every=10, graph_chunk=0, amp
                 if L["n"] <= 0:
                     continue
                 d = ens.derive(L, s["kT"])
-                row.append((L["block"][0], d["U_L"]))
+                row.append((L["block"][0], d["U_L"], d["chi_L"], d["c_HL"]))
             out.append(row)
+            if sk_every:
+                sk.append(ens.structure_factor(k, sk_bins))
     finally:
         ens.close()
-    return out
+    return out, sk
 
 
-def precision_accuracy(systems, steps, obs_every=10, max_block_fraction=1.0 / 8.0):
-    """Binder cumulants of the same systems and seeds in FP32 and FP64.
+def binder_cumulants(systems, steps, precision, obs_every=10, graph_chunk=0, amplitude=0.01):
+    """U_L per system and level after ``steps`` steps: (list of lists of (block side, U_L))."""
+    rows, _ = level_observables(systems, steps, precision, obs_every, graph_chunk=graph_chunk, amplitude=amplitude)
+    return [[(L, u) for L, u, _, _ in r] for r in rows]
+
+
+def precision_accuracy(systems, steps, obs_every=10, max_block_fraction=1.0 / 8.0, sk_every=0, sk_bins=0):
+    """Observables of the same systems and seeds in FP32 and FP64.
 
     Systems are grouped by (side, a); within a group the replicas (different
     seeds) give the statistical error sigma of the FP64 mean.  For every group
     and every block size L <= max_block_fraction * S (the finite-size-scaling
-    range of the analysis) returns (side, a, L, mean U fp32, mean U fp64, sigma)."""
-    u32 = binder_cumulants(systems, steps, "fp32", obs_every)
-    u64 = binder_cumulants(systems, steps, "fp64", obs_every)
+    range of the analysis) and each of U_L, chi_L, c_H,L returns a row
+    (quantity, side, a, L, mean fp32, mean fp64, sigma); with sk_every > 0 also
+    the structure factor per shell (quantity "C_k", L = shell index)."""
+    o32, k32 = level_observables(systems, steps, "fp32", obs_every, sk_every, sk_bins)
+    o64, k64 = level_observables(systems, steps, "fp64", obs_every, sk_every, sk_bins)
     groups = {}
     for k, s in enumerate(systems):
         groups.setdefault((s["nx"], round(s["a"], 12)), []).append(k)
     rows = []
     for (side, a), ks in sorted(groups.items()):
-        for li, (L, _) in enumerate(u64[ks[0]]):
+        def emit(name, L, v32, v64):
+            v32, v64 = np.asarray(v32), np.asarray(v64)
+            sigma = float(np.std(v64, ddof=1) / math.sqrt(len(ks))) if len(ks) > 1 else float("nan")
+            rows.append((name, side, a, L, float(v32.mean()), float(v64.mean()), sigma))
+        for li, (L, _, _, _) in enumerate(o64[ks[0]]):
             if L > max_block_fraction * side or L == side:
                 continue
-            v32 = np.array([u32[k][li][1] for k in ks])
-            v64 = np.array([u64[k][li][1] for k in ks])
-            sigma = float(np.std(v64, ddof=1) / math.sqrt(len(ks))) if len(ks) > 1 else float("nan")
-            rows.append((side, a, L, float(v32.mean()), float(v64.mean()), sigma))
+            for qi, name in ((1, "U_L"), (2, "chi_L"), (3, "c_HL")):
+                emit(name, L, [o32[k][li][qi] for k in ks], [o64[k][li][qi] for k in ks])
+        if sk_every:
+            for j in range(sk_bins):
+                c32 = [k32[k][0][j] / (k32[k][1][j] * k32[k][2]) for k in ks if k32[k][1][j] > 0]
+                c64 = [k64[k][0][j] / (k64[k][1][j] * k64[k][2]) for k in ks if k64[k][1][j] > 0]
+                if c32 and c64:
+                    emit("C_k", j + 1, c32, c64)
     return rows

@@ -64,13 +64,16 @@ def test_coupling_statics_at_the_papers_2d_parameters(lb, coupling):
     assert res["chi"] == pytest.approx(1.0 / rp, rel=0.03), (res["chi"], 1.0 / rp)
 
 
-def test_fp32_and_fp64_binder_cumulants_agree(lb):
-    """The FP32 throughput counts only where U_L of FP32 runs agrees with FP64 runs
-    of the same systems and seeds within 2 sigma at every L <= S/8."""
+def test_fp32_and_fp64_observables_agree(lb):
+    """The FP32 throughput counts only where FP32 runs agree with FP64 runs of the
+    same systems and seeds within 2 sigma: U_L, chi_L and c_H,L at every
+    L <= S/8, and C(k) on every shell."""
     from paper_1202_4748_gb300 import studies
     systems = [s for s in synth.ensemble("fss_160", "D3Q19") if s["nx"] in (16, 24)]
-    rows = studies.precision_accuracy(systems, steps=2000, obs_every=10)
-    assert len(rows) == 2 * 8 * 2                      # 2 sides x 8 values of a x 2 block sizes
-    for side, a, L, u32, u64, sigma in rows:
-        assert np.isfinite(u32) and np.isfinite(u64) and sigma > 0
-        assert abs(u32 - u64) <= 2.0 * sigma, (side, a, L, u32, u64, sigma)
+    rows = studies.precision_accuracy(systems, steps=2000, obs_every=10, sk_every=50, sk_bins=6)
+    names = [r[0] for r in rows]
+    assert names.count("U_L") == names.count("chi_L") == names.count("c_HL") == 2 * 8 * 2
+    assert names.count("C_k") == 2 * 8 * 6
+    for name, side, a, L, v32, v64, sigma in rows:
+        assert np.isfinite(v32) and np.isfinite(v64) and sigma > 0
+        assert abs(v32 - v64) <= 2.0 * sigma, (name, side, a, L, v32, v64, sigma)
