@@ -343,12 +343,17 @@ lb_status lb_save(lb_ctx* ctx, const char* path);
 lb_status lb_load(lb_ctx* ctx, const char* path);
 
 /* Step-kernel variants compiled for a lattice (LB_D2Q9 or LB_D3Q19): writes up
- * to max_rows rows of 5 int32 (tile x, tile y, tile z or z-chunk, resident CTAs
- * per SM of the register budget (0 = default), producer warps: 0 = every thread
- * stages and collides its own column, > 0 = warp-specialised kernel with that
- * many staging warps, used on the fully relaxed FP32 path) into out
- * (nullable) and returns the number of variants (negative lb_status on error).
- * Row 0 is the default.  Used by the autotuner; no device call. */
+ * to max_rows rows of LB_VARIANT_COLS int32 (tile x, tile y, tile z or z-chunk,
+ * resident CTAs per SM of the register budget (0 = default), producer warps:
+ * 0 = every thread stages and collides its own column, > 0 = warp-specialised
+ * kernel with that many staging warps, used on the fully relaxed FP32 path;
+ * staging: 0 = the producers pull the footprint with plain loads, 1 = with
+ * bulk copies (cp.async.bulk) of the footprint rows into shared memory, when
+ * every system has nx % 4 == 0, nx >= 8 and all sides >= 3, else the staging-0
+ * kernel of the same tile runs) into out (nullable) and returns the number of
+ * variants (negative lb_status on error).  Row 0 is the default.  Used by the
+ * autotuner; no device call. */
+#define LB_VARIANT_COLS 6
 int lb_kernel_variants(int lattice, int32_t* out, int max_rows);
 
 /* Host-armed fault injection for testing the error paths without faulting a

@@ -126,14 +126,16 @@ std::vector<LevelHost> make_levels(const lb_system_desc& d, int& imax, bool& uni
     return out;
 }
 
-int tile_table(int lattice, int (*t)[5]) {
+static_assert(kVariantCols == LB_VARIANT_COLS, "variant rows of the ABI");
+
+int tile_table(int lattice, int (*t)[kVariantCols]) {
     return lattice == LB_D2Q9 ? tile_shapes_d2q9(t, 32) : tile_shapes_d3q19(t, 32);
 }
 
 // The variant given by index, else the first compiled variant matching the
 // requested shape (and occupancy, if given), else the default (index 0).
 lb_status choose_tile(int lattice, const lb_run_opts* o, int& tile_id, int tdim[3]) {
-    int t[32][5];
+    int t[32][kVariantCols];
     const int nt = tile_table(lattice, t);
     tile_id = 0;
     if (o->variant < 0) return LB_ERR_ARG;
@@ -430,7 +432,7 @@ SysDev to_dev(const SysHost& h) {
 }  // namespace
 
 struct lb_ctx {
-    int lattice = 0, coupling = 0, fp32 = 0, q = 9, n_sys = 0, tile_id = 0, bgk_only = 0;
+    int lattice = 0, coupling = 0, fp32 = 0, q = 9, n_sys = 0, tile_id = 0, bgk_only = 0, bulk_ok = 0;
     lb_run_opts opts{};
     std::vector<SysHost> sys;
     Plan P;
@@ -602,6 +604,7 @@ cudaError_t launch_steps(lb_ctx* c, int64_t n) {
         a.status = c->at<int>(P.status);
         a.tile_id = c->tile_id;
         a.bgk_only = c->bgk_only;
+        a.bulk_ok = c->bulk_ok;
         cudaError_t e = launch_step_any(c, a);
         if (e != cudaSuccess) return e;
         c->launches += 1;
@@ -731,6 +734,12 @@ lb_status lb_create(const lb_system_desc* systems, int n_systems, const lb_run_o
         if (!s.bgk) c->bgk_only = 0;
         else if (s.lam_bgk != 1.0 && c->bgk_only == 2) c->bgk_only = 1;
     }
+    // bulk-copy staging: 16-byte aligned rows (nx % 4 == 0, so every system's
+    // populations start 16-byte aligned too), at most 4 seam pieces per staged
+    // row (nx >= 8) and single periodic wraps (every side >= 3)
+    c->bulk_ok = 1;
+    for (auto& s : sd)
+        if (s.nx % 4 != 0 || s.nx < 8 || s.small) c->bulk_ok = 0;
     bool ok = cudaMemcpyAsync(c->ws + P.sys, sd.data(), sizeof(SysDev) * sd.size(), cudaMemcpyHostToDevice,
                               c->stream) == cudaSuccess;
     // physics in the step kernel's precision (staged on the host, copied synchronously)
@@ -1410,10 +1419,10 @@ lb_status lb_selftest_wait_timeout(int* d_status, void* stream) {
 
 int lb_kernel_variants(int lattice, int32_t* out, int max_rows) {
     if (lattice != LB_D2Q9 && lattice != LB_D3Q19) return int(LB_ERR_ARG);
-    int t[32][5];
+    int t[32][kVariantCols];
     const int nt = tile_table(lattice, t);
     for (int r = 0; r < nt && r < max_rows && out; ++r)
-        for (int k = 0; k < 5; ++k) out[5 * r + k] = t[r][k];
+        for (int k = 0; k < kVariantCols; ++k) out[kVariantCols * r + k] = t[r][k];
     return nt;
 }
 

@@ -5,9 +5,9 @@
 namespace lbf {
 
 namespace {
-// (x, y, 1, resident CTAs per SM (0 = default), producer warps (0: none))
-constexpr int kTiles[][5] = {{32, 8, 1, 0, 0}, {64, 4, 1, 0, 0}, {128, 2, 1, 0, 0},
-                             {32, 4, 1, 0, 0}, {32, 16, 1, 0, 0}, {64, 8, 1, 0, 0}};
+// (x, y, 1, resident CTAs per SM (0 = default), producer warps (0: none), staging (0: loads))
+constexpr int kTiles[][kVariantCols] = {{32, 8, 1, 0, 0, 0},  {64, 4, 1, 0, 0, 0},  {128, 2, 1, 0, 0, 0},
+                                        {32, 4, 1, 0, 0, 0},  {32, 16, 1, 0, 0, 0}, {64, 8, 1, 0, 0, 0}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
 
 template <int CP, class Real>
@@ -24,9 +24,9 @@ cudaError_t step_tile(const StepLaunch& a, cudaStream_t st) {
 }
 }  // namespace
 
-int tile_shapes_d2q9(int (*out)[5], int max) {
+int tile_shapes_d2q9(int (*out)[kVariantCols], int max) {
     for (int t = 0; t < kNumTiles && t < max; ++t)
-        for (int k = 0; k < 5; ++k) out[t][k] = kTiles[t][k];
+        for (int k = 0; k < kVariantCols; ++k) out[t][k] = kTiles[t][k];
     return kNumTiles;
 }
 

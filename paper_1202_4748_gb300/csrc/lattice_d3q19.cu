@@ -8,21 +8,29 @@
 namespace lbf {
 
 namespace {
-// (x, y, z-chunk, resident CTAs per SM, producer warps) of the z-marching
-// kernel: producer warps 0 = every thread stages and collides its own column;
-// > 0 = warp-specialised kernel (used on the fully relaxed FP32 path; the other
-// paths run the plain kernel with the same tile).  The first entry is the
-// default (fastest on the 160-system ensemble by the autotuner).
-constexpr int kTiles[][5] = {{16, 8, 32, 3, 4}, {16, 8, 64, 3, 4}, {16, 8, 16, 3, 4}, {16, 8, 16, 6, 0},
-                             {16, 8, 32, 6, 0}, {16, 16, 16, 4, 0}, {16, 16, 32, 4, 0}};
+// (x, y, z-chunk, resident CTAs per SM, producer warps, staging) of the
+// z-marching kernel: producer warps 0 = every thread stages and collides its
+// own column; > 0 = warp-specialised kernel (used on the fully relaxed FP32
+// path; the other paths run the plain kernel with the same tile), whose
+// producers stage the footprint with plain loads (staging 0) or with bulk
+// copies into shared memory (staging 1; systems that do not allow it run the
+// staging-0 kernel of the same tile).  The first entry is the default.
+constexpr int kTiles[][kVariantCols] = {
+    {16, 8, 32, 3, 4, 0}, {16, 8, 64, 3, 4, 0}, {16, 8, 16, 3, 4, 0}, {16, 8, 32, 3, 4, 1},
+    {16, 8, 16, 6, 0, 0}, {16, 8, 32, 6, 0, 0}, {16, 16, 16, 4, 0, 0}, {16, 16, 32, 4, 0, 0}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
 
 template <int CP, class Real, int I>
 cudaError_t step_variant(const StepLaunch& a, cudaStream_t st) {
     constexpr int PW = kTiles[I][4];
     if constexpr (PW > 0 && std::is_same<Real, float>::value) {
-        if (a.bgk_only == 2)
-            return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3]>(a, st);
+        if (a.bgk_only == 2) {
+            if constexpr (kTiles[I][5] == 1) {
+                if (a.bulk_ok)
+                    return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3], 1>(a, st);
+            }
+            return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3], 0>(a, st);
+        }
     }
     return step_z<D3Q19, CP, Real, kTiles[I][0], kTiles[I][1], kTiles[I][2], kTiles[I][3]>(a, st);
 }
@@ -41,9 +49,9 @@ cudaError_t step_tile(const StepLaunch& a, cudaStream_t st) {
 }
 }  // namespace
 
-int tile_shapes_d3q19(int (*out)[5], int max) {
+int tile_shapes_d3q19(int (*out)[kVariantCols], int max) {
     for (int t = 0; t < kNumTiles && t < max; ++t)
-        for (int k = 0; k < 5; ++k) out[t][k] = kTiles[t][k];
+        for (int k = 0; k < kVariantCols; ++k) out[t][k] = kTiles[t][k];
     return kNumTiles;
 }
 

@@ -49,8 +49,9 @@ cudaError_t step_z(const StepLaunch& a, cudaStream_t st) {
 }
 
 // Warp-specialised launch (fully relaxed Guo path, FP32): TX x TY consumer
-// threads and PW producer warps per CTA.
-template <class L, int TX, int TY, int ZC, int PW, int MINB>
+// threads and PW producer warps per CTA; STG = 1 stages the footprint with
+// bulk copies (a dynamic shared-memory stage), 0 with plain loads.
+template <class L, int TX, int TY, int ZC, int PW, int MINB, int STG>
 cudaError_t step_ws(const StepLaunch& a, cudaStream_t st) {
     StepArgs<float> A;
     A.sys = a.sys;
@@ -61,7 +62,21 @@ cudaError_t step_ws(const StepLaunch& a, cudaStream_t st) {
     A.step_ptr = a.step_ptr;
     A.k = a.k;
     A.status = a.status;
-    step_kernel_ws<L, TX, TY, ZC, PW, MINB><<<a.n_tiles, TX * TY + 32 * PW, 0, st>>>(A);
+    size_t dyn = 0;
+    if constexpr (STG == 1) {
+        dyn = BulkStage<L, TX, TY, ZC, PW>::bytes;
+        static bool attr = false;              // once per instantiation
+        if (!attr) {
+            auto k = step_kernel_ws<L, TX, TY, ZC, PW, MINB, STG>;
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         int(cudaSharedmemCarveoutMaxShared));
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+    }
+    step_kernel_ws<L, TX, TY, ZC, PW, MINB, STG><<<a.n_tiles, TX * TY + 32 * PW, dyn, st>>>(A);
     return cudaGetLastError();
 }
 

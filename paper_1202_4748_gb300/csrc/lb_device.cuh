@@ -315,6 +315,41 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile
     return false;
 }
 
+// Bulk copies into shared memory (cp.async.bulk, no tensor map): the mbarrier
+// phase completes when its arrivals are in and the expected bytes have landed.
+// Both addresses and the size must be multiples of 16 bytes.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* b) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(b))
+        : "memory");
+}
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (bulk copy) writes to the same locations.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// Bounded wait for bulk copies: like mbar_wait, but it does not give up when
+// the abort flag is set, so a CTA never exits with its own copies in flight
+// (they read valid addresses and always complete; the limit only guards
+// against a fault elsewhere).
+__device__ __forceinline__ bool mbar_wait_copies(uint64_t* b, unsigned parity, volatile int* abort, int* status) {
+    if (mbar_try_wait(b, parity, 10000u)) return true;
+    const uint64_t t0 = global_ns();
+    for (int i = 0; i < (1 << 20); ++i) {
+        if (mbar_try_wait(b, parity, 10000u)) return true;
+        if (global_ns() - t0 > 300000000ull) break;
+    }
+    *abort = 1;
+    atomicOr(status, ST_TIMEOUT);
+    return false;
+}
+
 // Named barrier over `count` threads (a multiple of 32) of the CTA.
 __device__ __forceinline__ void named_barrier(int id, int count) {
     asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");

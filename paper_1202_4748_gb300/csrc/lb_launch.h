@@ -24,12 +24,14 @@ struct StepLaunch {
     int* status;
     int tile_id;            // index into the lattice's tile-shape table
     int bgk_only;           // 0: per-mode rates; 1: one rate per system; 2: one rate, equal to 1
+    int bulk_ok;            // every system allows bulk-copy staging (nx % 4 == 0, nx >= 8, sides >= 3)
 };
 
 // Step-kernel variants compiled for each lattice: (x, y, z, resident CTAs per
-// SM, producer warps); index = tile_id.
-int tile_shapes_d2q9(int (*out)[5], int max);
-int tile_shapes_d3q19(int (*out)[5], int max);
+// SM, producer warps, staging: 0 plain loads, 1 bulk copies); index = tile_id.
+constexpr int kVariantCols = 6;
+int tile_shapes_d2q9(int (*out)[kVariantCols], int max);
+int tile_shapes_d3q19(int (*out)[kVariantCols], int max);
 
 cudaError_t launch_step_d2q9(int coupling, int fp32, const StepLaunch& a, cudaStream_t st);
 cudaError_t launch_step_d3q19(int coupling, int fp32, const StepLaunch& a, cudaStream_t st);

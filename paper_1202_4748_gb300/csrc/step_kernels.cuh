@@ -785,7 +785,30 @@ __global__ void __launch_bounds__(TX* TY, MINB)
 // parity of the use count identifies the phase.  Every wait is bounded
 // (mbar_wait): a timeout flags the CTA and the status, and all threads keep
 // the same control flow, so the producers' named barrier is always reached.
-template <class L, int TX, int TY, int ZC, int PW, int MINB>
+//
+// Staging (STG):
+//  0  each producer thread pulls the populations of its footprint sites with
+//     plain loads (any system shape);
+//  1  bulk copies (cp.async.bulk): for footprint plane zz and direction i the
+//     producers copy the BH rows of population i on plane zz - c_iz that the
+//     footprint pulls from, each row the BW = TX + 8 floats from x0 - 4
+//     (16-byte aligned; split where it crosses the periodic seam) into a
+//     shared stage; two stages alternate, so the copies of plane zz + 2 run
+//     while plane zz + 1 is summed.  A footprint site then reads its 19 pulled
+//     values from the stage at fixed offsets.  Needs nx % 4 == 0, nx >= 8 and
+//     every side >= 3 (the host checks; the stage is dynamic shared memory).
+template <class L, int TX, int TY, int ZC, int PW>
+struct BulkStage {
+    static constexpr int H = HaloOf<L, GUO>::H;
+    static constexpr int BW = TX + 8;              // staged row: x0 - 4 .. x0 + TX + 3
+    static constexpr int BH = TY + 2 * H;          // rows per direction (the footprint rows)
+    static constexpr int BD = BH * BW;             // floats per direction
+    static constexpr int BSTAGE = L::Q * BD;       // floats per stage
+    static constexpr int NTASK = L::Q * BH;        // row copies per plane (before seam splits)
+    static constexpr size_t bytes = 2 * size_t(BSTAGE) * sizeof(float);
+};
+
+template <class L, int TX, int TY, int ZC, int PW, int MINB, int STG>
 __global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const StepArgs<float> A) {
     using Real = float;
     static_assert(L::D == 3, "z-marching is for 3-D lattices");
@@ -802,6 +825,12 @@ __global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const S
     __shared__ Real sj[R * 3 * NC];
     __shared__ uint64_t full[R], empty[R];
     __shared__ int abort_flag;
+    using BS = BulkStage<L, TX, TY, ZC, PW>;
+    static_assert(STG == 0 || TX % 4 == 0, "staged rows start 16-byte aligned");
+    extern __shared__ __align__(128) float stage_smem[];
+    __shared__ uint64_t tfull[2];                  // bulk-copy stages
+    __shared__ int2 rowtab[STG ? BS::NTASK : 1];   // per row copy: (i N + y nx, c_iz + 1)
+    __shared__ int4 pieces[4];                     // (source x, stage column, length) of the row
 
     const int4 tl = A.tiles[blockIdx.x];
     const SysDev& S = A.sys[tl.x];
@@ -814,6 +843,11 @@ __global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const S
             mbar_init(&full[r], NP);
             mbar_init(&empty[r], NC);
         }
+        if constexpr (STG == 1) {
+            mbar_init(&tfull[0], 1);
+            mbar_init(&tfull[1], 1);
+            fence_proxy_async_smem();              // the inits are seen by the copy engine
+        }
         abort_flag = 0;
     }
     __syncthreads();
@@ -824,10 +858,62 @@ __global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const S
         const Real* __restrict__ fb = A.fin + S.pop_offset;
         const int ptid = tid - NC;
         const bool sm = S.small != 0;
-        for (int zz = z0 - H; zz < z1 + H; ++zz) {
+        // row copies of footprint plane zp into stage st: direction i reads plane
+        // zp - c_iz (rowtab: c_iz + 1 selects the plane offset)
+        auto issue_rows = [&](int zp, int st) {
+            if constexpr (STG == 1) {
+                const int pl = nx * ny;
+                const int zo[3] = {wrap2(zp + 1, nz) * pl, wrap2(zp, nz) * pl, wrap2(zp - 1, nz) * pl};
+                Real* dst0 = stage_smem + st * BS::BSTAGE;
+                for (int t = ptid; t < BS::NTASK; t += NP) {
+                    const int2 rt = rowtab[t];
+                    const Real* src = fb + rt.x + (rt.y == 0 ? zo[0] : (rt.y == 1 ? zo[1] : zo[2]));
+                    Real* dst = dst0 + t * BS::BW;
+                    sfor<0, 4>([&](auto P) {
+                        const int4 pc = pieces[int(P)];
+                        if (pc.z > 0)
+                            bulk_copy_g2s(dst + pc.y, src + pc.x, unsigned(pc.z * sizeof(Real)), &tfull[st]);
+                    });
+                }
+            }
+        };
+        // bulk staging: row-copy table and seam pieces, then the first two planes
+        if constexpr (STG == 1) {
+            if (ptid < BS::BH) {
+                const int r = ptid;
+                sfor<0, Q>([&](auto I) {
+                    constexpr int i = I;
+                    const int gy = wrapm(tl.z - H - L::c(i, 1) + r, ny);
+                    rowtab[i * BS::BH + r] = make_int2(i * N + gy * nx, L::c(i, 2) + 1);
+                });
+            }
+            if (ptid == 0) {
+                const int xs = tl.y - 4;
+                int pos = xs;
+                for (int p = 0; p < 4; ++p) {
+                    const int rem = xs + BS::BW - pos;
+                    if (rem > 0) {
+                        const int w = wrapm(pos, nx);
+                        const int len = min(rem, nx - w);
+                        pieces[p] = make_int4(w, pos - xs, len, 0);
+                        pos += len;
+                    } else {
+                        pieces[p] = make_int4(0, 0, 0, 0);
+                    }
+                }
+                mbar_arrive_expect_tx(&tfull[0], unsigned(BS::BSTAGE * sizeof(Real)));
+                mbar_arrive_expect_tx(&tfull[1], unsigned(BS::BSTAGE * sizeof(Real)));
+            }
+            named_barrier(1, NP);
+            issue_rows(z0 - H, 0);
+            issue_rows(z0 - H + 1, 1);
+        }
+        int it = 0;
+        for (int zz = z0 - H; zz < z1 + H; ++zz, ++it) {
             const int zw = zz - R;                       // plane whose slots this iteration reuses
             if (zw >= z0) mbar_wait(&empty[(zw - z0) % R], unsigned(((zw - z0) / R) & 1), &abort_flag, A.status);
             const int slot = dslot(zz);
+            if constexpr (STG == 0) {
             const int wz = sm ? wrapm(zz, nz) : wrap2(zz, nz);
             // every footprint site of this producer thread is requested before any
             // is summed (FS sites per thread, FS x Q loads in flight)
@@ -865,7 +951,49 @@ __global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const S
                     srho[slot * SP + idx] = v;
                 }
             });
+            } else {
+            // the copies of this plane were issued two planes ago (or in the prologue)
+            const int st = it & 1;
+            mbar_wait_copies(&tfull[st], unsigned((it >> 1) & 1), &abort_flag, A.status);
+            const Real* stg = stage_smem + st * BS::BSTAGE;
+            constexpr int FS = (SP + NP - 1) / NP;
+            sfor<0, FS>([&](auto SI) {
+                constexpr int si = SI;
+                const int idx = ptid + si * NP;
+                if (idx < SP) {
+                    const int px = idx % SX, py = idx / SX;
+                    Real v = Real(0);
+                    if (tl.y + px - H < nx + H && tl.z + py - H < ny + H) {
+                        // pulled value of direction i: row py, column px + 2 - c_ix of its block
+                        const Real* sb = stg + py * BS::BW + px + 2;
+                        Real g[Q];
+                        sfor<0, Q>([&](auto I) {
+                            constexpr int i = I;
+                            g[i] = sb[i * BS::BD - L::c(i, 0)];
+                        });
+                        sfor<0, Q>([&](auto I) { v += g[decltype(I)::value]; });
+                        const int ix = px - H, iy = py - H;
+                        if (ix >= 0 && ix < TX && iy >= 0 && iy < TY) {
+                            Real jm[3];
+                            momentum_of<L, Real>(g, jm);
+                            sfor<0, 3>([&](auto C) {
+                                sj[(slot * 3 + int(C)) * NC + iy * TX + ix] = jm[decltype(C)::value];
+                            });
+                        }
+                    }
+                    srho[slot * SP + idx] = v;
+                }
+            });
+            if (zz + 2 < z1 + H && ptid == 0) mbar_arrive_expect_tx(&tfull[st], unsigned(BS::BSTAGE * sizeof(Real)));
+            }
             named_barrier(1, NP);                        // density plane zz complete (producers)
+            if constexpr (STG == 1) {
+                // every producer has read stage it & 1: refill it with plane zz + 2
+                if (zz + 2 < z1 + H) {
+                    fence_proxy_async_smem();
+                    issue_rows(zz + 2, it & 1);
+                }
+            }
             const int zl = zz - 1;                       // Laplacian plane (needs density zl-1 .. zl+1)
             if (zl >= z0 - 1) {
                 const int r0 = dslot(zl) * SP, rm = dslot(zl - 1) * SP, rp = dslot(zl + 1) * SP;

@@ -135,9 +135,10 @@ def test_kernel_variant_table():
     for lat in ("D2Q9", "D3Q19"):
         rows = lb.kernel_variants(lat)
         assert len(rows) >= 3 and len(set(rows)) == len(rows)
-        for x, y, z, occ, pw in rows:
-            assert x > 0 and y > 0 and z > 0 and occ >= 0 and pw >= 0
+        for x, y, z, occ, pw, stg in rows:
+            assert x > 0 and y > 0 and z > 0 and occ >= 0 and pw >= 0 and stg in (0, 1)
             assert x * y + 32 * pw <= 1024 and x % 16 == 0
+            assert stg == 0 or pw > 0                    # bulk staging is done by producer warps
             if lat == "D2Q9":
                 assert pw == 0                           # producer warps only on the 3-D kernel
         if lat == "D2Q9":
