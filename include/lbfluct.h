@@ -347,12 +347,16 @@ lb_status lb_load(lb_ctx* ctx, const char* path);
  * resident CTAs per SM of the register budget (0 = default), producer warps:
  * 0 = every thread stages and collides its own column, > 0 = warp-specialised
  * kernel with that many staging warps, used on the fully relaxed FP32 path;
- * staging: 0 = the producers pull the footprint with plain loads, 1 = with
- * bulk copies (cp.async.bulk) of the footprint rows into shared memory, when
- * every system has nx % 4 == 0, nx >= 8 and all sides >= 3, else the staging-0
- * kernel of the same tile runs) into out (nullable) and returns the number of
- * variants (negative lb_status on error).  Row 0 is the default.  Used by the
- * autotuner; no device call. */
+ * scheme: 0 = tiles or columns whose threads pull the footprint with plain
+ * loads, 1 = (D3Q19) producers stage the footprint rows with bulk copies
+ * (cp.async.bulk) into shared memory, when every system has nx % 4 == 0,
+ * nx >= 8 and all sides >= 3, else the scheme-0 kernel of the same tile runs,
+ * 2 = (D2Q9, modified equilibrium only) row-marching strips: one warp per tile
+ * of 32 sites x y rows, densities in registers and warp shuffles) into out
+ * (nullable) and returns the number of variants (negative lb_status on error).
+ * Row 0 is the default; where the coupling cannot run it (scheme 2 with the
+ * Guo form) the first row it can run is.  Selecting a row the coupling cannot
+ * run gives LB_ERR_UNSUPPORTED.  Used by the autotuner; no device call. */
 #define LB_VARIANT_COLS 6
 int lb_kernel_variants(int lattice, int32_t* out, int max_rows);
 

@@ -133,22 +133,25 @@ int tile_table(int lattice, int (*t)[kVariantCols]) {
 }
 
 // The variant given by index, else the first compiled variant matching the
-// requested shape (and occupancy, if given), else the default (index 0).
-lb_status choose_tile(int lattice, const lb_run_opts* o, int& tile_id, int tdim[3]) {
+// requested shape (and occupancy, if given), else the default: the first
+// variant the coupling runs (row-marching strips, scheme 2, are compiled for
+// the modified equilibrium only).
+lb_status choose_tile(int lattice, int coupling, const lb_run_opts* o, int& tile_id, int tdim[3]) {
     int t[32][kVariantCols];
     const int nt = tile_table(lattice, t);
+    auto runs = [&](int k) { return t[k][5] != 2 || coupling == LB_MODEQ; };
     tile_id = 0;
     if (o->variant < 0) return LB_ERR_ARG;
     if (o->variant > 0) {
-        if (o->variant > nt) return LB_ERR_UNSUPPORTED;
+        if (o->variant > nt || !runs(o->variant - 1)) return LB_ERR_UNSUPPORTED;
         tile_id = o->variant - 1;
-    } else if (o->tile[0] > 0 || o->occupancy > 0) {
+    } else {
         tile_id = -1;
         for (int k = 0; k < nt && tile_id < 0; ++k) {
             const bool shape = o->tile[0] <= 0 || (t[k][0] == o->tile[0] && t[k][1] == o->tile[1] &&
                                                    t[k][2] == (o->tile[2] > 0 ? o->tile[2] : 1));
             const bool occ = o->occupancy <= 0 || t[k][3] == o->occupancy;
-            if (shape && occ) tile_id = k;
+            if (shape && occ && runs(k)) tile_id = k;
         }
         if (tile_id < 0) return LB_ERR_UNSUPPORTED;
     }
@@ -161,7 +164,7 @@ lb_status make_plan(const lb_system_desc* s, int n, const lb_run_opts* o, std::v
     lb_status st = validate(s, n, o);
     if (st != LB_OK) return st;
     int tdim[3];
-    st = choose_tile(s[0].lattice, o, tile_id, tdim);
+    st = choose_tile(s[0].lattice, s[0].coupling, o, tile_id, tdim);
     if (st != LB_OK) return st;
     const int q = q_of(s[0].lattice);
     const size_t es = o->precision == LB_FP64 ? 8 : 4;

@@ -5,20 +5,36 @@
 namespace lbf {
 
 namespace {
-// (x, y, 1, resident CTAs per SM (0 = default), producer warps (0: none), staging (0: loads))
-constexpr int kTiles[][kVariantCols] = {{32, 8, 1, 0, 0, 0},  {64, 4, 1, 0, 0, 0},  {128, 2, 1, 0, 0, 0},
+// (x, y, 1, resident CTAs per SM (0 = default), producer warps (0: none), scheme):
+// scheme 2 = row-marching warp strips of 32 sites x y rows (modified
+// equilibrium only), scheme 0 = CTA tiles of x by y sites with a density halo.
+// Row 0 is the default of the modified equilibrium; the Guo form takes the
+// first tile row.
+constexpr int kTiles[][kVariantCols] = {{32, 32, 1, 6, 0, 2}, {32, 64, 1, 6, 0, 2}, {32, 16, 1, 6, 0, 2},
+                                        {32, 32, 1, 7, 0, 2},
+                                        {32, 8, 1, 0, 0, 0},  {64, 4, 1, 0, 0, 0},  {128, 2, 1, 0, 0, 0},
                                         {32, 4, 1, 0, 0, 0},  {32, 16, 1, 0, 0, 0}, {64, 8, 1, 0, 0, 0}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
+
+template <int CP, class Real, int YC, int MINB>
+cudaError_t strip_of(const StepLaunch& a, cudaStream_t st) {
+    if constexpr (CP == MODEQ) return step_strip<D2Q9, CP, Real, YC, 4, MINB>(a, st);
+    return cudaErrorInvalidValue;            // the plan admits strips only with Eq. 65
+}
 
 template <int CP, class Real>
 cudaError_t step_tile(const StepLaunch& a, cudaStream_t st) {
     switch (a.tile_id) {
-        case 0: return step_one<D2Q9, CP, Real, 32, 8, 1>(a, st);
-        case 1: return step_one<D2Q9, CP, Real, 64, 4, 1>(a, st);
-        case 2: return step_one<D2Q9, CP, Real, 128, 2, 1>(a, st);
-        case 3: return step_one<D2Q9, CP, Real, 32, 4, 1>(a, st);
-        case 4: return step_one<D2Q9, CP, Real, 32, 16, 1>(a, st);
-        case 5: return step_one<D2Q9, CP, Real, 64, 8, 1>(a, st);
+        case 0: return strip_of<CP, Real, 32, 6>(a, st);
+        case 1: return strip_of<CP, Real, 64, 6>(a, st);
+        case 2: return strip_of<CP, Real, 16, 6>(a, st);
+        case 3: return strip_of<CP, Real, 32, 7>(a, st);
+        case 4: return step_one<D2Q9, CP, Real, 32, 8, 1>(a, st);
+        case 5: return step_one<D2Q9, CP, Real, 64, 4, 1>(a, st);
+        case 6: return step_one<D2Q9, CP, Real, 128, 2, 1>(a, st);
+        case 7: return step_one<D2Q9, CP, Real, 32, 4, 1>(a, st);
+        case 8: return step_one<D2Q9, CP, Real, 32, 16, 1>(a, st);
+        case 9: return step_one<D2Q9, CP, Real, 64, 8, 1>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -23,6 +23,31 @@ cudaError_t step_one_mode(const StepLaunch& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Row-marching strips (D2Q9, modified equilibrium): WPC warps per CTA, one
+// tile (32 sites x YC rows) per warp.
+template <class L, int CP, class Real, int YC, int WPC, int MINB, int MODE>
+cudaError_t step_strip_mode(const StepLaunch& a, cudaStream_t st) {
+    StepArgs<Real> A;
+    A.sys = a.sys;
+    A.phys = static_cast<const SysPhys<Real>*>(a.phys);
+    A.tiles = a.tiles;
+    A.fin = static_cast<const Real*>(a.fin);
+    A.fout = static_cast<Real*>(a.fout);
+    A.step_ptr = a.step_ptr;
+    A.k = a.k;
+    A.status = a.status;
+    const int grid = (a.n_tiles + WPC - 1) / WPC;
+    step_kernel_strip<L, CP, Real, YC, WPC, MINB, MODE><<<grid, 32 * WPC, 0, st>>>(A, a.n_tiles);
+    return cudaGetLastError();
+}
+template <class L, int CP, class Real, int YC, int WPC, int MINB>
+cudaError_t step_strip(const StepLaunch& a, cudaStream_t st) {
+    constexpr int MB = sizeof(Real) == 4 && MINB > 0 ? MINB : 1;   // FP64 keeps its registers
+    if (a.bgk_only == 2) return step_strip_mode<L, CP, Real, YC, WPC, MB, 2>(a, st);
+    if (a.bgk_only == 1) return step_strip_mode<L, CP, Real, YC, WPC, MB, 1>(a, st);
+    return step_strip_mode<L, CP, Real, YC, WPC, MB, 0>(a, st);
+}
+
 template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB, int MODE>
 cudaError_t step_z_mode(const StepLaunch& a, cudaStream_t st) {
     StepArgs<Real> A;

@@ -285,7 +285,9 @@ __device__ __forceinline__ void collide_guo_bgk(Real (&f)[L::Q], const Real drho
 
 // Collision of one site given its pulled deviations f[], the density halo and
 // (Guo) the Laplacian halo.  Returns post-collision deviations in f[].
-template <class L, int CP, class Real, bool BGK_ONLY, class RhoV, class LapV>
+// TAU1 (with BGK_ONLY): the single rate is 1, so f is replaced by the
+// equilibrium (plus force) and the noise amplitudes are the lattice constants.
+template <class L, int CP, class Real, bool BGK_ONLY, class RhoV, class LapV, bool TAU1 = false>
 __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, const RhoV& rv, const LapV& lv,
                                              const SysDev& S, const SysPhys<Real>& P, const uint32_t site,
                                              const int64_t step, int* status) {
@@ -331,7 +333,7 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
             if constexpr (L::c(i, 1) != 0) g[1] += Real(3.0 * L::w(i) * L::c(i, 1)) * rn;
             lap += Real(6.0 * L::w(i)) * (rn - drho);
         });
-        const Real ir = Real(1) / rho;
+        const Real ir = fast_rcp(rho);
         const Real ux = j[0] * ir, uy = j[1] * ir;
         const Real nu = P.nu;
         const Real iso = p0 - kap * rho * lap;                     // p0 - kappa rho lap rho
@@ -355,11 +357,13 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
                      Real(pooley_wyy(i)) * gyy;
             if constexpr (pooley_wxy(i) != 0.0) v += Real(pooley_wxy(i)) * gxy;
             s += v;
-            if constexpr (BGK_ONLY) f[i] -= lam_b * (f[i] - v);
+            if constexpr (BGK_ONLY && TAU1) f[i] = v;
+            else if constexpr (BGK_ONLY) f[i] -= lam_b * (f[i] - v);
             else feq[i] = v;
         });
         // deviation form of f_0 = rho - sum_{i>=1} f_i
-        if constexpr (BGK_ONLY) f[0] -= lam_b * (f[0] - (drho - s));
+        if constexpr (BGK_ONLY && TAU1) f[0] = drho - s;
+        else if constexpr (BGK_ONLY) f[0] -= lam_b * (f[0] - (drho - s));
         else feq[0] = drho - s;
     } else {
         // Guo body force F = kappa rho grad(lap rho)
@@ -420,7 +424,7 @@ __device__ __forceinline__ void collide_site(Real (&f)[L::Q], const Real drho, c
 
     Real xi[K];
     sfor<0, K>([&](auto A) { xi[decltype(A)::value] = Real(0); });
-    if (P.kT > Real(0)) noise_modes<L, Real>(S, P, site, step, rho, cs2, xi, status);
+    if (P.kT > Real(0)) noise_modes<L, Real, BGK_ONLY && TAU1>(S, P, site, step, rho, cs2, xi, status);
 
     if constexpr (BGK_ONLY) {
         // f already relaxed and forced; add the noise through f_i += sum_a t_i T_ai xi_a / N_a
@@ -598,13 +602,121 @@ __global__ void __launch_bounds__(TX* TY* TZ)
     if constexpr (CP == GUO && BGK_ONLY)
         collide_guo_bgk<L, Real, TAU1>(f, drho, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
     else
-        collide_site<L, CP, Real, BGK_ONLY>(f, drho, rv, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
+        collide_site<L, CP, Real, BGK_ONLY, TileView<Real, SX, SY>, TileView<Real, LX, LY>, TAU1>(
+            f, drho, rv, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
 
     Real* __restrict__ fo = A.fout + S.pop_offset;
     sfor<0, Q>([&](auto I) {
         constexpr int i = I;
         fo[i * N + site] = f[i];
     });
+}
+
+// Density deviation on the 3 x 3 neighbourhood of a site, held in registers:
+// at<cx, cy, 0>() is the value at r + c.
+template <class Real>
+struct Nbr9 {
+    Real v[3][3];   // [1 + c_y][1 + c_x]
+    template <int CX, int CY, int CZ>
+    __device__ __forceinline__ Real at() const { return v[1 + CY][1 + CX]; }
+};
+template <class Real>
+struct NoView {
+    template <int CX, int CY, int CZ>
+    __device__ __forceinline__ Real at() const { return Real(0); }
+};
+
+// Row-marching strips for the D2Q9 modified-equilibrium step (Eq. 65 needs
+// the density on the 3 x 3 neighbourhood only).  Each warp owns 32
+// consecutive sites of a row (tile (system, x0, y0)) and walks YC rows.  Per
+// footprint row yy a lane pulls its site's 9 populations, forms rho, and the
+// neighbours' rho comes by warp shuffles; lanes 0 and 31 also pull the halo
+// sites x0 - 1 and x0 + 32.  Three density rows live in registers as
+// (x - 1, x, x + 1) triples, and the site of row yy - 1 collides from its
+// populations pulled one iteration earlier.  No shared memory and no CTA
+// barrier: every footprint value is formed once per chunk (halo 2/32 in x,
+// 2/YC in y).  Lanes past the system's last column form the periodic image
+// of their column for their neighbours and do not collide.  (Colliding two
+// rows behind, to overlap the next row's loads, measured slower: 8 more
+// registers per thread, fewer warps in flight.)
+template <class L, int CP, class Real, int YC, int WPC, int MINB, int MODE>
+__global__ void __launch_bounds__(32 * WPC, MINB) step_kernel_strip(const StepArgs<Real> A, int n_tiles) {
+    static_assert(L::D == 2 && CP == MODEQ, "row strips: D2Q9 with the modified equilibrium");
+    constexpr bool BGK_ONLY = MODE >= 1;
+    constexpr int Q = L::Q;
+    const int lane = threadIdx.x & 31;
+    const int wt = blockIdx.x * WPC + int(threadIdx.x >> 5);
+    if (wt >= n_tiles) return;                       // the whole warp leaves together
+    const int4 tl = A.tiles[wt];
+    // register copies of the per-system records: read once, not again after every row's stores
+    const SysDev S = A.sys[tl.x];
+    const SysPhys<Real> P = A.phys[tl.x];
+    const int nx = S.nx, ny = S.ny, N = S.ns;
+    const bool sm = S.small != 0;
+    const Real* __restrict__ fb = A.fin + S.pop_offset;
+    Real* __restrict__ fo = A.fout + S.pop_offset;
+    const int x = tl.y + lane;
+    const bool own = x < nx;
+    const bool extra = lane == 0 || lane == 31;
+    // pulled columns x - c_x for c_x = -1, 0, 1 (index 1 + c_x), of the lane's site and of its halo site
+    const int xs = wrapm(x, nx);
+    const int xh = wrapm(lane == 0 ? tl.y - 1 : tl.y + 32, nx);
+    const int xo[3] = {wrap1(xs + 1, nx), xs, wrap1(xs - 1, nx)};
+    const int ho[3] = {wrap1(xh + 1, nx), xh, wrap1(xh - 1, nx)};
+    const int64_t step = *A.step_ptr + A.k;
+    const int y0 = tl.z, y1 = min(y0 + YC, ny);
+
+    Real fp[Q];                                      // pulled populations of row yy - 1
+    Real Rm[3] = {Real(0), Real(0), Real(0)}, R0[3] = {Real(0), Real(0), Real(0)},
+         Rp[3] = {Real(0), Real(0), Real(0)};        // rho rows yy - 2, yy - 1, yy
+    sfor<0, Q>([&](auto I) { fp[decltype(I)::value] = Real(0); });
+    for (int yy = y0 - 1; yy <= y1; ++yy) {
+        // pulled rows yy - c_y for c_y = -1, 0, 1 (index 1 + c_y)
+        const int ro[3] = {(sm ? wrapm(yy + 1, ny) : wrap2(yy + 1, ny)) * nx,
+                           (sm ? wrapm(yy, ny) : wrap2(yy, ny)) * nx,
+                           (sm ? wrapm(yy - 1, ny) : wrap2(yy - 1, ny)) * nx};
+        Real fc[Q];
+        sfor<0, Q>([&](auto I) {
+            constexpr int i = I;
+            fc[i] = fb[i * N + ro[1 + L::c(i, 1)] + xo[1 + L::c(i, 0)]];
+        });
+        Real re = Real(0);
+        if (extra) {
+            Real g[Q];
+            sfor<0, Q>([&](auto I) {
+                constexpr int i = I;
+                g[i] = fb[i * N + ro[1 + L::c(i, 1)] + ho[1 + L::c(i, 0)]];
+            });
+            sfor<0, Q>([&](auto I) { re += g[decltype(I)::value]; });
+        }
+        Real rc = Real(0);
+        sfor<0, Q>([&](auto I) { rc += fc[decltype(I)::value]; });
+        Real rl = __shfl_up_sync(0xffffffffu, rc, 1);
+        Real rr = __shfl_down_sync(0xffffffffu, rc, 1);
+        if (lane == 0) rl = re;
+        if (lane == 31) rr = re;
+        sfor<0, 3>([&](auto K) {
+            constexpr int k = K;
+            Rm[k] = R0[k];
+            R0[k] = Rp[k];
+        });
+        Rp[0] = rl;
+        Rp[1] = rc;
+        Rp[2] = rr;
+        if (yy > y0 && own) {
+            const int y = yy - 1;
+            const Nbr9<Real> nb{{{Rm[0], Rm[1], Rm[2]}, {R0[0], R0[1], R0[2]}, {Rp[0], Rp[1], Rp[2]}}};
+            const NoView<Real> nl;
+            const int site = y * nx + x;
+            collide_site<L, CP, Real, BGK_ONLY, Nbr9<Real>, NoView<Real>, MODE == 2>(fp, R0[1], nb, nl, S, P,
+                                                                                  uint32_t(site), step, A.status);
+            sfor<0, Q>([&](auto I) {
+                constexpr int i = I;
+                fo[i * N + site] = fp[i];
+            });
+        }
+        sfor<0, Q>([&](auto I) { fp[decltype(I)::value] = fc[decltype(I)::value]; });
+    }
 }
 
 }  // namespace lbf

@@ -130,15 +130,35 @@ def test_derive_matches_oracle_formulas():
     assert lb.lb_derive(ctypes.byref(L), kT, out) == lb.LB_ERR_ARG
 
 
+def test_strip_variants_are_refused_for_the_guo_form():
+    """Row-marching strips are compiled for the modified equilibrium only: a Guo
+    ensemble that asks for one is refused at plan time, and its default is the
+    first tile row."""
+    import paper_1202_4748_gb300 as lb
+    s = synth.system("D2Q9", "guo", n=16)
+    rows = lb.kernel_variants("D2Q9")
+    strip = [i for i, r in enumerate(rows) if r[5] == 2]
+    assert strip and strip[0] == 0                      # the modified equilibrium's default
+    with pytest.raises(lb.LBError) as e:
+        lb.workspace_bytes([s], precision="fp32", variant=strip[0] + 1)
+    assert e.value.status == lb.LB_ERR_UNSUPPORTED
+    assert lb.workspace_bytes([s], precision="fp32") > 0
+    assert lb.workspace_bytes([synth.system("D2Q9", "modeq", n=16)], precision="fp32", variant=1) > 0
+
+
 def test_kernel_variant_table():
     import paper_1202_4748_gb300 as lb
     for lat in ("D2Q9", "D3Q19"):
         rows = lb.kernel_variants(lat)
         assert len(rows) >= 3 and len(set(rows)) == len(rows)
         for x, y, z, occ, pw, stg in rows:
-            assert x > 0 and y > 0 and z > 0 and occ >= 0 and pw >= 0 and stg in (0, 1)
-            assert x * y + 32 * pw <= 1024 and x % 16 == 0
-            assert stg == 0 or pw > 0                    # bulk staging is done by producer warps
+            assert x > 0 and y > 0 and z > 0 and occ >= 0 and pw >= 0 and stg in (0, 1, 2)
+            assert x % 16 == 0
+            assert stg != 1 or pw > 0                    # bulk staging is done by producer warps
+            if stg == 2:                                 # row strips: one warp per 32-site tile
+                assert lat == "D2Q9" and x == 32 and pw == 0
+            else:
+                assert x * y + 32 * pw <= 1024
             if lat == "D2Q9":
                 assert pw == 0                           # producer warps only on the 3-D kernel
         if lat == "D2Q9":
