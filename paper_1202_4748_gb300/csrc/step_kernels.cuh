@@ -945,7 +945,7 @@ __global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const S
     __shared__ int4 pieces[4];                     // (source x, stage column, length) of the row
 
     const int4 tl = A.tiles[blockIdx.x];
-    const SysDev& S = A.sys[tl.x];
+    const SysDev S = A.sys[tl.x];          // register copy: not re-read after the stores
     const int nx = S.nx, ny = S.ny, nz = S.nz;
     const int N = S.ns;
     const int z0 = tl.w, z1 = min(z0 + ZC, nz);
@@ -1027,27 +1027,30 @@ __global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const S
             const int slot = dslot(zz);
             if constexpr (STG == 0) {
             const int wz = sm ? wrapm(zz, nz) : wrap2(zz, nz);
-            // every footprint site of this producer thread is requested before any
-            // is summed (FS sites per thread, FS x Q loads in flight)
+            // the footprint sites of this producer thread go in batches of FB: all
+            // FB x Q loads of a batch are requested before any is summed
             constexpr int FS = (SP + NP - 1) / NP;
-            Real g[FS][Q];
-            bool inb[FS];
-            sfor<0, FS>([&](auto SI) {
+            constexpr int FB = FS < 2 ? FS : 2;
+#pragma unroll 1
+            for (int b0 = 0; b0 < FS; b0 += FB) {
+            Real g[FB][Q];
+            bool inb[FB];
+            sfor<0, FB>([&](auto SI) {
                 constexpr int si = SI;
-                const int idx = ptid + si * NP;
+                const int idx = ptid + (b0 + si) * NP;
                 const int px = idx % SX, py = idx / SX;
                 const int gx = tl.y + px - H, gy = tl.z + py - H;
-                inb[si] = idx < SP && gx < nx + H && gy < ny + H;
+                inb[si] = b0 + si < FS && idx < SP && gx < nx + H && gy < ny + H;
                 if (inb[si]) {
                     const Nbr nb(sm ? wrapm(gx, nx) : wrap2(gx, nx), sm ? wrapm(gy, ny) : wrap2(gy, ny), wz, nx, ny,
                                  nz, true);
                     pull_site<L, Real>(fb, N, nb, g[si]);
                 }
             });
-            sfor<0, FS>([&](auto SI) {
+            sfor<0, FB>([&](auto SI) {
                 constexpr int si = SI;
-                const int idx = ptid + si * NP;
-                if (idx < SP) {
+                const int idx = ptid + (b0 + si) * NP;
+                if (b0 + si < FS && idx < SP) {
                     Real v = Real(0);
                     if (inb[si]) {
                         sfor<0, Q>([&](auto I) { v += g[si][decltype(I)::value]; });
@@ -1063,6 +1066,7 @@ __global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const S
                     srho[slot * SP + idx] = v;
                 }
             });
+            }
             } else {
             // the copies of this plane were issued two planes ago (or in the prologue)
             const int st = it & 1;
@@ -1131,6 +1135,7 @@ __global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const S
         // ---------------- consumers ----------------
         Real* __restrict__ fo = A.fout + S.pop_offset;
         const int64_t step = *A.step_ptr + A.k;
+        const SysPhys<Real> P = A.phys[tl.x];
         const int tx = tid % TX, ty = tid / TX;
         const int x = tl.y + tx, y = tl.z + ty;
         const bool valid_xy = x < nx && y < ny;
@@ -1147,7 +1152,7 @@ __global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const S
                                             (ty + 1) * LX + (tx + 1)};
                 const int site = site_index(x, y, zc, nx, ny);
                 Real f[Q];
-                collide_guo_bgk_m<L, Real, true>(f, drho, jc, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
+                collide_guo_bgk_m<L, Real, true>(f, drho, jc, lv, S, P, uint32_t(site), step, A.status);
                 sfor<0, Q>([&](auto I) {
                     constexpr int i = I;
                     fo[i * N + site] = f[i];
