@@ -32,6 +32,7 @@ LB_INIT_UNIFORM_NOISE, LB_INIT_FROM_RHO = 0, 1
 LB_MAX_Q = 19
 LB_MAX_LEVELS = 32
 LB_MAX_HIST_BINS = 4096
+LB_HIST_EST = 11
 LB_VARIANT_COLS = VARIANT_COLS = 6
 LB_FAULT_NONE, LB_FAULT_DENSITY, LB_FAULT_NOISE, LB_FAULT_NONFINITE, LB_FAULT_TIMEOUT, LB_FAULT_LAUNCH = range(6)
 LB_NOALLOC_MAX_SITES = 1 << 18

@@ -29,6 +29,18 @@ def test_every_declared_symbol_is_exported():
     assert sorted(lb.EXPORTED) == names
 
 
+def test_header_constants_match_the_binding():
+    """Every numeric #define of the header has the same value in the binding."""
+    import paper_1202_4748_gb300 as lb
+    src = open(os.path.join(ROOT, "include", "lbfluct.h")).read()
+    defs = re.findall(r"^#define (LB_[A-Z0-9_]+) (.+)$", src, flags=re.M)
+    assert len(defs) >= 5
+    for name, expr in defs:
+        value = eval(expr.strip(), {})
+        assert getattr(lb, name) == value, name
+    assert len(lb.HIST_EST_FIELDS) == lb.LB_HIST_EST
+
+
 def test_observables_all_rejects_missing_arguments():
     import paper_1202_4748_gb300 as lb
     assert lb.lb_observables_all(None, None, 0, None, None) == lb.LB_ERR_ARG
