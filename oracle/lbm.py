@@ -274,8 +274,12 @@ def noise_matrix(cs2, p):
     return M * g
 
 
-def noise(rho, cs2, t, p):
-    """Moment-space noise xi on the non-conserved modes, shape (K, nz, ny, nx)."""
+def noise(rho, cs2, t, p, sites=None):
+    """Moment-space noise xi on the non-conserved modes, shape (K, nz, ny, nx).
+
+    ``sites``: the global site index (x + nx (y + ny z) in the whole system) of
+    every site of ``rho`` in its (z, y, x) order, when ``rho`` is a cut-out;
+    default: the sites of the whole system ``p`` in order."""
     lat = p.lat
     K = lat.q - lat.n_conserved
     M = noise_matrix(cs2, p)
@@ -286,7 +290,9 @@ def noise(rho, cs2, t, p):
         L = np.linalg.cholesky(flatM)
     except np.linalg.LinAlgError as exc:
         raise NoiseNotPositiveDefinite(str(exc)) from exc
-    sites = np.arange(p.n_sites, dtype=np.uint64)
+    if sites is None:
+        sites = np.arange(p.n_sites, dtype=np.uint64)
+    sites = np.asarray(sites, dtype=np.uint64).reshape(-1)
     n = philox.site_normals(sites, t, p.system_id, p.seed, K)        # (K, nsites)
     s = np.sqrt(3.0 * rho.reshape(-1) * p.kT)
     xi = s[None, :] * np.einsum("sab,bs->as", L, n)
@@ -297,8 +303,13 @@ def noise(rho, cs2, t, p):
 # the step
 # --------------------------------------------------------------------------
 
-def collide(f, t, p):
-    """Post-collision populations f*_i(r, t) (right-hand side of Eq. 61)."""
+def collide(f, t, p, sites=None):
+    """Post-collision populations f*_i(r, t) (right-hand side of Eq. 61).
+
+    ``f`` may be a periodic cut-out of a larger system (``p`` then describes
+    the cut-out's shape) with ``sites`` its global site indices for the noise
+    keys; sites farther than the stencil from the cut-out's edge get the
+    whole system's result."""
     lat = p.lat
     rho = density(f)
     if not np.all(rho > 0):
@@ -325,7 +336,7 @@ def collide(f, t, p):
     mp = m - lam_b * (m - meq) + src
     if p.kT > 0:
         _, _, _, _, cs2 = landau(rho, p)
-        mp[lat.n_conserved:] += noise(rho, cs2, t, p)
+        mp[lat.n_conserved:] += noise(rho, cs2, t, p, sites)
     return lat.populations(mp)
 
 

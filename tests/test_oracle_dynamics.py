@@ -166,3 +166,30 @@ def test_noise_uses_the_site_counter():
     L = np.linalg.cholesky(lbm.noise_matrix(np.float64(0.0), p))
     want = np.sqrt(3 * p.kT) * (L @ n)
     assert np.allclose(x1.reshape(6, -1), want, atol=1e-16)
+
+
+@pytest.mark.parametrize("case", [CASES[0], dict(CASES[2], nx=12, ny=11, nz=9, a=-0.002, tau=tuple([1.0] * 19))])
+def test_cut_out_collision_matches_the_whole_system(case):
+    """collide on a periodic cut-out of radius 3 around a site, with the global
+    site indices as noise keys, gives the whole system's post-collision
+    populations at the sites within radius 1 of the centre, and so the centre's
+    streamed update (the stencil: density to radius 2 for the Guo force)."""
+    import dataclasses
+    p = lbm.Params(**case)
+    f = _rand_state(p, seed=7)
+    t = 11
+    full = lbm.step(f, t, p)
+    d3 = p.lattice == "D3Q19"
+    for (x, y, z) in [(0, 0, 0), (p.nx - 1, 2, p.nz - 1), (5, p.ny - 1, 1)]:
+        z = z if d3 else 0
+        ix = (np.arange(-3, 4) + x) % p.nx
+        iy = (np.arange(-3, 4) + y) % p.ny
+        iz = (np.arange(-3, 4) + z) % p.nz if d3 else np.array([0])
+        blk = f[:, iz][:, :, iy][:, :, :, ix]
+        gid = (iz[:, None, None] * p.ny + iy[None, :, None]) * p.nx + ix[None, None, :]
+        pb = dataclasses.replace(p, nx=7, ny=7, nz=7 if d3 else 1)
+        fs = lbm.collide(blk, t, pb, sites=gid.ravel())
+        c = p.lat.c
+        zc = 3 if d3 else 0
+        got = np.array([fs[i, zc - (c[i, 2] if d3 else 0), 3 - c[i, 1], 3 - c[i, 0]] for i in range(p.lat.q)])
+        assert np.allclose(got, full[:, z, y, x], rtol=0, atol=1e-15)

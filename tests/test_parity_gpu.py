@@ -204,6 +204,50 @@ def test_fss_160_full_size_sampled_parity(lb):
     ens.close()
 
 
+def test_large_256_sampled_parity_and_observables(lb):
+    """The one-system 256^3 FP32 workload (the largest single lattice) in the
+    benchmark's launch configuration: after one step, sampled sites (corners,
+    edges, faces, interior) match the oracle's update of each site from the same
+    state (its radius-3 cut-out, noise keyed by the global site index), and the
+    block observables of that step match the oracle's block moments of the
+    GPU's own state to 1e-10."""
+    s = synth.ensemble("large_256", "D3Q19")[0]
+    p = params_of(s)
+    n = p.nx
+    ens = lb.Ensemble([s], precision="fp32", obs_every=1)
+    ens.init(amplitude=0.01)
+    before = ens.read_fields(0)
+    ens.step(1)
+    ens.sync()
+    after = ens.read_fields(0)
+    fmax = np.abs(before).max()
+    c = p.lat.c
+    picks = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 17), (n - 1, 0, 0), (128, 0, 200), (77, 131, 0),
+             (15, 16, 17), (16, 15, 255), (200, 201, 202), (255, 100, 1)]
+    for (x, y, z) in picks:
+        ix, iy, iz = [(np.arange(-3, 4) + v) % n for v in (x, y, z)]
+        blk = before[:, iz][:, :, iy][:, :, :, ix]
+        gid = (iz[:, None, None] * n + iy[None, :, None]) * n + ix[None, None, :]
+        fs = lbm.collide(blk, 0, dataclasses.replace(p, nx=7, ny=7, nz=7), sites=gid.ravel())
+        want = np.array([fs[i, 3 - c[i, 2], 3 - c[i, 1], 3 - c[i, 0]] for i in range(p.lat.q)])
+        assert np.abs(after[:, z, y, x] - want).max() < TOL32 * fmax, (x, y, z)
+    levels, glob = ens.observables(0)
+    assert glob["n_samples"] == 1
+    lv = ob.levels(p)
+    row_all = ob.sample(ob.order_parameter(after), lv)
+    assert len(levels) == len(lv)
+    for L, blk, row in zip(levels, lv, row_all):
+        assert L["block"] == blk
+        got = np.array([L["n"], L["sum_m"], L["sum_m2"], L["sum_abs_m"], L["sum_m4"], L["sum_e"], L["sum_e2"]])
+        if blk == (n, n, n):
+            assert abs(got[1]) < 1e-12 * got[0] and got[0] == row[0]
+            continue
+        scale = np.maximum(np.abs(row), 1e-300)
+        scale[1] = row[3]
+        assert np.all(np.abs(got - row) <= 1e-10 * scale), (blk, got, row)
+    ens.close()
+
+
 def test_errors_are_reported_and_sticky(lb):
     s = _sys("D2Q9", "modeq", 16, 16, kT=1e-4, tau=[1.0] * 9)
     p = params_of(s)
