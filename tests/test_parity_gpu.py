@@ -186,14 +186,17 @@ def test_single_16_thousand_step_trajectory(lb, lattice):
     ens.close()
 
 
-def test_fss_160_full_size_sampled_parity(lb):
-    """The 160-system D3Q19 FP32 ensemble in the launch configuration the benchmark
-    times: after one step, three systems (smallest, a middle one, largest) are
-    compared with the oracle stepping each from the same state."""
-    systems = synth.ensemble("fss_160", "D3Q19")
-    ens = lb.Ensemble(systems, precision="fp32", obs_every=100)
+@pytest.mark.parametrize("workload,lattice", [("fss_160", "D3Q19"), ("fss_60", "D3Q19"), ("fss_160", "D2Q9")])
+def test_full_size_ensembles_sampled_parity(lb, workload, lattice):
+    """The batched FP32 ensembles in the launch configuration the benchmark times
+    (160 systems of 16^3..64^3, the uneven 60 systems of 32^3..128^3, and the
+    paper's D2Q9 lattice at 64^2..512^2): after one step, three systems
+    (smallest, a middle one, largest) are compared with the oracle stepping each
+    from the same state."""
+    systems = synth.ensemble(workload, lattice)
+    ens = lb.Ensemble(systems, precision="fp32", obs_every=100, graph_chunk=100)
     ens.init(amplitude=0.01)
-    picks = [0, 77, len(systems) - 1]
+    picks = [0, len(systems) // 2, len(systems) - 1]
     before = {k: ens.read_fields(k) for k in picks}
     ens.step(1)
     ens.sync()
