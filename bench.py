@@ -38,6 +38,8 @@ WORKLOADS = {
     "single_64": dict(ensemble="single_64", lattice="D3Q19", precision="fp32"),
     "large_256": dict(ensemble="large_256", lattice="D3Q19", precision="fp32"),
     "fss_160_fp64": dict(ensemble="fss_160", lattice="D3Q19", precision="fp64"),
+    "large_256_fp64": dict(ensemble="large_256", lattice="D3Q19", precision="fp64"),
+    "large_256_d2q9": dict(ensemble="large_256", lattice="D2Q9", precision="fp32"),
     "fss_160_64": dict(ensemble="fss_160_64", lattice="D3Q19", precision="fp32"),
     "fss_60": dict(ensemble="fss_60", lattice="D3Q19", precision="fp32"),
 }
@@ -184,17 +186,26 @@ def load_peak():
 
 def load_traffic(workload):
     """DRAM bytes per step-kernel launch from the committed ncu summary ("key: value"
-    lines), if it was taken on this kernel source and this workload; else None."""
+    lines; each "workload:" line starts the record of one workload), if it was
+    taken on this kernel source and this workload; else None."""
     try:
         with open(TRAFFIC_FILE) as fh:
-            t = dict(line.split(":", 1) for line in fh if ":" in line and not line.startswith("#"))
+            lines = [ln for ln in fh if ":" in ln and not ln.startswith("#")]
     except OSError:
         return None
-    t = {k.strip(): v.strip() for k, v in t.items()}
-    if t.get("kernel_source_hash") != kernel_source_hash() or t.get("workload") != workload:
+    common, records, cur = {}, {}, None
+    for ln in lines:
+        k, v = (x.strip() for x in ln.split(":", 1))
+        if k == "workload":
+            cur = records.setdefault(v, {})
+        elif cur is None:
+            common[k] = v
+        else:
+            cur[k] = v
+    if common.get("kernel_source_hash") != kernel_source_hash() or workload not in records:
         return None
     try:
-        return float(t["dram_bytes_per_launch"])
+        return float(records[workload]["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
 
