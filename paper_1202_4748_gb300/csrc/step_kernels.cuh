@@ -909,6 +909,24 @@ __global__ void __launch_bounds__(TX* TY, MINB)
 //     while plane zz + 1 is summed.  A footprint site then reads its 19 pulled
 //     values from the stage at fixed offsets.  Needs nx % 4 == 0, nx >= 8 and
 //     every side >= 3 (the host checks; the stage is dynamic shared memory).
+// Footprint slot -> footprint index (row-major over the (TX + 2H) x (TY + 2H)
+// plane): slots 0 .. TX TY - 1 are the tile's own sites row by row, then the
+// H rows above and below, then the H columns on each side, so a warp's slots
+// are all tile sites or all halo sites.
+template <int TX, int TY, int H>
+__device__ __forceinline__ int foot_slot(int s) {
+    constexpr int SX = TX + 2 * H;
+    if (s < TX * TY) return (s / TX + H) * SX + (s % TX + H);
+    int h = s - TX * TY;
+    if (h < 2 * H * SX) {
+        const int r = h / SX, c = h % SX;
+        return (r < H ? r : TY + r) * SX + c;
+    }
+    h -= 2 * H * SX;
+    const int r = h / (2 * H), c = h % (2 * H);
+    return (H + r) * SX + (c < H ? c : TX + c);
+}
+
 template <class L, int TX, int TY, int ZC, int PW>
 struct BulkStage {
     static constexpr int H = HaloOf<L, GUO>::H;
@@ -1037,10 +1055,11 @@ __global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const S
             bool inb[FB];
             sfor<0, FB>([&](auto SI) {
                 constexpr int si = SI;
-                const int idx = ptid + (b0 + si) * NP;
+                const int sl = ptid + (b0 + si) * NP;
+                const int idx = sl < SP ? foot_slot<TX, TY, H>(sl) : SP;
                 const int px = idx % SX, py = idx / SX;
                 const int gx = tl.y + px - H, gy = tl.z + py - H;
-                inb[si] = b0 + si < FS && idx < SP && gx < nx + H && gy < ny + H;
+                inb[si] = b0 + si < FS && sl < SP && gx < nx + H && gy < ny + H;
                 if (inb[si]) {
                     const Nbr nb(sm ? wrapm(gx, nx) : wrap2(gx, nx), sm ? wrapm(gy, ny) : wrap2(gy, ny), wz, nx, ny,
                                  nz, true);
@@ -1049,17 +1068,17 @@ __global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const S
             });
             sfor<0, FB>([&](auto SI) {
                 constexpr int si = SI;
-                const int idx = ptid + (b0 + si) * NP;
-                if (b0 + si < FS && idx < SP) {
+                const int sl = ptid + (b0 + si) * NP;
+                if (b0 + si < FS && sl < SP) {
+                    const int idx = foot_slot<TX, TY, H>(sl);
                     Real v = Real(0);
                     if (inb[si]) {
                         sfor<0, Q>([&](auto I) { v += g[si][decltype(I)::value]; });
-                        const int ix = idx % SX - H, iy = idx / SX - H;
-                        if (ix >= 0 && ix < TX && iy >= 0 && iy < TY) {
+                        if (sl < NC) {                   // slots 0 .. NC - 1 are the tile sites, row by row
                             Real jm[3];
                             momentum_of<L, Real>(g[si], jm);
                             sfor<0, 3>([&](auto C) {
-                                sj[(slot * 3 + int(C)) * NC + iy * TX + ix] = jm[decltype(C)::value];
+                                sj[(slot * 3 + int(C)) * NC + sl] = jm[decltype(C)::value];
                             });
                         }
                     }
