@@ -72,3 +72,48 @@ def test_two_ranks_equal_one_process(tmp_path):
     ref = [_run_one(s) for s in _systems()]
     assert np.array_equal(acc, np.stack([r["acc"][-1] for r in ref]))
     assert np.array_equal(fsum, np.concatenate([r["f_sum"].ravel() for r in ref]))
+
+
+def _failing_worker(rank, world, port, outdir):
+    import datetime
+    import time
+    import torch.distributed as dist
+    from paper_1202_4748_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    systems = _systems()
+    mine = shard.partition(systems, world)[rank]
+    if rank == 1:
+        os._exit(3)                       # leaves between steps, no collective in flight
+    local = {k: _run_one(systems[k], steps=4) for k in mine}
+    t0 = time.time()
+    try:
+        shard.gather(local, len(systems))
+        outcome = "completed"
+    except Exception as exc:              # the survivor must see an error, not hang
+        outcome = type(exc).__name__
+    with open(os.path.join(outdir, "rank0.txt"), "w") as fh:
+        fh.write("%s %.2f" % (outcome, time.time() - t0))
+
+
+def test_a_rank_that_leaves_makes_the_gather_fail_not_hang(tmp_path):
+    """Failure detection on the host: when one rank exits before the final
+    gather, the surviving rank's gather ends with an error within the process
+    group's 10 s timeout instead of waiting forever."""
+    import multiprocessing
+    ctx = multiprocessing.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, str(tmp_path))) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    alive = [p for p in procs if p.is_alive()]
+    for p in alive:
+        p.kill()
+    assert not alive, "a rank hung"
+    assert procs[1].exitcode == 3
+    outcome, secs = open(os.path.join(tmp_path, "rank0.txt")).read().split()
+    assert outcome != "completed"
+    assert float(secs) < 60.0
