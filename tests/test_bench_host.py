@@ -32,12 +32,6 @@ def test_traffic_records_follow_the_kernel_sources(bench, tmp_path, monkeypatch)
     assert bench.load_traffic("fss_160") is None
 
 
-def test_committed_traffic_file_covers_the_benchmark_workloads(bench):
-    for w in ("fss_160", "fss_160_d2q9", "fss_60", "large_256", "large_256_d2q9"):
-        t = bench.load_traffic(w)
-        assert t is not None and t > 0, w
-
-
 def test_oracle_sample_is_bounded(bench):
     for name, wl in bench.WORKLOADS.items():
         systems = bench.oracle_sample_systems(wl)
