@@ -65,7 +65,7 @@ typedef enum {
 enum { LB_D2Q9 = 0, LB_D3Q19 = 1 };
 enum { LB_MODEQ = 0, LB_GUO = 1 };
 enum { LB_FP64 = 0, LB_FP32_DEVIATION = 1 };
-enum { LB_INIT_UNIFORM_NOISE = 0, LB_INIT_FROM_RHO = 1 };
+enum { LB_INIT_UNIFORM_NOISE = 0, LB_INIT_FROM_RHO = 1, LB_INIT_TANH_STRIPE = 2 };
 #define LB_MAX_Q 19
 #define LB_MAX_LEVELS 32
 
@@ -169,10 +169,25 @@ lb_status lb_create(const lb_system_desc* systems, int n_systems, const lb_run_o
  *                          system's Philox stream (draw 0xFF, step 0), minus its
  *                          FP64 mean so that the average density is rho_c;
  *   LB_INIT_FROM_RHO       rho from h_rho: float64, all systems concatenated in
- *                          descriptor order, each [nz][ny][nx].
+ *                          descriptor order, each [nz][ny][nx];
+ *   LB_INIT_TANH_STRIPE    the two-interface mean-field stripe of
+ *                          lb_stripe_density (h_rho and amplitude unused).
  * Clears observables and the sticky error.  Synchronises the stream.
- * Errors: LB_ERR_ARG (mode, missing h_rho), LB_ERR_CUDA. */
+ * Errors: LB_ERR_ARG (mode, missing h_rho, a stripe for a system without
+ * a < 0 < b), LB_ERR_CUDA. */
 lb_status lb_init(lb_ctx* ctx, int mode, double amplitude, const double* h_rho);
+
+/* Mean-field stripe density (host only, no device call), Sec. II A: below the
+ * critical point (a < 0, b > 0) the Landau potential has the coexistence
+ * densities rho_c +- phi0, phi0 = sqrt(-a/b) (Eq. 20), joined by a tanh
+ * interface of width w = sqrt(-2 kappa / a) (Eqs. 22-23).  Writes, for every
+ * system in descriptor order ([nz][ny][nx] each, concatenated into out, a
+ * caller-owned array of the ensemble's site count), two flat interfaces
+ * normal to x at x = nx/4 and 3 nx/4:
+ *   rho(x) = rho_c + phi0 (tanh((x - nx/4)/w) - tanh((x - 3nx/4)/w) - 1),
+ * the sharp step rho_c +- phi0 when kappa = 0.  Errors: LB_ERR_ARG (null
+ * pointers, n < 1, a side < 1, a >= 0, b <= 0 or kappa < 0 in a system). */
+lb_status lb_stripe_density(const lb_system_desc* systems, int n_systems, double* out);
 
 /* Advance all systems nsteps time steps (Eq. 61: collide, add noise, stream),
  * sampling observables on the obs_every / sk_every schedule.  Asynchronous

@@ -28,7 +28,7 @@ LB_ERR_UNSUPPORTED, LB_ERR_STATE, LB_ERR_IO, LB_ERR_NO_ROOT, LB_ERR_TIMEOUT = -7
 LB_D2Q9, LB_D3Q19 = 0, 1
 LB_MODEQ, LB_GUO = 0, 1
 LB_FP64, LB_FP32_DEVIATION = 0, 1
-LB_INIT_UNIFORM_NOISE, LB_INIT_FROM_RHO = 0, 1
+LB_INIT_UNIFORM_NOISE, LB_INIT_FROM_RHO, LB_INIT_TANH_STRIPE = 0, 1, 2
 LB_MAX_Q = 19
 LB_MAX_LEVELS = 32
 LB_MAX_HIST_BINS = 4096
@@ -76,6 +76,7 @@ _SIG = {
     "lb_create": (ctypes.c_int, [ctypes.POINTER(lb_system_desc), ctypes.c_int, ctypes.POINTER(lb_run_opts),
                                  _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
     "lb_init": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, _P]),
+    "lb_stripe_density": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "lb_step": (ctypes.c_int, [_P, ctypes.c_int64]),
     "lb_sync": (ctypes.c_int, [_P]),
     "lb_observables": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(lb_obs_level), ctypes.c_int,
@@ -241,6 +242,16 @@ def kernel_variants(lattice):
     buf = (ctypes.c_int32 * (VARIANT_COLS * n))()
     lb_kernel_variants(code, buf, n)
     return [tuple(buf[VARIANT_COLS * r + k] for k in range(VARIANT_COLS)) for r in range(n)]
+
+
+def stripe_density(systems):
+    """The mean-field two-interface stripe density of every system (lb_stripe_density),
+    concatenated in descriptor order, each [nz][ny][nx]."""
+    desc = make_desc(systems)
+    n = sum(s["nx"] * s["ny"] * s["nz"] for s in systems)
+    out = np.empty(n, dtype=np.float64)
+    check(lb_stripe_density(desc, len(systems), out.ctypes.data_as(_P)), "lb_stripe_density")
+    return out
 
 
 def workspace_bytes(systems, **opts):

@@ -794,10 +794,42 @@ lb_status lb_create(const lb_system_desc* systems, int n_systems, const lb_run_o
     return LB_OK;
 }
 
+lb_status lb_stripe_density(const lb_system_desc* s, int n, double* out) {
+    if (!s || n < 1 || !out) return LB_ERR_ARG;
+    size_t off = 0;
+    for (int k = 0; k < n; ++k) {
+        const lb_system_desc& d = s[k];
+        if (d.nx < 1 || d.ny < 1 || d.nz < 1) return LB_ERR_ARG;
+        if (!(d.a < 0) || !(d.b > 0) || !(d.kappa >= 0) || !std::isfinite(d.a) || !std::isfinite(d.b))
+            return LB_ERR_ARG;
+        const double phi0 = std::sqrt(-d.a / d.b), w = std::sqrt(-2.0 * d.kappa / d.a);
+        const double x1 = 0.25 * d.nx, x2 = 0.75 * d.nx;
+        for (int x = 0; x < d.nx; ++x) {
+            const double t = w > 0 ? std::tanh((x - x1) / w) - std::tanh((x - x2) / w) - 1.0
+                                   : (x >= x1 && x < x2 ? 1.0 : -1.0);
+            const double rho = d.rho_c + phi0 * t;
+            for (int z = 0; z < d.nz; ++z)
+                for (int y = 0; y < d.ny; ++y) out[off + (size_t(z) * d.ny + y) * d.nx + x] = rho;
+        }
+        off += size_t(d.nx) * d.ny * d.nz;
+    }
+    return LB_OK;
+}
+
 lb_status lb_init(lb_ctx* c, int mode, double amplitude, const double* h_rho) {
     if (!c) return LB_ERR_ARG;
-    if (mode != LB_INIT_UNIFORM_NOISE && mode != LB_INIT_FROM_RHO) return LB_ERR_ARG;
+    if (mode != LB_INIT_UNIFORM_NOISE && mode != LB_INIT_FROM_RHO && mode != LB_INIT_TANH_STRIPE) return LB_ERR_ARG;
     if (mode == LB_INIT_FROM_RHO && !h_rho) return LB_ERR_ARG;
+    std::vector<double> stripe;
+    if (mode == LB_INIT_TANH_STRIPE) {
+        std::vector<lb_system_desc> desc;
+        for (auto& h : c->sys) desc.push_back(h.d);
+        stripe.resize(size_t(c->P.n_sites));
+        const lb_status st = lb_stripe_density(desc.data(), int(desc.size()), stripe.data());
+        if (st != LB_OK) return st;
+        h_rho = stripe.data();          // then exactly the LB_INIT_FROM_RHO path
+        mode = LB_INIT_FROM_RHO;
+    }
     if (mode == LB_INIT_UNIFORM_NOISE && !(amplitude >= 0 && std::isfinite(amplitude))) return LB_ERR_ARG;
     const Plan& P = c->P;
     const SysDev* sys = c->at<SysDev>(P.sys);

@@ -292,3 +292,29 @@ def test_pt_workspace_sizes_and_validation():
     assert lb.lb_pt_symmetric(lb.LB_D2Q9, 8, 1e-3, -0.1, 0.01, 1e-4, None, 0, None, out) == lb.LB_ERR_ARG
     assert lb.lb_pt_sums(lb.LB_D2Q9, 8, 0.0, 0.01, None, 0, None, out) == lb.LB_ERR_ARG
     assert lb.lb_pt_sums(lb.LB_D2Q9, 8, 1.0, 0.01, None, 0, None, out) == lb.LB_ERR_WORKSPACE
+
+
+def test_stripe_density_is_the_mean_field_profile():
+    """lb_stripe_density (host only): coexistence plateaus rho_c +- sqrt(-a/b)
+    (Eq. 20) joined by tanh interfaces of width sqrt(-2 kappa/a) (Eqs. 22-23) at
+    x = nx/4 and 3nx/4, every system in descriptor order."""
+    import paper_1202_4748_gb300 as lb
+    systems = [synth.system("D2Q9", "modeq", n=64, a=-0.01, b=0.1, kappa=0.1),
+               dict(synth.system("D3Q19", "guo", n=12, a=-0.004, b=0.1, kappa=0.0, rho_c=1.3), ny=5, nz=3)]
+    rho = lb.stripe_density(systems)
+    assert rho.shape == (64 * 64 + 12 * 5 * 3,)
+    a = rho[:64 * 64].reshape(64, 64)
+    x = np.arange(64.0)
+    phi0, w = np.sqrt(0.1), np.sqrt(20.0)
+    want = 1.0 + phi0 * (np.tanh((x - 16) / w) - np.tanh((x - 48) / w) - 1)
+    assert np.allclose(a, want[None, :], rtol=0, atol=1e-14)
+    assert abs(a[:, 32].mean() - (1 + phi0)) < 2e-3 and abs(a[:, 0].mean() - (1 - phi0)) < 2e-3
+    b = rho[64 * 64:].reshape(3, 5, 12)                    # kappa = 0: the sharp step
+    phi1 = np.sqrt(0.04)
+    step = np.where((np.arange(12) >= 3) & (np.arange(12) < 9), 1.3 + phi1, 1.3 - phi1)
+    assert np.array_equal(b, np.broadcast_to(step, b.shape))
+    for bad in (dict(a=0.001), dict(a=-0.01, b=-0.1), dict(a=-0.01, kappa=-1.0)):
+        with pytest.raises(lb.LBError) as e:
+            lb.stripe_density([dict(systems[0], **bad)])
+        assert e.value.status == lb.LB_ERR_ARG
+    assert lb.lb_stripe_density(None, 1, None) == lb.LB_ERR_ARG

@@ -251,6 +251,37 @@ def test_large_256_sampled_parity_and_observables(lb):
     ens.close()
 
 
+@pytest.mark.parametrize("lattice,coupling", [("D2Q9", "modeq"), ("D3Q19", "guo")])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tanh_stripe_init_is_the_stripe_density(lb, lattice, coupling, precision):
+    """LB_INIT_TANH_STRIPE starts every system from lb_stripe_density's profile:
+    the same state, bit for bit, as LB_INIT_FROM_RHO with that density, whose
+    populations sum to it."""
+    n = 32 if lattice == "D2Q9" else 12
+    systems = [synth.system(lattice, coupling, n=n, a=-0.01, b=0.1, kappa=0.05, kT=0.0, system_id=0),
+               synth.system(lattice, coupling, n=n + 4, a=-0.004, b=0.1, kappa=0.02, kT=0.0, system_id=1)]
+    rho = lb.stripe_density(systems)
+    ea = lb.Ensemble(systems, precision=precision)
+    ea.init(mode=lb.LB_INIT_TANH_STRIPE)
+    eb = lb.Ensemble(systems, precision=precision)
+    eb.init(rho=rho)
+    tol = 1e-13 if precision == "fp64" else 1e-6
+    off = 0
+    for k, s in enumerate(systems):
+        fa, fb = ea.read_fields(k), eb.read_fields(k)
+        assert np.array_equal(fa, fb)
+        m = s["nx"] * s["ny"] * s["nz"]
+        want = rho[off:off + m].reshape(s["nz"], s["ny"], s["nx"])
+        assert np.abs(fa.sum(axis=0) - want).max() < tol
+        off += m
+    ea.step(3)
+    eb.step(3)
+    for k in range(len(systems)):
+        assert np.array_equal(ea.read_fields(k), eb.read_fields(k))
+    ea.close()
+    eb.close()
+
+
 def test_errors_are_reported_and_sticky(lb):
     s = _sys("D2Q9", "modeq", 16, 16, kT=1e-4, tau=[1.0] * 9)
     p = params_of(s)
