@@ -45,7 +45,9 @@ WORKLOADS = {
 }
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
-KERNEL_SOURCES = ["paper_1202_4748_gb300/csrc/step_kernels.cuh", "paper_1202_4748_gb300/csrc/lb_device.cuh"]
+KERNEL_SOURCES = ["paper_1202_4748_gb300/csrc/step_kernels.cuh", "paper_1202_4748_gb300/csrc/lb_device.cuh",
+                  "paper_1202_4748_gb300/csrc/step_kernel_pair.cuh", "paper_1202_4748_gb300/csrc/collide_d3q19.cuh",
+                  "paper_1202_4748_gb300/csrc/vec2.cuh"]
 
 
 def kernel_source_hash():

@@ -367,12 +367,16 @@ lb_status lb_load(lb_ctx* ctx, const char* path);
  * (cp.async.bulk) into shared memory, when every system has nx % 4 == 0,
  * nx >= 8 and all sides >= 3, else the scheme-0 kernel of the same tile runs,
  * 2 = (D2Q9, modified equilibrium only) row-marching strips: one warp per tile
- * of 32 sites x y rows, densities in registers and warp shuffles) into out
- * (nullable) and returns the number of variants (negative lb_status on error).
+ * of 32 sites x y rows, densities in registers and warp shuffles; sites per
+ * consumer thread: 1, or 2 = (D3Q19, warp-specialised) two x-adjacent sites
+ * per consumer thread with paired FP32 arithmetic, when every system has
+ * nx % 4 == 0, else the one-site warp-specialised kernel of the same tile runs)
+ * into out (nullable) and returns the number of variants (negative lb_status
+ * on error).
  * Row 0 is the default; where the coupling cannot run it (scheme 2 with the
  * Guo form) the first row it can run is.  Selecting a row the coupling cannot
  * run gives LB_ERR_UNSUPPORTED.  Used by the autotuner; no device call. */
-#define LB_VARIANT_COLS 6
+#define LB_VARIANT_COLS 7
 int lb_kernel_variants(int lattice, int32_t* out, int max_rows);
 
 /* Host-armed fault injection for testing the error paths without faulting a

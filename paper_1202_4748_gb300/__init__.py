@@ -33,7 +33,7 @@ LB_MAX_Q = 19
 LB_MAX_LEVELS = 32
 LB_MAX_HIST_BINS = 4096
 LB_HIST_EST = 11
-LB_VARIANT_COLS = VARIANT_COLS = 6
+LB_VARIANT_COLS = VARIANT_COLS = 7
 LB_FAULT_NONE, LB_FAULT_DENSITY, LB_FAULT_NOISE, LB_FAULT_NONFINITE, LB_FAULT_TIMEOUT, LB_FAULT_LAUNCH = range(6)
 LB_NOALLOC_MAX_SITES = 1 << 18
 Q_OF = {LB_D2Q9: 9, LB_D3Q19: 19}
@@ -234,7 +234,7 @@ def histogram_estimates(counts, lo, hi, vol, kT, m_cut=0.0, frac=0.2):
 
 def kernel_variants(lattice):
     """Compiled step-kernel variants of a lattice: list of
-    (x, y, z, occupancy, producer warps, staging)."""
+    (x, y, z, occupancy, producer warps, staging, sites per thread)."""
     code = _LATTICE[lattice] if isinstance(lattice, str) else int(lattice)
     n = lb_kernel_variants(code, None, 0)
     if n < 0:

@@ -13,9 +13,11 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbfluct.so")
 SOURCES = ["api.cu", "obs.cu", "sk.cu", "noalloc.cu", "lattice_d2q9.cu", "lattice_d3q19.cu", "pt.cu"]
-HEADERS = ["lb_device.cuh", "lb_launch.h", "step_kernels.cuh", "lattice_kernels.cuh", "lattice_tu.cuh"]
+HEADERS = ["lb_device.cuh", "lb_launch.h", "step_kernels.cuh", "lattice_kernels.cuh", "lattice_tu.cuh", "vec2.cuh",
+           "collide_d3q19.cuh", "step_kernel_pair.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+TU_FLAGS = {}                # extra nvcc flags per translation unit
 
 
 def nvcc():
@@ -44,7 +46,7 @@ def build(force=False, verbose=False, extra_flags=()):
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [exe, *FLAGS, *ARCH, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [exe, *FLAGS, *ARCH, *TU_FLAGS.get(src, []), *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))

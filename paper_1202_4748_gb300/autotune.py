@@ -7,7 +7,7 @@ of step launches, after a warm-up) through the public API, and the fastest is
 returned.  Results are cached in a JSON file keyed by lattice, coupling,
 precision and the multiset of system sizes, so a later run of the same ensemble
 picks its variant without re-timing.  A variant is named by its row
-``(x, y, z, occupancy, producer warps, staging)``; ``Ensemble(..., variant=variant_index(...))``
+``(x, y, z, occupancy, producer warps, staging, sites per thread)``; ``Ensemble(..., variant=variant_index(...))``
 selects it.
 """
 import json

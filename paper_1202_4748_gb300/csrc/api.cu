@@ -435,7 +435,8 @@ SysDev to_dev(const SysHost& h) {
 }  // namespace
 
 struct lb_ctx {
-    int lattice = 0, coupling = 0, fp32 = 0, q = 9, n_sys = 0, tile_id = 0, bgk_only = 0, bulk_ok = 0;
+    int lattice = 0, coupling = 0, fp32 = 0, q = 9, n_sys = 0, tile_id = 0, bgk_only = 0, bulk_ok = 0,
+        pair_ok = 0;
     lb_run_opts opts{};
     std::vector<SysHost> sys;
     Plan P;
@@ -608,6 +609,7 @@ cudaError_t launch_steps(lb_ctx* c, int64_t n) {
         a.tile_id = c->tile_id;
         a.bgk_only = c->bgk_only;
         a.bulk_ok = c->bulk_ok;
+        a.pair_ok = c->pair_ok;
         cudaError_t e = launch_step_any(c, a);
         if (e != cudaSuccess) return e;
         c->launches += 1;
@@ -743,6 +745,12 @@ lb_status lb_create(const lb_system_desc* systems, int n_systems, const lb_run_o
     c->bulk_ok = 1;
     for (auto& s : sd)
         if (s.nx % 4 != 0 || s.nx < 8 || s.small) c->bulk_ok = 0;
+    // paired-site kernel: its producers pull aligned quads of x-adjacent sites
+    // and its consumers store aligned pairs, which needs every nx to be a
+    // multiple of 4 (every population array then starts 16-byte aligned)
+    c->pair_ok = 1;
+    for (auto& s : sd)
+        if (s.nx % 4 != 0) c->pair_ok = 0;
     bool ok = cudaMemcpyAsync(c->ws + P.sys, sd.data(), sizeof(SysDev) * sd.size(), cudaMemcpyHostToDevice,
                               c->stream) == cudaSuccess;
     // physics in the step kernel's precision (staged on the host, copied synchronously)

@@ -1,0 +1,347 @@
+// Fully relaxed (every non-conserved mode at tau = 1) Guo-forced collision of
+// the D3Q19 model (Eq. 61 with the moment expansion of Eq. 66, the noise of
+// Eq. 68 in its lattice-general form, and the Landau pressure p0 of Eq. 3 in
+// the equilibrium), written out for this basis so that the arithmetic is a
+// short straight line:
+//
+//  * post-collision moments (deviation form, lambda = 1):
+//      w_0 = drho,  w_a = j_a + F_a (a = x, y, z),
+//      with A_bc = rho u_b u_c + (u_b F_c + u_c F_b) / 2 (the equilibrium's
+//      second moments plus half the Guo source, whose projections on the
+//      second-order modes come out with unit coefficients),
+//      w_4 = tr A - iso + xi_4,  w_5 = 3 A_xx - tr A + xi_5,  w_6 = A_yy - A_zz + xi_6,
+//      w_7 = A_xy + xi_7,  w_8 = A_yz + xi_8,  w_9 = A_zx + xi_9,
+//      w_16 = iso + xi_16,  w_a = xi_a on the other ghost modes,
+//      iso = drho - 3 p0, u = (j + F / 2) / rho, F = kappa rho grad(lap rho);
+//  * h_a = w_a / (36 N_a), and f_i = 36 t_i sum_a T_ai h_a evaluated through
+//    the sums that the velocities share (the rest, face and edge classes of
+//    the basis table), about half the operations of a dense T^-1 product.
+//
+// V is float or double (one site) or float2 (two sites in lockstep, the
+// paired FP32 instructions); each lane of the float2 form gives the bits of
+// the float form.  The noise draws (Philox4x32-10, Box-Muller) are per site.
+#pragma once
+
+#include "lb_device.cuh"
+#include "vec2.cuh"
+
+namespace lbf {
+
+// Philox counter words shared by the sites of one step of one system.
+struct NoiseKey {
+    uint32_t k0, k1;      // key: the seed
+    uint32_t slo, shi;    // step
+    uint32_t tag;         // system_id << 8 (the draw index fills the low byte)
+};
+__device__ __forceinline__ NoiseKey noise_key(const SysDev& S, int64_t step) {
+    NoiseKey k;
+    k.k0 = S.seed_lo;
+    k.k1 = S.seed_hi;
+    k.slo = uint32_t(uint64_t(step) & 0xffffffffu);
+    k.shi = uint32_t(uint64_t(step) >> 32);
+    k.tag = S.system_id << 8;
+    return k;
+}
+
+// Site indices of the lanes: one per lane.
+template <class V>
+struct SiteIdx {
+    using type = uint32_t;
+};
+template <>
+struct SiteIdx<float2> {
+    using type = uint2;
+};
+
+// Four normals of draw d for every lane, multiplied by the lane's noise scale
+// sc (n = sc R cos, sc R sin from the words (w0, w1), (w2, w3)).  need3 = false
+// skips the sine of the second pair (its normal is not used).
+__device__ __forceinline__ void draw4(const NoiseKey& k, uint32_t site, uint32_t d, float sc, float (&n)[4],
+                                      bool need3) {
+    const uint4 w = philox4x32_10(make_uint4(site, k.slo, k.shi, k.tag | d), k.k0, k.k1);
+    const float nsc = -sc;     // the angle is taken as 2 pi U - pi: cos and sin change sign
+    const float ua0 = vfma(float(w.x), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float ub0 = vfma(float(w.y), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float ua1 = vfma(float(w.z), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float ub1 = vfma(float(w.w), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float r20 = fmaxf(vmul(__log2f(ua0), -1.3862943611198906f), 1e-30f);
+    const float r21 = fmaxf(vmul(__log2f(ua1), -1.3862943611198906f), 1e-30f);
+    const float rr0 = vmul(vmul(r20, rsqrtf(r20)), nsc);
+    const float rr1 = vmul(vmul(r21, rsqrtf(r21)), nsc);
+    const float t0 = vfma(ub0, 6.2831853071795865f, -3.1415926535897932f);
+    const float t1 = vfma(ub1, 6.2831853071795865f, -3.1415926535897932f);
+    float s0, c0;
+    __sincosf(t0, &s0, &c0);
+    n[0] = vmul(rr0, c0);
+    n[1] = vmul(rr0, s0);
+    if (need3) {
+        float s1, c1;
+        __sincosf(t1, &s1, &c1);
+        n[2] = vmul(rr1, c1);
+        n[3] = vmul(rr1, s1);
+    } else {
+        n[2] = vmul(rr1, __cosf(t1));
+        n[3] = 0.0f;
+    }
+}
+
+// Two sites: the same sequence lane by lane, the lane-independent arithmetic paired.
+__device__ __forceinline__ void draw4(const NoiseKey& k, uint2 site, uint32_t d, float2 sc, float2 (&n)[4],
+                                      bool need3) {
+    const uint4 wa = philox4x32_10(make_uint4(site.x, k.slo, k.shi, k.tag | d), k.k0, k.k1);
+    const uint4 wb = philox4x32_10(make_uint4(site.y, k.slo, k.shi, k.tag | d), k.k0, k.k1);
+    const float2 nsc = make_float2(-sc.x, -sc.y);
+    const float2 sA = vk<float2>(2.3283064365386963e-10), sB = vk<float2>(1.1641532182693481e-10);
+    const float2 ua0 = vfma(make_float2(float(wa.x), float(wb.x)), sA, sB);
+    const float2 ub0 = vfma(make_float2(float(wa.y), float(wb.y)), sA, sB);
+    const float2 ua1 = vfma(make_float2(float(wa.z), float(wb.z)), sA, sB);
+    const float2 ub1 = vfma(make_float2(float(wa.w), float(wb.w)), sA, sB);
+    const float2 m2ln2 = vk<float2>(-1.3862943611198906);
+    float2 r20 = vmul(make_float2(__log2f(ua0.x), __log2f(ua0.y)), m2ln2);
+    float2 r21 = vmul(make_float2(__log2f(ua1.x), __log2f(ua1.y)), m2ln2);
+    r20 = make_float2(fmaxf(r20.x, 1e-30f), fmaxf(r20.y, 1e-30f));
+    r21 = make_float2(fmaxf(r21.x, 1e-30f), fmaxf(r21.y, 1e-30f));
+    const float2 rr0 = vmul(vmul(r20, make_float2(rsqrtf(r20.x), rsqrtf(r20.y))), nsc);
+    const float2 rr1 = vmul(vmul(r21, make_float2(rsqrtf(r21.x), rsqrtf(r21.y))), nsc);
+    const float2 tw = vk<float2>(6.2831853071795865), tp = vk<float2>(-3.1415926535897932);
+    const float2 t0 = vfma(ub0, tw, tp);
+    const float2 t1 = vfma(ub1, tw, tp);
+    float2 s0, c0;
+    __sincosf(t0.x, &s0.x, &c0.x);
+    __sincosf(t0.y, &s0.y, &c0.y);
+    n[0] = vmul(rr0, c0);
+    n[1] = vmul(rr0, s0);
+    if (need3) {
+        float2 s1, c1;
+        __sincosf(t1.x, &s1.x, &c1.x);
+        __sincosf(t1.y, &s1.y, &c1.y);
+        n[2] = vmul(rr1, c1);
+        n[3] = vmul(rr1, s1);
+    } else {
+        n[2] = vmul(rr1, make_float2(__cosf(t1.x), __cosf(t1.y)));
+        n[3] = make_float2(0.0f, 0.0f);
+    }
+}
+
+// FP64: U = (x + 1/2) 2^-32 exactly, R = sqrt(-2 ln U), angle 2 pi U_b, with
+// the library's correctly rounded functions.
+__device__ __forceinline__ void draw4(const NoiseKey& k, uint32_t site, uint32_t d, double sc, double (&n)[4],
+                                      bool need3) {
+    const uint4 w = philox4x32_10(make_uint4(site, k.slo, k.shi, k.tag | d), k.k0, k.k1);
+    double a, b;
+    box_muller(w.x, w.y, a, b);
+    n[0] = vmul(sc, a);
+    n[1] = vmul(sc, b);
+    box_muller(w.z, w.w, a, b);
+    n[2] = vmul(sc, a);
+    n[3] = need3 ? vmul(sc, b) : 0.0;
+}
+
+// sqrt(x) for x >= 0 in the lane precision (0 at 0): x rsqrt(x) in float.
+__device__ __forceinline__ float lane_sqrt(float x) { return x > 0.0f ? vmul(x, rsqrtf(x)) : 0.0f; }
+__device__ __forceinline__ double lane_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float lane_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double lane_rsqrt(double x) { return rsqrt(x); }
+
+// Laplacian of the density, lap rho = 6 sum_i t_i (rho(r + c_i) - rho(r))
+// = (1/3) (sum of the 6 face neighbours) + (1/6) (sum of the 12 edge
+// neighbours) - 4 rho(r), summed in a fixed order (rv.at<cx, cy, cz>() is the
+// density at r + c).
+template <class V, class RV>
+__device__ __forceinline__ V lap_d3q19(const RV& rv) {
+    const V faces = vadd(vadd(vadd(rv.template at<1, 0, 0>(), rv.template at<-1, 0, 0>()),
+                              vadd(rv.template at<0, 1, 0>(), rv.template at<0, -1, 0>())),
+                         vadd(rv.template at<0, 0, 1>(), rv.template at<0, 0, -1>()));
+    const V exy = vadd(vadd(rv.template at<1, 1, 0>(), rv.template at<-1, -1, 0>()),
+                       vadd(rv.template at<1, -1, 0>(), rv.template at<-1, 1, 0>()));
+    const V exz = vadd(vadd(rv.template at<1, 0, 1>(), rv.template at<-1, 0, -1>()),
+                       vadd(rv.template at<1, 0, -1>(), rv.template at<-1, 0, 1>()));
+    const V eyz = vadd(vadd(rv.template at<0, 1, 1>(), rv.template at<0, -1, -1>()),
+                       vadd(rv.template at<0, 1, -1>(), rv.template at<0, -1, 1>()));
+    const V edges = vadd(vadd(exy, exz), eyz);
+    return vfma(faces, vk<V>(1.0 / 3.0), vfma(edges, vk<V>(1.0 / 6.0), vmul(rv.template at<0, 0, 0>(), vk<V>(-4.0))));
+}
+
+// Gradient of the Laplacian, times 12: 12 sum_i 3 t_i c_ia lap(r + c_i), i.e.
+// 2 (L(+a) - L(-a)) plus the four edges with c_a = +1 minus the four with -1.
+template <class V, class LapV>
+__device__ __forceinline__ void grad_lap12_d3q19(const LapV& lv, V& gx, V& gy, V& gz) {
+    {
+        const V p = vadd(vadd(lv.template at<1, 1, 0>(), lv.template at<1, -1, 0>()),
+                         vadd(lv.template at<1, 0, 1>(), lv.template at<1, 0, -1>()));
+        const V m = vadd(vadd(lv.template at<-1, -1, 0>(), lv.template at<-1, 1, 0>()),
+                         vadd(lv.template at<-1, 0, -1>(), lv.template at<-1, 0, 1>()));
+        gx = vfma(vsub(lv.template at<1, 0, 0>(), lv.template at<-1, 0, 0>()), vk<V>(2.0), vsub(p, m));
+    }
+    {
+        const V p = vadd(vadd(lv.template at<1, 1, 0>(), lv.template at<-1, 1, 0>()),
+                         vadd(lv.template at<0, 1, 1>(), lv.template at<0, 1, -1>()));
+        const V m = vadd(vadd(lv.template at<-1, -1, 0>(), lv.template at<1, -1, 0>()),
+                         vadd(lv.template at<0, -1, -1>(), lv.template at<0, -1, 1>()));
+        gy = vfma(vsub(lv.template at<0, 1, 0>(), lv.template at<0, -1, 0>()), vk<V>(2.0), vsub(p, m));
+    }
+    {
+        const V p = vadd(vadd(lv.template at<1, 0, 1>(), lv.template at<-1, 0, 1>()),
+                         vadd(lv.template at<0, 1, 1>(), lv.template at<0, -1, 1>()));
+        const V m = vadd(vadd(lv.template at<-1, 0, -1>(), lv.template at<1, 0, -1>()),
+                         vadd(lv.template at<0, -1, -1>(), lv.template at<0, 1, -1>()));
+        gz = vfma(vsub(lv.template at<0, 0, 1>(), lv.template at<0, 0, -1>()), vk<V>(2.0), vsub(p, m));
+    }
+}
+
+// f[i] <- post-collision deviations of the site(s) with density deviation
+// drho and momentum j = sum_i c_i f_i; lv views the Laplacian of the density
+// around the site(s).
+template <class V, class LapV>
+__device__ __forceinline__ void collide_d3q19_tau1(V (&f)[19], const V drho, const V jx, const V jy, const V jz,
+                                                   const LapV& lv, const SysPhys<typename VT<V>::S>& P,
+                                                   const NoiseKey& key, const typename SiteIdx<V>::type site,
+                                                   int* status) {
+    using S = typename VT<V>::S;
+    constexpr int W = VT<V>::W;
+    const V rho = vadd(vbc<V>(P.rho_c), drho);
+    bool bad_rho = false;
+#pragma unroll
+    for (int l = 0; l < W; ++l) bad_rho |= !(lane(rho, l) > S(0));
+    if (bad_rho) atomicOr(status, ST_RHO);
+
+    // thermodynamics (Eq. 3 and below Eq. 64), phi = drho / rho_c
+    const V phi = vmul(drho, vbc<V>(P.inv_rho_c));
+    const V phi2 = vmul(phi, phi);
+    const V df0 = vmul(phi, vfma(vbc<V>(P.b), phi2, vbc<V>(P.a)));
+    const V f0 = vmul(phi2, vfma(vbc<V>(S(0.25) * P.b), phi2, vbc<V>(S(0.5) * P.a)));
+    const V rr = vmul(rho, vbc<V>(P.inv_rho_c));
+    const V p0 = vsub(vmul(rr, df0), f0);
+    const V cs2 = vmul(vmul(rr, vbc<V>(P.inv_rho_c)), vfma(vbc<V>(S(3) * P.b), phi2, vbc<V>(P.a)));
+    const V iso = vfma(p0, vk<V>(-3.0), drho);
+
+    // Guo force F = kappa rho grad(lap rho); u = (j + F / 2) / rho
+    V gx, gy, gz;
+    grad_lap12_d3q19<V>(lv, gx, gy, gz);
+    const V kr = vmul(rho, vbc<V>(P.kappa * S(1.0 / 12.0)));
+    const V Fx = vmul(kr, gx), Fy = vmul(kr, gy), Fz = vmul(kr, gz);
+    const V ir = vmap(rho, [](S x) { return fast_rcp(x); });
+    const V ux = vmul(vfma(Fx, vk<V>(0.5), jx), ir);
+    const V uy = vmul(vfma(Fy, vk<V>(0.5), jy), ir);
+    const V uz = vmul(vfma(Fz, vk<V>(0.5), jz), ir);
+    // A_bc with V_b = rho u_b + F_b:  A_bb = u_b V_b,  2 A_bc = u_b V_c + u_c V_b
+    const V Vx = vfma(rho, ux, Fx), Vy = vfma(rho, uy, Fy), Vz = vfma(rho, uz, Fz);
+    const V Axx = vmul(ux, Vx), Ayy = vmul(uy, Vy), Azz = vmul(uz, Vz);
+    const V Axy2 = vfma(ux, Vy, vmul(uy, Vx));
+    const V Ayz2 = vfma(uy, Vz, vmul(uz, Vy));
+    const V Azx2 = vfma(uz, Vx, vmul(ux, Vz));
+    const V tr = vadd(vadd(Axx, Ayy), Azz);
+
+    // h_a = w_a / (36 N_a); N = (1, 1/3 x3, 2/3, 4/3, 4/9, 1/9 x3, 2/3 x3, 2/9 x3, 2, 4/3, 4/9)
+    V h[19];
+    h[0] = vmul(drho, vk<V>(1.0 / 36.0));
+    h[1] = vmul(vadd(jx, Fx), vk<V>(1.0 / 12.0));
+    h[2] = vmul(vadd(jy, Fy), vk<V>(1.0 / 12.0));
+    h[3] = vmul(vadd(jz, Fz), vk<V>(1.0 / 12.0));
+    h[4] = vmul(vsub(tr, iso), vk<V>(1.0 / 24.0));
+    h[5] = vmul(vfma(Axx, vk<V>(3.0), vsub(vk<V>(0.0), tr)), vk<V>(1.0 / 48.0));
+    h[6] = vmul(vsub(Ayy, Azz), vk<V>(1.0 / 16.0));
+    h[7] = vmul(Axy2, vk<V>(1.0 / 8.0));
+    h[8] = vmul(Ayz2, vk<V>(1.0 / 8.0));
+    h[9] = vmul(Azx2, vk<V>(1.0 / 8.0));
+    h[16] = vmul(iso, vk<V>(1.0 / 72.0));
+
+    if (P.kT > S(0)) {
+        // scale sqrt(3 rho kT) (Eq. 68 with Delta V = Delta t = 1) and the
+        // Cholesky factor of the coupled pair (modes c^2 - 1, 3c^4 - 6c^2 + 1):
+        // M = [[2/3 + om, -om], [-om, 2 + om]], om = 1 - 3 c_s^2
+        V sc, k11, k21, k22;
+        bool bad_noise = false;
+#pragma unroll
+        for (int l = 0; l < W; ++l) {
+            const S r = lane(rho, l);
+            set_lane(sc, l, lane_sqrt(vmul(S(3) * P.kT, r > S(0) ? r : S(0))));
+            const S om = vfma(lane(cs2, l), S(-3), S(1));
+            const S mpp = vadd(S(2.0 / 3.0), om);
+            const S det = vfma(mpp, vadd(S(2), om), -vmul(om, om));
+            if (mpp > S(0) && det > S(0)) {
+                const S q = lane_rsqrt(mpp);
+                set_lane(k11, l, vmul(vmul(mpp, q), S(1.0 / 24.0)));
+                set_lane(k21, l, vmul(vmul(-om, q), S(1.0 / 72.0)));
+                set_lane(k22, l, vmul(vmul(lane_sqrt(det), q), S(1.0 / 72.0)));
+            } else {
+                bad_noise = true;
+                set_lane(k11, l, S(0));
+                set_lane(k21, l, S(0));
+                set_lane(k22, l, S(0));
+            }
+        }
+        if (bad_noise) atomicOr(status, ST_NOISE);
+        // the normal of mode a is number a - 4 in draw order; c_a = 1 / (36 sqrt(N_a))
+        const double c5 = 1.0 / (36.0 * 1.1547005383792515), c6 = 1.0 / 24.0, c7 = 1.0 / 12.0;
+        const double c10 = 1.0 / (36.0 * 0.81649658092772603), c13 = 1.0 / (12.0 * 1.4142135623730951);
+        V n[4];
+        draw4(key, site, 0u, sc, n, true);
+        const V n4 = n[0];
+        h[4] = vfma(k11, n4, h[4]);
+        h[5] = vfma(n[1], vk<V>(c5), h[5]);
+        h[6] = vfma(n[2], vk<V>(c6), h[6]);
+        h[7] = vfma(n[3], vk<V>(c7), h[7]);
+        draw4(key, site, 1u, sc, n, true);
+        h[8] = vfma(n[0], vk<V>(c7), h[8]);
+        h[9] = vfma(n[1], vk<V>(c7), h[9]);
+        h[10] = vmul(n[2], vk<V>(c10));
+        h[11] = vmul(n[3], vk<V>(c10));
+        draw4(key, site, 2u, sc, n, true);
+        h[12] = vmul(n[0], vk<V>(c10));
+        h[13] = vmul(n[1], vk<V>(c13));
+        h[14] = vmul(n[2], vk<V>(c13));
+        h[15] = vmul(n[3], vk<V>(c13));
+        draw4(key, site, 3u, sc, n, false);
+        h[16] = vfma(k22, n[0], vfma(k21, n4, h[16]));
+        h[17] = vmul(n[1], vk<V>(c5));
+        h[18] = vmul(n[2], vk<V>(c6));
+    } else {
+#pragma unroll
+        for (int a = 10; a < 16; ++a) h[a] = vk<V>(0.0);
+        h[17] = vk<V>(0.0);
+        h[18] = vk<V>(0.0);
+    }
+
+    // f_i = 36 t_i sum_a T_ai h_a.  Rest: 12 (h0 - h4 + h16).
+    f[0] = vmul(vadd(vsub(h[0], h[4]), h[16]), vk<V>(12.0));
+    // faces (36 t = 2): even parts G + 2 D5, G - D5 +- D6; odd parts h_a - 2 h_{a+9}
+    {
+        const V G = vfma(h[16], vk<V>(-2.0), h[0]);
+        const V D5 = vsub(h[5], h[17]), D6 = vsub(h[6], h[18]);
+        const V Ex = vfma(D5, vk<V>(2.0), G);
+        const V GD = vsub(G, D5);
+        const V Ey = vadd(GD, D6), Ez = vsub(GD, D6);
+        const V Ox = vfma(h[10], vk<V>(-2.0), h[1]);
+        const V Oy = vfma(h[11], vk<V>(-2.0), h[2]);
+        const V Oz = vfma(h[12], vk<V>(-2.0), h[3]);
+        V s;
+        s = vadd(Ex, Ox); f[1] = vadd(s, s);
+        s = vsub(Ex, Ox); f[2] = vadd(s, s);
+        s = vadd(Ey, Oy); f[3] = vadd(s, s);
+        s = vsub(Ey, Oy); f[4] = vadd(s, s);
+        s = vadd(Ez, Oz); f[5] = vadd(s, s);
+        s = vsub(Ez, Oz); f[6] = vadd(s, s);
+    }
+    // edges (36 t = 1): even parts C + P5 +- P6 (xy, xz), C - 2 P5 (yz), plus the
+    // off-diagonal stress mode of the plane; odd parts from X+-, Y+-, Z+-
+    {
+        const V C = vadd(vadd(h[0], h[4]), h[16]);
+        const V P5 = vadd(h[5], h[17]), P6 = vadd(h[6], h[18]);
+        const V CP5 = vadd(C, P5);
+        const V Bxy = vadd(CP5, P6), Bxz = vsub(CP5, P6), Byz = vfma(P5, vk<V>(-2.0), C);
+        const V X = vadd(h[1], h[10]), Y = vadd(h[2], h[11]), Z = vadd(h[3], h[12]);
+        const V Xp = vadd(X, h[13]), Xm = vsub(X, h[13]);
+        const V Yp = vadd(Y, h[14]), Ym = vsub(Y, h[14]);
+        const V Zp = vadd(Z, h[15]), Zm = vsub(Z, h[15]);
+        V E, O;
+        E = vadd(Bxy, h[7]); O = vadd(Xp, Ym); f[7] = vadd(E, O); f[8] = vsub(E, O);
+        E = vsub(Bxy, h[7]); O = vsub(Xp, Ym); f[9] = vadd(E, O); f[10] = vsub(E, O);
+        E = vadd(Bxz, h[9]); O = vadd(Xm, Zp); f[11] = vadd(E, O); f[12] = vsub(E, O);
+        E = vsub(Bxz, h[9]); O = vsub(Xm, Zp); f[13] = vadd(E, O); f[14] = vsub(E, O);
+        E = vadd(Byz, h[8]); O = vadd(Yp, Zm); f[15] = vadd(E, O); f[16] = vsub(E, O);
+        E = vsub(Byz, h[8]); O = vsub(Yp, Zm); f[17] = vadd(E, O); f[18] = vsub(E, O);
+    }
+}
+
+}  // namespace lbf

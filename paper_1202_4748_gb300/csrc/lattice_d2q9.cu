@@ -5,15 +5,16 @@
 namespace lbf {
 
 namespace {
-// (x, y, 1, resident CTAs per SM (0 = default), producer warps (0: none), scheme):
+// (x, y, 1, resident CTAs per SM (0 = default), producer warps (0: none), scheme,
+// sites per thread (1)):
 // scheme 2 = row-marching warp strips of 32 sites x y rows (modified
 // equilibrium only), scheme 0 = CTA tiles of x by y sites with a density halo.
 // Row 0 is the default of the modified equilibrium; the Guo form takes the
 // first tile row.
-constexpr int kTiles[][kVariantCols] = {{32, 32, 1, 6, 0, 2}, {32, 64, 1, 6, 0, 2}, {32, 16, 1, 6, 0, 2},
-                                        {32, 32, 1, 7, 0, 2},
-                                        {32, 8, 1, 0, 0, 0},  {64, 4, 1, 0, 0, 0},  {128, 2, 1, 0, 0, 0},
-                                        {32, 4, 1, 0, 0, 0},  {32, 16, 1, 0, 0, 0}, {64, 8, 1, 0, 0, 0}};
+constexpr int kTiles[][kVariantCols] = {{32, 32, 1, 6, 0, 2, 1}, {32, 64, 1, 6, 0, 2, 1}, {32, 16, 1, 6, 0, 2, 1},
+                                        {32, 32, 1, 7, 0, 2, 1},
+                                        {32, 8, 1, 0, 0, 0, 1},  {64, 4, 1, 0, 0, 0, 1},  {128, 2, 1, 0, 0, 0, 1},
+                                        {32, 4, 1, 0, 0, 0, 1},  {32, 16, 1, 0, 0, 0, 1}, {64, 8, 1, 0, 0, 0, 1}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
 
 template <int CP, class Real, int YC, int MINB>

@@ -8,28 +8,39 @@
 namespace lbf {
 
 namespace {
-// (x, y, z-chunk, resident CTAs per SM, producer warps, staging) of the
-// z-marching kernel: producer warps 0 = every thread stages and collides its
-// own column; > 0 = warp-specialised kernel (used on the fully relaxed FP32
-// path; the other paths run the plain kernel with the same tile), whose
-// producers stage the footprint with plain loads (staging 0) or with bulk
-// copies into shared memory (staging 1; systems that do not allow it run the
-// staging-0 kernel of the same tile).  The first entry is the default.
+// (x, y, z-chunk, resident CTAs per SM, producer warps, staging, sites per
+// consumer thread) of the z-marching kernel: producer warps 0 = every thread
+// stages and collides its own column; > 0 = warp-specialised kernel (used on
+// the fully relaxed FP32 path; the other paths run the plain kernel with the
+// same tile), whose producers stage the footprint with plain loads (staging 0)
+// or with bulk copies into shared memory (staging 1; systems that do not allow
+// it run the staging-0 kernel of the same tile).  Two sites per consumer
+// thread: the paired kernel (x-adjacent site pairs, paired FP32 arithmetic;
+// ensembles with an odd nx run the one-site warp-specialised kernel of the
+// same tile).  The first entry is the default.
 constexpr int kTiles[][kVariantCols] = {
-    {16, 8, 32, 3, 4, 0}, {16, 8, 64, 3, 4, 0}, {16, 8, 16, 3, 4, 0}, {16, 8, 32, 3, 4, 1},
-    {16, 8, 16, 6, 0, 0}, {16, 8, 32, 6, 0, 0}, {16, 16, 16, 4, 0, 0}, {16, 16, 32, 4, 0, 0}};
+    {32, 8, 32, 2, 4, 0, 2}, {16, 16, 32, 2, 4, 0, 2}, {32, 8, 64, 2, 4, 0, 2}, {16, 8, 32, 3, 4, 0, 1},
+    {16, 8, 64, 3, 4, 0, 1}, {16, 8, 16, 3, 4, 0, 1},  {16, 8, 32, 3, 4, 1, 1},  {16, 8, 16, 6, 0, 0, 1},
+    {16, 8, 32, 6, 0, 0, 1}, {16, 16, 16, 4, 0, 0, 1}, {16, 16, 32, 4, 0, 0, 1}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
+constexpr int kPairRing = 8;     // ring planes of the paired kernel
 
 template <int CP, class Real, int I>
 cudaError_t step_variant(const StepLaunch& a, cudaStream_t st) {
     constexpr int PW = kTiles[I][4];
     if constexpr (PW > 0 && std::is_same<Real, float>::value) {
         if (a.bgk_only == 2) {
-            if constexpr (kTiles[I][5] == 1) {
-                if (a.bulk_ok)
-                    return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3], 1>(a, st);
+            if constexpr (kTiles[I][6] == 2) {
+                if (a.pair_ok)
+                    return step_pair<kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3], kPairRing>(a, st);
+                return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, 1, 0>(a, st);
+            } else {
+                if constexpr (kTiles[I][5] == 1) {
+                    if (a.bulk_ok)
+                        return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3], 1>(a, st);
+                }
+                return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3], 0>(a, st);
             }
-            return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3], 0>(a, st);
         }
     }
     return step_z<D3Q19, CP, Real, kTiles[I][0], kTiles[I][1], kTiles[I][2], kTiles[I][3]>(a, st);

@@ -4,6 +4,7 @@
 
 #include "lattice_kernels.cuh"
 #include "lb_launch.h"
+#include "step_kernel_pair.cuh"
 #include "step_kernels.cuh"
 
 namespace lbf {
@@ -102,6 +103,38 @@ cudaError_t step_ws(const StepLaunch& a, cudaStream_t st) {
         }
     }
     step_kernel_ws<L, TX, TY, ZC, PW, MINB, STG><<<a.n_tiles, TX * TY + 32 * PW, dyn, st>>>(A);
+    return cudaGetLastError();
+}
+
+// Paired-site warp-specialised launch (fully relaxed Guo path on D3Q19, FP32,
+// every nx even): TX TY / 2 consumer threads and PW producer warps per CTA,
+// rings of R planes in dynamic shared memory.
+template <int TX, int TY, int ZC, int PW, int MINB, int R>
+cudaError_t step_pair(const StepLaunch& a, cudaStream_t st) {
+    StepArgs<float> A;
+    A.sys = a.sys;
+    A.phys = static_cast<const SysPhys<float>*>(a.phys);
+    A.tiles = a.tiles;
+    A.fin = static_cast<const float*>(a.fin);
+    A.fout = static_cast<float*>(a.fout);
+    A.step_ptr = a.step_ptr;
+    A.k = a.k;
+    A.status = a.status;
+    constexpr size_t dyn = PairLayout<TX, TY, R>::bytes;
+    static int state = 0;                      // once per instantiation: 1 usable, -1 not
+    if (state == 0) {
+        auto k = step_kernel_pair<TX, TY, ZC, PW, MINB, R>;
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, k);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn));
+        // (no carve-out preference: the rings need a fraction of the SM's
+        // shared memory, and the producers' load misses are staged in L1)
+        if (e != cudaSuccess) return e;
+        // the register split must balance against the launch count it assumes
+        state = (!PairRegs<TX, TY, PW, MINB>::split || fa.numRegs == PairRegs<TX, TY, PW, MINB>::launch) ? 1 : -1;
+    }
+    if (state < 0) return step_ws<D3Q19, TX, TY, ZC, PW, 1, 0>(a, st);
+    step_kernel_pair<TX, TY, ZC, PW, MINB, R><<<a.n_tiles, TX * TY / 2 + 32 * PW, dyn, st>>>(A);
     return cudaGetLastError();
 }
 

@@ -350,6 +350,20 @@ __device__ __forceinline__ bool mbar_wait_copies(uint64_t* b, unsigned parity, v
     return false;
 }
 
+// Register reallocation between warpgroups (sm_90a and later): the calling
+// warpgroup's per-thread register count becomes N (a multiple of 8 in
+// [24, 256]).  An increase waits for registers that other warpgroups of the
+// CTA released, so the decreases and increases of one CTA must balance
+// against the registers it was launched with.
+template <int N>
+__device__ __forceinline__ void regs_dec() {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(N));
+}
+template <int N>
+__device__ __forceinline__ void regs_inc() {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(N));
+}
+
 // Named barrier over `count` threads (a multiple of 32) of the CTA.
 __device__ __forceinline__ void named_barrier(int id, int count) {
     asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");

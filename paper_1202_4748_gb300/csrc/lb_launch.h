@@ -25,11 +25,13 @@ struct StepLaunch {
     int tile_id;            // index into the lattice's tile-shape table
     int bgk_only;           // 0: per-mode rates; 1: one rate per system; 2: one rate, equal to 1
     int bulk_ok;            // every system allows bulk-copy staging (nx % 4 == 0, nx >= 8, sides >= 3)
+    int pair_ok;            // every system has nx % 4 == 0 (the paired-site kernel can run)
 };
 
 // Step-kernel variants compiled for each lattice: (x, y, z, resident CTAs per
-// SM, producer warps, staging: 0 plain loads, 1 bulk copies); index = tile_id.
-constexpr int kVariantCols = 6;
+// SM, producer warps, staging: 0 plain loads, 1 bulk copies, sites per
+// consumer thread); index = tile_id.
+constexpr int kVariantCols = 7;
 int tile_shapes_d2q9(int (*out)[kVariantCols], int max);
 int tile_shapes_d3q19(int (*out)[kVariantCols], int max);
 

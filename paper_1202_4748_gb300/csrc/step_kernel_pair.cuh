@@ -1,0 +1,324 @@
+// Warp-specialised z-marching D3Q19 step with two x-adjacent sites per
+// consumer thread (fully relaxed Guo path, FP32, every nx a multiple of 4).
+//
+// Per CTA a TX x TY column of sites walks a chunk of ZC planes.  PW producer
+// warps stage each plane into shared-memory rings of R planes:
+//   * density deviation on the footprint (columns x0 - 4 .. x0 + TX + 3, rows
+//     y0 - 2 .. y0 + TY + 1), from the 19 populations pulled to each footprint
+//     site (pull streaming, f_i(r) = f*_i(r - c_i)).  A producer lane owns four
+//     consecutive footprint sites: each direction is one aligned 128-bit load
+//     of the source row, and the c_x = +-1 directions take the value that
+//     crosses the quad boundary from the neighbouring lane by a warp shuffle
+//     (quads never straddle the periodic seam because nx is a multiple of 4).
+//     Every load of a plane is issued before any is summed, and the loads of
+//     plane z + 1 are issued as soon as plane z is summed;
+//   * momentum j = sum_i c_i f_i of the tile sites;
+//   * Laplacian of the density on the tile + 1, stored twice (at column px and
+//     px + 1) so that every stencil pair a consumer needs is one aligned
+//     64-bit shared load.
+// TX TY / 2 consumer threads collide two sites each from the rings with the
+// paired FP32 instructions (collide_d3q19_tau1<float2>) and store both sites
+// of every population with one 64-bit store.  The consumers read no global
+// memory.  Every per-site sum and product is done in the same order as in the
+// one-site kernels, so both give the same bits.
+//
+// Ring slot of plane z: (z - z0 + 2) mod R.  mbarriers: full[(zl - z0 + 1) mod R]
+// completes when every producer has written Laplacian plane zl (and so every
+// plane the collision of zl - 1 reads); empty[(zc - z0) mod R] completes when
+// every consumer has collided plane zc.  The producers reuse the slots of
+// plane zz - R for plane zz only after the collision of zz - R, which also
+// frees the Laplacian slot written in the same iteration; each side runs at
+// most R - 2 planes ahead, so a phase of one barrier cannot complete twice
+// before its waiter looks and the parity of the use count names the phase.
+// Every wait is bounded (mbar_wait): a timeout flags the CTA and the status
+// word, and every thread keeps the same control flow.
+#pragma once
+
+#include "collide_d3q19.cuh"
+#include "step_kernels.cuh"
+
+namespace lbf {
+
+
+// Shared-memory layout of one ring plane (floats): density footprint, the two
+// Laplacian copies, momentum pairs.  Row pitches: when a half warp of
+// consumers spans two rows (8 pairs per row) they read rows r and r + 2, so a
+// pitch of 8 (mod 16) floats keeps the two rows' 64-bit loads on disjoint banks.
+template <int TX, int TY, int R>
+struct PairLayout {
+    static constexpr int H = 2;
+    static constexpr int NPR = TX / 2;                 // site pairs per tile row
+    static constexpr int SXQ = TX + 8, SY = TY + 2 * H;   // footprint columns x0 - 4 .. x0 + TX + 3
+    static constexpr int NQ = SXQ / 4;                 // producer quads per footprint row
+    static constexpr int RPW = 32 / NQ;                // footprint rows per producer warp
+    static constexpr int PWN = (SY + RPW - 1) / RPW;   // producer warps needed
+    static constexpr int LX = TX + 2, LY = TY + 2;
+    static constexpr int pitch(int w) {
+        return NPR >= 16 ? (w + 3) / 4 * 4 : (w % 16 <= 8 ? w - w % 16 + 8 : w - w % 16 + 24);
+    }
+    static constexpr int SXP = pitch(SXQ);            // density row
+    static constexpr int LXP = pitch(LX + 1);         // Laplacian row (copy E is shifted by one)
+    static constexpr int JRP = NPR >= 16 ? NPR * 6 : pitch(NPR * 6);   // momentum row: 6 floats per pair
+    static constexpr int RHO = SY * SXP;
+    static constexpr int LAP = LY * LXP;
+    static constexpr int JPL = TY * JRP;
+    static constexpr int PLANE = RHO + 2 * LAP + JPL; // floats per ring plane
+    static constexpr int O_LO = RHO, O_LE = RHO + LAP, O_J = RHO + 2 * LAP;
+    static constexpr size_t bytes = size_t(R) * PLANE * sizeof(float);
+    static constexpr int NLP = (LX / 2) * LY;         // Laplacian pairs
+    static_assert(TX % 16 == 0 && TY % 4 == 0, "tile shape");
+    static_assert(SXP % 4 == 0 && PLANE % 4 == 0, "16-byte aligned density quads");
+    static_assert(RHO % 2 == 0 && LAP % 2 == 0 && JPL % 2 == 0, "64-bit aligned regions");
+};
+
+// Density pairs around a Laplacian pair (lanes at footprint columns fx, fx + 1
+// with fx odd; c = footprint row * SXP + fx - 1): the c_x = -1 and +1
+// neighbours are the aligned pairs at fx - 1 and fx + 1, and the c_x = 0
+// neighbour pair straddles them.
+template <int SXP>
+struct PairRhoView {
+    const float* p[3];      // density planes z - 1, z, z + 1
+    int c;
+    template <int CX, int CY, int CZ>
+    __device__ __forceinline__ float2 at() const {
+        if constexpr (CX != 0) {
+            return *reinterpret_cast<const float2*>(p[1 + CZ] + c + SXP * CY + 1 + CX);
+        } else {
+            const float2 m = at<-1, CY, CZ>(), q = at<1, CY, CZ>();
+            return make_float2(m.y, q.x);
+        }
+    }
+};
+
+// Laplacian pairs around a consumer pair (sites at Laplacian columns 2k + 1,
+// 2k + 2; c = (row + 1) * LXP + 2k): c_x = 0 from copy E (the value of column
+// px sits at px + 1, lap_e floats after copy O), c_x = +-1 from copy O.
+template <int LXP>
+struct PairLapView {
+    const float* o[3];      // copy O of the Laplacian planes z - 1, z, z + 1
+    int c;
+    int lap_e;
+    template <int CX, int CY, int CZ>
+    __device__ __forceinline__ float2 at() const {
+        if constexpr (CX == 0)
+            return *reinterpret_cast<const float2*>(o[1 + CZ] + lap_e + c + LXP * CY + 2);
+        else
+            return *reinterpret_cast<const float2*>(o[1 + CZ] + c + LXP * CY + 1 + CX);
+    }
+};
+
+// Register split between the warpgroups: the producers' batched loads want
+// about twice the registers of the collision, so when consumers and producers
+// are whole warpgroups of equal size the consumers give up registers
+// (setmaxnreg.dec) and the producers take them (setmaxnreg.inc).  The launch
+// count is the budget of MINB resident CTAs; the host checks that the compiled
+// kernel has exactly that many registers before it launches the kernel (an
+// increase that the decreases do not cover would wait forever).
+template <int TX, int TY, int PW, int MINB>
+struct PairRegs {
+    static constexpr int NC = TX * TY / 2, NP = 32 * PW, NT = NC + NP;
+    static constexpr int raw = 65536 / (MINB * NT);
+    static constexpr int launch = (raw > 255 ? 255 : raw) & ~7;
+    static constexpr int cons = 80;
+    static constexpr bool split = NC % 128 == 0 && NC == NP && launch > cons;
+    static constexpr int prod = split ? 2 * launch - cons : launch;
+    static_assert(!split || (prod <= 256 && prod % 8 == 0), "register split");
+};
+
+template <int TX, int TY, int ZC, int PW, int MINB, int R>
+__global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(const StepArgs<float> A) {
+    using RG = PairRegs<TX, TY, PW, MINB>;
+    using L = D3Q19;
+    using LY_ = PairLayout<TX, TY, R>;
+    constexpr int H = 2;
+    constexpr int NPR = LY_::NPR;
+    constexpr int LX2 = LY_::LX / 2;
+    constexpr int NC = TX * TY / 2;                   // consumer threads
+    constexpr int NP = 32 * PW;                       // producer threads
+    constexpr int SXP = LY_::SXP, LXP = LY_::LXP, JRP = LY_::JRP, PLANE = LY_::PLANE;
+    static_assert((R & (R - 1)) == 0 && R >= 4, "ring of 2^k >= 4 planes");
+    static_assert(NC % 32 == 0, "whole consumer warps");
+    extern __shared__ __align__(16) float ring[];
+    __shared__ uint64_t full[R], empty[R];
+    __shared__ int abort_flag;
+
+    const int4 tl = A.tiles[blockIdx.x];
+    const SysDev S = A.sys[tl.x];          // register copy: not re-read after the stores
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const int N = S.ns;
+    const int z0 = tl.w, z1 = min(z0 + ZC, nz);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int r = 0; r < R; ++r) {
+            mbar_init(&full[r], NP);
+            mbar_init(&empty[r], NC);
+        }
+        abort_flag = 0;
+    }
+    __syncthreads();
+    auto slot = [&](int z) { return (z - z0 + H) & (R - 1); };
+
+    if (tid >= NC) {
+        // ---------------- producers ----------------
+        if constexpr (RG::split) regs_inc<RG::prod>();
+        const float* __restrict__ fb = A.fin + S.pop_offset;
+        const int ptid = tid - NC;
+        static_assert(PW >= LY_::PWN, "producer warps cover the footprint rows");
+        constexpr int NQ = LY_::NQ, RPW = LY_::RPW;
+        // lane -> quad q of footprint row py: sites x0 - 4 + 4q .. + 3
+        const int rw = (ptid & 31) / NQ, q = (ptid & 31) % NQ;
+        const int py = (ptid >> 5) * RPW + rw;
+        const bool act = rw < RPW && py < LY_::SY;
+        const bool tile = act && py >= H && py < H + TY && q >= 1 && q <= TX / 4;
+        const int xq = wrapm(tl.y - 4 + 4 * q, nx);  // first column of the quad (nx % 4 == 0: contiguous)
+        const int gy = tl.z - H + py;
+        // source rows y - c_y for c_y = -1, 0, +1
+        const float* const rowp[3] = {fb + wrapm(gy + 1, ny) * nx + xq, fb + wrapm(gy, ny) * nx + xq,
+                                      fb + wrapm(gy - 1, ny) * nx + xq};
+        const int dst = py * SXP + 4 * q;
+        const int jdst = LY_::O_J + (py - H) * JRP + (q - 1) * 12;   // pairs 2(q - 1), 2(q - 1) + 1
+        const int pl = nx * ny;
+        const bool sm = S.small != 0;
+        // the loads of plane zz + 1 are issued as soon as plane zz has been
+        // summed, so they are in flight across the barrier and the Laplacian
+        float4 g[19];
+        sfor<0, 19>([&](auto I) { g[decltype(I)::value] = make_float4(0.0f, 0.0f, 0.0f, 0.0f); });
+        auto pull = [&](int zz) {
+            // source planes z - c_z for c_z = -1, 0, +1
+            const int zo[3] = {(sm ? wrapm(zz + 1, nz) : wrap2(zz + 1, nz)) * pl,
+                               (sm ? wrapm(zz, nz) : wrap2(zz, nz)) * pl,
+                               (sm ? wrapm(zz - 1, nz) : wrap2(zz - 1, nz)) * pl};
+            if (act) {
+                sfor<0, 19>([&](auto I) {
+                    constexpr int i = I;
+                    constexpr int cy = L::c(i, 1), cz = L::c(i, 2);
+                    g[i] = *reinterpret_cast<const float4*>(rowp[1 + cy] + (i * N + zo[1 + cz]));
+                });
+            }
+        };
+        pull(z0 - H);
+        for (int zz = z0 - H; zz < z1 + H; ++zz) {
+            const int zw = zz - R;                       // plane whose slots this iteration reuses
+            if (zw >= z0) mbar_wait(&empty[(zw - z0) & (R - 1)], unsigned(((zw - z0) / R) & 1), &abort_flag, A.status);
+            float* const rp = ring + slot(zz) * PLANE;
+            // per direction, the pulled values of the quad's four sites: the
+            // c_x = +1 (-1) direction pulls x - 1 (x + 1), one of which lives in
+            // the neighbouring lane.  Density and momentum are summed in the
+            // order of the one-site kernels (from 0, direction by direction).
+            float2 r01 = make_float2(0.0f, 0.0f), r23 = r01;
+            float2 j01[3] = {r01, r01, r01}, j23[3] = {r01, r01, r01};
+            sfor<0, 19>([&](auto I) {
+                constexpr int i = I;
+                constexpr int cx = L::c(i, 0);
+                float2 a01, a23;
+                if constexpr (cx == 0) {
+                    a01 = make_float2(g[i].x, g[i].y);
+                    a23 = make_float2(g[i].z, g[i].w);
+                } else if constexpr (cx == 1) {
+                    const float pw = __shfl_up_sync(0xffffffffu, g[i].w, 1);
+                    a01 = make_float2(pw, g[i].x);
+                    a23 = make_float2(g[i].y, g[i].z);
+                } else {
+                    const float nw = __shfl_down_sync(0xffffffffu, g[i].x, 1);
+                    a01 = make_float2(g[i].y, g[i].z);
+                    a23 = make_float2(g[i].w, nw);
+                }
+                r01 = vadd(r01, a01);
+                r23 = vadd(r23, a23);
+                if constexpr (i > 0) {
+                    if (tile) {
+                        sfor<0, 3>([&](auto C) {
+                            constexpr int c = C;
+                            if constexpr (L::c(i, c) == 1) {
+                                j01[c] = vadd(j01[c], a01);
+                                j23[c] = vadd(j23[c], a23);
+                            }
+                            if constexpr (L::c(i, c) == -1) {
+                                j01[c] = vsub(j01[c], a01);
+                                j23[c] = vsub(j23[c], a23);
+                            }
+                        });
+                    }
+                }
+            });
+            if (act) *reinterpret_cast<float4*>(rp + dst) = make_float4(r01.x, r01.y, r23.x, r23.y);
+            if (tile) {
+                sfor<0, 3>([&](auto C) {
+                    constexpr int c = C;
+                    *reinterpret_cast<float2*>(rp + jdst + 2 * c) = j01[c];
+                    *reinterpret_cast<float2*>(rp + jdst + 6 + 2 * c) = j23[c];
+                });
+            }
+            if (zz + 1 < z1 + H) pull(zz + 1);
+            named_barrier(1, NP);                        // density plane zz complete (producers)
+            const int zl = zz - 1;                       // Laplacian plane (needs density zl-1 .. zl+1)
+            if (zl >= z0 - 1) {
+                PairRhoView<SXP> rv{{ring + slot(zl - 1) * PLANE, ring + slot(zl) * PLANE, ring + slot(zl + 1) * PLANE},
+                                    0};
+                float* lo = ring + slot(zl) * PLANE + LY_::O_LO;
+                float* le = ring + slot(zl) * PLANE + LY_::O_LE;
+                for (int lq = ptid; lq < LY_::NLP; lq += NP) {
+                    const int lpx = 2 * (lq % LX2), lpy = lq / LX2;
+                    // Laplacian column lpx <-> footprint column lpx + 3, row lpy <-> lpy + 1
+                    rv.c = (lpy + 1) * SXP + lpx + 2;
+                    const float2 lap = lap_d3q19<float2>(rv);
+                    *reinterpret_cast<float2*>(lo + lpy * LXP + lpx) = lap;
+                    le[lpy * LXP + lpx + 1] = lap.x;
+                    le[lpy * LXP + lpx + 2] = lap.y;
+                }
+                mbar_arrive(&full[(zl - z0 + 1) & (R - 1)]);
+            }
+        }
+    } else {
+        // ---------------- consumers ----------------
+        if constexpr (RG::split) regs_dec<RG::cons>();
+        float* __restrict__ fo = A.fout + S.pop_offset;
+        const int64_t step = *A.step_ptr + A.k;
+        const SysPhys<float> P = A.phys[tl.x];
+        const NoiseKey key = noise_key(S, step);
+        const int w = tid >> 5, l = tid & 31;
+        int pk, ty;
+        if constexpr (NPR >= 16) {
+            pk = tid % NPR;
+            ty = tid / NPR;
+        } else {
+            static_assert(NPR == 8, "8 or >= 16 pairs per row");
+            pk = l & 7;
+            const int q = l >> 3;                        // half warp 0: rows 0 and 2; half warp 1: rows 1 and 3
+            ty = 4 * w + (q == 1 ? 2 : (q == 2 ? 1 : q));
+        }
+        const int x = tl.y + 2 * pk, y = tl.z + ty;
+        const bool valid = x < nx && y < ny;
+        const int rho_off = (ty + H) * SXP + 2 * pk + 4;
+        const int j_off = LY_::O_J + ty * JRP + pk * 6;
+        const int lap_c = (ty + 1) * LXP + 2 * pk;
+        for (int zc = z0; zc < z1; ++zc) {
+            const int zl = zc + 1;                       // the last Laplacian plane the collision reads
+            const bool ok = mbar_wait(&full[(zl - z0 + 1) & (R - 1)], unsigned(((zl - z0 + 1) / R) & 1),
+                                      &abort_flag, A.status);
+            if (valid && ok) {
+                const float* cp = ring + slot(zc) * PLANE;
+                const float2 drho = *reinterpret_cast<const float2*>(cp + rho_off);
+                const float2 jx = *reinterpret_cast<const float2*>(cp + j_off);
+                const float2 jy = *reinterpret_cast<const float2*>(cp + j_off + 2);
+                const float2 jz = *reinterpret_cast<const float2*>(cp + j_off + 4);
+                PairLapView<LXP> lv;
+                lv.o[0] = ring + slot(zc - 1) * PLANE + LY_::O_LO;
+                lv.o[1] = cp + LY_::O_LO;
+                lv.o[2] = ring + slot(zc + 1) * PLANE + LY_::O_LO;
+                lv.c = lap_c;
+                lv.lap_e = LY_::LAP;
+                const int site = site_index(x, y, zc, nx, ny);
+                float2 f[19];
+                collide_d3q19_tau1<float2>(f, drho, jx, jy, jz, lv, P, key, make_uint2(site, site + 1), A.status);
+                sfor<0, 19>([&](auto I) {
+                    constexpr int i = I;
+                    *reinterpret_cast<float2*>(fo + (i * N + site)) = f[i];
+                });
+            }
+            mbar_arrive(&empty[(zc - z0) & (R - 1)]);
+        }
+    }
+}
+
+}  // namespace lbf

@@ -16,6 +16,7 @@
 // otherwise each moment relaxes at its own rate in the basis of Eq. 66.
 #pragma once
 
+#include "collide_d3q19.cuh"
 #include "lb_device.cuh"
 
 namespace lbf {
@@ -830,16 +831,8 @@ __global__ void __launch_bounds__(TX* TY, MINB)
             for (int idx = tid; idx < LP; idx += NT) {
                 const int px = idx % LX, py = idx / LX;
                 const int c = (py + H - 1) * SX + (px + H - 1);
-                const Real rc = srho[r0 * SP + c];
-                Real lap = Real(0);
-                sfor<1, Q>([&](auto I) {
-                    constexpr int i = I;
-                    constexpr int cz = L::c(i, 2);
-                    constexpr int off = L::c(i, 0) + SX * L::c(i, 1);
-                    const int pl = cz == 0 ? r0 : (cz > 0 ? rp : rm);
-                    lap += Real(6.0 * L::w(i)) * (srho[pl * SP + c + off] - rc);
-                });
-                slap[lslot * LP + idx] = lap;
+                const RingView<Real, SX> rv{srho, rm * SP, r0 * SP, rp * SP, c};
+                slap[lslot * LP + idx] = lap_d3q19<Real>(rv);
             }
         }
         // collision of plane zc = zz - H - 1
@@ -862,7 +855,8 @@ __global__ void __launch_bounds__(TX* TY, MINB)
             const RingView<Real, LX> lv{slap, ((zc - 1 - z0 + 2 * NL) % NL) * LP, ((zc - z0 + 2 * NL) % NL) * LP,
                                         ((zc + 1 - z0 + 2 * NL) % NL) * LP, (ty + 1) * LX + (tx + 1)};
             if constexpr (PULLFREE)
-                collide_guo_bgk_m<L, Real, true>(f, drho, jc, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
+                collide_d3q19_tau1<Real>(f, drho, jc[0], jc[1], jc[2], lv, A.phys[tl.x], noise_key(S, step),
+                                         uint32_t(site), A.status);
             else if constexpr (BGK_ONLY)
                 collide_guo_bgk<L, Real, TAU1>(f, drho, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
             else
@@ -1136,16 +1130,8 @@ __global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const S
                 for (int idx = ptid; idx < LP; idx += NP) {
                     const int px = idx % LX, py = idx / LX;
                     const int c = (py + H - 1) * SX + (px + H - 1);
-                    const Real rc = srho[r0 + c];
-                    Real lap = Real(0);
-                    sfor<1, Q>([&](auto I) {
-                        constexpr int i = I;
-                        constexpr int cz = L::c(i, 2);
-                        constexpr int off = L::c(i, 0) + SX * L::c(i, 1);
-                        const int pl = cz == 0 ? r0 : (cz > 0 ? rp : rm);
-                        lap += Real(6.0 * L::w(i)) * (srho[pl + c + off] - rc);
-                    });
-                    slap[lslot * LP + idx] = lap;
+                    const RingView<Real, SX> rv{srho, rm, r0, rp, c};
+                    slap[lslot * LP + idx] = lap_d3q19<Real>(rv);
                 }
                 mbar_arrive(&full[(zl - z0 + 1) % R]);
             }
@@ -1171,7 +1157,8 @@ __global__ void __launch_bounds__(TX* TY + 32 * PW, MINB) step_kernel_ws(const S
                                             (ty + 1) * LX + (tx + 1)};
                 const int site = site_index(x, y, zc, nx, ny);
                 Real f[Q];
-                collide_guo_bgk_m<L, Real, true>(f, drho, jc, lv, S, P, uint32_t(site), step, A.status);
+                collide_d3q19_tau1<Real>(f, drho, jc[0], jc[1], jc[2], lv, P, noise_key(S, step), uint32_t(site),
+                                         A.status);
                 sfor<0, Q>([&](auto I) {
                     constexpr int i = I;
                     fo[i * N + site] = f[i];

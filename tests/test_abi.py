@@ -163,14 +163,17 @@ def test_kernel_variant_table():
     for lat in ("D2Q9", "D3Q19"):
         rows = lb.kernel_variants(lat)
         assert len(rows) >= 3 and len(set(rows)) == len(rows)
-        for x, y, z, occ, pw, stg in rows:
-            assert x > 0 and y > 0 and z > 0 and occ >= 0 and pw >= 0 and stg in (0, 1, 2)
+        for x, y, z, occ, pw, stg, spt in rows:
+            assert x > 0 and y > 0 and z > 0 and occ >= 0 and pw >= 0 and stg in (0, 1, 2) and spt in (1, 2)
             assert x % 16 == 0
             assert stg != 1 or pw > 0                    # bulk staging is done by producer warps
+            if spt == 2:                                 # paired sites: the D3Q19 warp-specialised kernel
+                assert lat == "D3Q19" and pw > 0 and stg == 0 and (x * y // 2) % 32 == 0
             if stg == 2:                                 # row strips: one warp per 32-site tile
                 assert lat == "D2Q9" and x == 32 and pw == 0
             else:
-                assert x * y + 32 * pw <= 1024
+                assert x * y // spt + 32 * pw <= 1024
+                assert x * y + 32 * pw <= 1024           # the one-site fallback of the same tile
             if lat == "D2Q9":
                 assert pw == 0                           # producer warps only on the 3-D kernel
         if lat == "D2Q9":
