@@ -367,7 +367,9 @@ lb_status lb_load(lb_ctx* ctx, const char* path);
  * (cp.async.bulk) into shared memory, when every system has nx % 4 == 0,
  * nx >= 8 and all sides >= 3, else the scheme-0 kernel of the same tile runs,
  * 2 = (D2Q9, modified equilibrium only) row-marching strips: one warp per tile
- * of 32 sites x y rows, densities in registers and warp shuffles; sites per
+ * of 32 sites x y rows, densities in registers and warp shuffles, 3 = (paired
+ * D3Q19 kernel) producers stage their 16-byte quads of pulled populations in
+ * shared memory with cp.async instead of holding them in registers; sites per
  * consumer thread: 1, or 2 = (D3Q19, warp-specialised) two x-adjacent sites
  * per consumer thread with paired FP32 arithmetic, when every system has
  * nx % 4 == 0, else the one-site warp-specialised kernel of the same tile runs)

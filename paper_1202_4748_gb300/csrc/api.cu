@@ -8,6 +8,7 @@
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <utility>
@@ -186,12 +187,18 @@ lb_status make_plan(const lb_system_desc* s, int n, const lb_run_opts* o, std::v
     P.n_sites = site_off;
     P.n_levels = lv_count;
 
-    // step tiles, system by system
+    // step tiles, system by system; then the longest z-chunks first, so that
+    // the last wave of CTAs holds the shortest ones (the tiles are independent)
     for (int k = 0; k < n; ++k) {
         const lb_system_desc& d = s[k];
         for (int z = 0; z < d.nz; z += tdim[2])
             for (int y = 0; y < d.ny; y += tdim[1])
                 for (int x = 0; x < d.nx; x += tdim[0]) P.tiles_h.push_back(make_int4(k, x, y, z));
+    }
+    {
+        auto planes = [&](const int4& t) { return std::min(tdim[2], s[t.x].nz - t.w); };
+        std::stable_sort(P.tiles_h.begin(), P.tiles_h.end(),
+                         [&](const int4& a, const int4& b) { return planes(a) > planes(b); });
     }
     P.n_tiles = int(P.tiles_h.size());
 

@@ -19,11 +19,14 @@ namespace {
 // ensembles with an odd nx run the one-site warp-specialised kernel of the
 // same tile).  The first entry is the default.
 constexpr int kTiles[][kVariantCols] = {
-    {32, 8, 32, 2, 4, 0, 2}, {16, 16, 32, 2, 4, 0, 2}, {32, 8, 64, 2, 4, 0, 2}, {16, 8, 32, 3, 4, 0, 1},
-    {16, 8, 64, 3, 4, 0, 1}, {16, 8, 16, 3, 4, 0, 1},  {16, 8, 32, 3, 4, 1, 1},  {16, 8, 16, 6, 0, 0, 1},
-    {16, 8, 32, 6, 0, 0, 1}, {16, 16, 16, 4, 0, 0, 1}, {16, 16, 32, 4, 0, 0, 1}};
+    {32, 8, 32, 3, 4, 3, 2}, {32, 8, 64, 3, 4, 3, 2}, {16, 16, 32, 3, 4, 3, 2}, {32, 8, 32, 2, 4, 0, 2}, {16, 16, 32, 2, 4, 0, 2},
+    {32, 8, 64, 2, 4, 0, 2}, {16, 8, 32, 3, 4, 0, 1},  {16, 8, 64, 3, 4, 0, 1},  {16, 8, 16, 3, 4, 0, 1},
+    {16, 8, 32, 3, 4, 1, 1}, {16, 8, 16, 6, 0, 0, 1},  {16, 8, 32, 6, 0, 0, 1},  {16, 16, 16, 4, 0, 0, 1},
+    {16, 16, 32, 4, 0, 0, 1}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
-constexpr int kPairRing = 8;     // ring planes of the paired kernel
+// ring planes of the paired kernel: 8 with register staging (2 CTAs per SM),
+// 4 with cp.async staging (3 CTAs per SM share the shared memory)
+constexpr int pair_ring(int stg) { return stg == 3 ? 4 : 8; }
 
 template <int CP, class Real, int I>
 cudaError_t step_variant(const StepLaunch& a, cudaStream_t st) {
@@ -32,7 +35,8 @@ cudaError_t step_variant(const StepLaunch& a, cudaStream_t st) {
         if (a.bgk_only == 2) {
             if constexpr (kTiles[I][6] == 2) {
                 if (a.pair_ok)
-                    return step_pair<kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3], kPairRing>(a, st);
+                    return step_pair<kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3],
+                                     pair_ring(kTiles[I][5]), kTiles[I][5]>(a, st);
                 return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, 1, 0>(a, st);
             } else {
                 if constexpr (kTiles[I][5] == 1) {

@@ -107,9 +107,10 @@ cudaError_t step_ws(const StepLaunch& a, cudaStream_t st) {
 }
 
 // Paired-site warp-specialised launch (fully relaxed Guo path on D3Q19, FP32,
-// every nx even): TX TY / 2 consumer threads and PW producer warps per CTA,
-// rings of R planes in dynamic shared memory.
-template <int TX, int TY, int ZC, int PW, int MINB, int R>
+// every nx a multiple of 4): TX TY / 2 consumer threads and PW producer warps
+// per CTA, rings of R planes (and, STG = 3, the producers' staging area) in
+// dynamic shared memory.
+template <int TX, int TY, int ZC, int PW, int MINB, int R, int STG>
 cudaError_t step_pair(const StepLaunch& a, cudaStream_t st) {
     StepArgs<float> A;
     A.sys = a.sys;
@@ -120,10 +121,10 @@ cudaError_t step_pair(const StepLaunch& a, cudaStream_t st) {
     A.step_ptr = a.step_ptr;
     A.k = a.k;
     A.status = a.status;
-    constexpr size_t dyn = PairLayout<TX, TY, R>::bytes;
+    constexpr size_t dyn = PairSmem<TX, TY, PW, R, STG>::bytes;
     static int state = 0;                      // once per instantiation: 1 usable, -1 not
     if (state == 0) {
-        auto k = step_kernel_pair<TX, TY, ZC, PW, MINB, R>;
+        auto k = step_kernel_pair<TX, TY, ZC, PW, MINB, R, STG>;
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, k);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn));
@@ -134,7 +135,7 @@ cudaError_t step_pair(const StepLaunch& a, cudaStream_t st) {
         state = (!PairRegs<TX, TY, PW, MINB>::split || fa.numRegs == PairRegs<TX, TY, PW, MINB>::launch) ? 1 : -1;
     }
     if (state < 0) return step_ws<D3Q19, TX, TY, ZC, PW, 1, 0>(a, st);
-    step_kernel_pair<TX, TY, ZC, PW, MINB, R><<<a.n_tiles, TX * TY / 2 + 32 * PW, dyn, st>>>(A);
+    step_kernel_pair<TX, TY, ZC, PW, MINB, R, STG><<<a.n_tiles, TX * TY / 2 + 32 * PW, dyn, st>>>(A);
     return cudaGetLastError();
 }
 

@@ -125,7 +125,17 @@ struct PairRegs {
     static_assert(!split || (prod <= 256 && prod % 8 == 0), "register split");
 };
 
-template <int TX, int TY, int ZC, int PW, int MINB, int R>
+// STG: 0 = each producer lane loads its quads into registers (in flight one
+// plane ahead); 3 = cp.async copies them into a per-lane staging area in
+// shared memory (no registers held by loads in flight), which leaves room
+// for more resident CTAs.
+template <int TX, int TY, int PW, int R, int STG>
+struct PairSmem {
+    static constexpr size_t stage = STG == 3 ? size_t(19) * 32 * PW * 16 : 0;   // [19][producers] float4
+    static constexpr size_t bytes = PairLayout<TX, TY, R>::bytes + stage;
+};
+
+template <int TX, int TY, int ZC, int PW, int MINB, int R, int STG>
 __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(const StepArgs<float> A) {
     using RG = PairRegs<TX, TY, PW, MINB>;
     using L = D3Q19;
@@ -180,9 +190,13 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
         const int pl = nx * ny;
         const bool sm = S.small != 0;
         // the loads of plane zz + 1 are issued as soon as plane zz has been
-        // summed, so they are in flight across the barrier and the Laplacian
-        float4 g[19];
-        sfor<0, 19>([&](auto I) { g[decltype(I)::value] = make_float4(0.0f, 0.0f, 0.0f, 0.0f); });
+        // summed (and, staged, its density stored: every staged value has been
+        // read back before the copies that overwrite it are issued), so they
+        // are in flight across the barrier and the Laplacian
+        float4 g[STG == 3 ? 1 : 19];
+        float4* const stage = reinterpret_cast<float4*>(ring + R * PLANE) + ptid;   // [19][NP], this lane's column
+        if constexpr (STG != 3)
+            sfor<0, 19>([&](auto I) { g[decltype(I)::value] = make_float4(0.0f, 0.0f, 0.0f, 0.0f); });
         auto pull = [&](int zz) {
             // source planes z - c_z for c_z = -1, 0, +1
             const int zo[3] = {(sm ? wrapm(zz + 1, nz) : wrap2(zz + 1, nz)) * pl,
@@ -192,9 +206,16 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
                 sfor<0, 19>([&](auto I) {
                     constexpr int i = I;
                     constexpr int cy = L::c(i, 1), cz = L::c(i, 2);
-                    g[i] = *reinterpret_cast<const float4*>(rowp[1 + cy] + (i * N + zo[1 + cz]));
+                    const float* src = rowp[1 + cy] + (i * N + zo[1 + cz]);
+                    if constexpr (STG == 3) cp_async16(stage + i * NP, src);
+                    else g[i] = *reinterpret_cast<const float4*>(src);
                 });
             }
+            if constexpr (STG == 3) cp_async_commit();
+        };
+        auto pulled = [&](auto I) -> float4 {
+            if constexpr (STG == 3) return stage[decltype(I)::value * NP];
+            else return g[decltype(I)::value];
         };
         pull(z0 - H);
         for (int zz = z0 - H; zz < z1 + H; ++zz) {
@@ -205,23 +226,25 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
             // c_x = +1 (-1) direction pulls x - 1 (x + 1), one of which lives in
             // the neighbouring lane.  Density and momentum are summed in the
             // order of the one-site kernels (from 0, direction by direction).
+            if constexpr (STG == 3) cp_async_wait_all();     // this lane's copies of plane zz have landed
             float2 r01 = make_float2(0.0f, 0.0f), r23 = r01;
             float2 j01[3] = {r01, r01, r01}, j23[3] = {r01, r01, r01};
             sfor<0, 19>([&](auto I) {
                 constexpr int i = I;
                 constexpr int cx = L::c(i, 0);
+                const float4 v = pulled(I);
                 float2 a01, a23;
                 if constexpr (cx == 0) {
-                    a01 = make_float2(g[i].x, g[i].y);
-                    a23 = make_float2(g[i].z, g[i].w);
+                    a01 = make_float2(v.x, v.y);
+                    a23 = make_float2(v.z, v.w);
                 } else if constexpr (cx == 1) {
-                    const float pw = __shfl_up_sync(0xffffffffu, g[i].w, 1);
-                    a01 = make_float2(pw, g[i].x);
-                    a23 = make_float2(g[i].y, g[i].z);
+                    const float pw = __shfl_up_sync(0xffffffffu, v.w, 1);
+                    a01 = make_float2(pw, v.x);
+                    a23 = make_float2(v.y, v.z);
                 } else {
-                    const float nw = __shfl_down_sync(0xffffffffu, g[i].x, 1);
-                    a01 = make_float2(g[i].y, g[i].z);
-                    a23 = make_float2(g[i].w, nw);
+                    const float nw = __shfl_down_sync(0xffffffffu, v.x, 1);
+                    a01 = make_float2(v.y, v.z);
+                    a23 = make_float2(v.w, nw);
                 }
                 r01 = vadd(r01, a01);
                 r23 = vadd(r23, a23);

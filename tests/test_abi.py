@@ -164,11 +164,12 @@ def test_kernel_variant_table():
         rows = lb.kernel_variants(lat)
         assert len(rows) >= 3 and len(set(rows)) == len(rows)
         for x, y, z, occ, pw, stg, spt in rows:
-            assert x > 0 and y > 0 and z > 0 and occ >= 0 and pw >= 0 and stg in (0, 1, 2) and spt in (1, 2)
+            assert x > 0 and y > 0 and z > 0 and occ >= 0 and pw >= 0 and stg in (0, 1, 2, 3) and spt in (1, 2)
             assert x % 16 == 0
             assert stg != 1 or pw > 0                    # bulk staging is done by producer warps
             if spt == 2:                                 # paired sites: the D3Q19 warp-specialised kernel
-                assert lat == "D3Q19" and pw > 0 and stg == 0 and (x * y // 2) % 32 == 0
+                assert lat == "D3Q19" and pw > 0 and stg in (0, 3) and (x * y // 2) % 32 == 0
+            assert stg != 3 or spt == 2                  # cp.async staging: the paired kernel's producers
             if stg == 2:                                 # row strips: one warp per 32-site tile
                 assert lat == "D2Q9" and x == 32 and pw == 0
             else:
