@@ -417,30 +417,37 @@ lb_status lb_kernel_launches(lb_ctx* ctx, int64_t* count);
 #define LB_NOALLOC_MAX_SITES (1 << 18)
 
 /* Block moments of one density snapshot, for callers that cannot allocate
- * device memory (no counterpart in the paper: the paper defines the moments,
- * Eqs. 46-50, not this calling convention).  Callers such as an application
+ * device memory.  The paper has no counterpart: it defines the moments
+ * (Sec. II B), not this calling convention.  Callers such as an application
  * whose framework already reserves the whole device memory pool, or a stepping
  * loop that cannot afford the device-wide synchronisation of cudaMalloc and
  * cudaFree, can neither allocate nor provide a scratch workspace; this entry
  * point keeps its scratch in a fixed 6 MiB device array inside the library
  * (held on every device that loads it until the process exits) and allocates
- * nothing, on the device or the host.
+ * nothing, on the device or the host.  Its work lists are built on the device
+ * from the lattice shape, so it copies nothing from host memory and does not
+ * wait for the stream.
  *   d_rho      device array of rho, float64 [nz][ny][nx] (caller-owned input)
  *   lattice    LB_D2Q9 (2-D blocks, nz must be 1) or LB_D3Q19 (3-D blocks)
  *   d_out      device array of max_levels x 7 float64 (caller-owned output):
  *              per level n, sum m, sum m^2, sum |m|, sum m^4, sum e, sum e^2 of
  *              this one snapshot, levels ordered as in lb_observables, with
- *              phi = (rho - mean rho)/mean rho (Eq. 1)
+ *              phi = (rho - mean rho)/mean rho
  *   n_levels   receives the number of levels (also when max_levels is too small)
+ *   d_status   nullable device int (caller-owned): receives 0, or the bit
+ *              4 (non-finite) when some moment is NaN or infinite -- the call
+ *              itself returns before the device has computed anything, so a
+ *              non-finite input shows here, not in the return value
  * Asynchronous on `stream`.  All calls share the library's scratch array, which
  * keeps the previous call's contents (this call clears what it accumulates
- * into): calls that overlap on the GPU race, so order them on one stream.  The
- * first call on a device looks up the array's device address there; make it
- * before any stream capture.
+ * into): calls that overlap on the GPU race, so order them on one stream.
+ * Every call looks up the array's address on the current device; the first
+ * call on a device also loads the library's device code there, so make that
+ * first call before any stream capture.
  * Errors: LB_ERR_ARG (pointers, sizes, max_levels), LB_ERR_UNSUPPORTED
  * (nx * ny * nz > LB_NOALLOC_MAX_SITES), LB_ERR_CUDA. */
 lb_status lb_block_moments_noalloc(const double* d_rho, int nx, int ny, int nz, int lattice, double* d_out,
-                                   int max_levels, int* n_levels, void* stream);
+                                   int max_levels, int* n_levels, int* d_status, void* stream);
 
 /* Release host-side resources (graphs, context); the workspace stays the caller's. */
 void lb_destroy(lb_ctx* ctx);

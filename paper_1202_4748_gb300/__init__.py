@@ -109,7 +109,7 @@ _SIG = {
     "lb_selftest_wait_timeout": (ctypes.c_int, [_P, _P]),
     "lb_kernel_variants": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int]),
     "lb_block_moments_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
-                                                ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P]),
+                                                ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P, _P]),
     "lb_destroy": (None, [_P]),
     "lb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lb_version": (ctypes.c_char_p, []),
