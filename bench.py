@@ -42,6 +42,7 @@ WORKLOADS = {
     "large_256_d2q9": dict(ensemble="large_256", lattice="D2Q9", precision="fp32"),
     "fss_160_64": dict(ensemble="fss_160_64", lattice="D3Q19", precision="fp32"),
     "fss_60": dict(ensemble="fss_60", lattice="D3Q19", precision="fp32"),
+    "fss_160_64_fp64": dict(ensemble="fss_160_64", lattice="D3Q19", precision="fp64"),
 }
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
@@ -275,6 +276,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fss_160", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-arm", action="store_true", help="skip the plain FP64 256^3 comparator")
     ap.add_argument("--variant", default="default",
                     help="step-kernel variant: 'default', 'auto' (autotuner, timed on this ensemble) or a row index")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
@@ -397,6 +399,34 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_mlups = sites * LB_STEPS_PER_STEP * k_e2e * world / e2e_s / 1e6
 
+    ens.close()
+    # ---- the plain FP64 single-system path on the 256^3 lattice of the same
+    # model (the comparator of the metric: batched FP32 vs plain FP64), and the
+    # FP32 path on that lattice, timed in this run -----------------------------
+    fp64_plain = None
+    if wl["precision"] == "fp32" and not args.no_fp64_arm:
+        big = synth.ensemble("large_256", wl["lattice"])
+        big_sites = synth.sites(big)
+        arm = {"workload": "large_256: one %s system %dx%dx%d, a = %g, b = 0.1, kappa = 0.01, kT = 1e-4, tau = 1"
+                           % (wl["lattice"], big[0]["nx"], big[0]["ny"], big[0]["nz"], big[0]["a"])}
+        for prec, nsteps in (("fp64", 10), ("fp32", 100)):
+            e = lb.Ensemble(big, precision=prec)
+            e.init(amplitude=0.01)
+            e.step(3)
+            e.sync()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a0.record(stream)
+            e.step(nsteps)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ms_step = a0.elapsed_time(a1) / nsteps
+            e.close()
+            arm[prec] = {"value": round(big_sites / (ms_step * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                         "ms_per_step": round(ms_step, 4), "steps": nsteps}
+        arm["fp32_over_fp64"] = round(arm["fp32"]["value"] / arm["fp64"]["value"], 1)
+        fp64_plain = arm
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = cpu_baseline_subprocess(args.workload, steps=2, warmup=0)
@@ -417,7 +447,6 @@ def main():
         except Exception as exc:          # the single-core figure stands on its own
             cpu["all_cores"] = {"value": None, "error": str(exc)[-200:]}
 
-    ens.close()
     if rank == 0:
         out = {
             "metric": METRIC,
@@ -436,6 +465,7 @@ def main():
                          "frac_of_8TBs": round(achieved / 8000.0, 4)},
             "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": sites * 8,
                     "d2h_bytes_per_step": d2h // k_e2e},
+            "fp64_plain": fp64_plain,
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cpu,

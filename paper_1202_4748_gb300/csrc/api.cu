@@ -61,6 +61,11 @@ struct Plan {
     std::vector<SkSys> sk_h;
     std::vector<int> tw_sides, tw_offs;
     int tw_total = 0, tw_max = 0, sk_max_bins = 0;
+    // line-FFT work list of the structure factor (every side 2^a 3^b), else the direct sums
+    bool sk_fft = false;
+    std::vector<int4> fft_items_h;
+    int n_fft_items = 0, fft_max_elems = 0;
+    size_t fft_items = 0;
 };
 
 int q_of(int lattice) { return lattice == LB_D2Q9 ? 9 : 19; }
@@ -323,6 +328,22 @@ lb_status make_plan(const lb_system_desc* s, int n, const lb_run_opts* o, std::v
             const int side = h.d.nx;
             P.sk_max_bins = std::max(P.sk_max_bins, int(std::ceil(std::sqrt(3.0) * side / 2.0)) + 2);
         }
+        P.sk_fft = true;
+        for (auto& h : sys)
+            if (!sk_fft_side(h.d.nx)) P.sk_fft = false;
+        if (P.sk_fft) {
+            for (int k = 0; k < n; ++k) {
+                const int side = sys[k].d.nx;
+                const int lines = int(sys[k].n / side);
+                const int per = std::max(1, kSkFftMaxElems / side);
+                for (int l = 0; l < lines; l += per) {
+                    const int cnt = std::min(per, lines - l);
+                    P.fft_items_h.push_back(make_int4(k, l, cnt, 0));
+                    P.fft_max_elems = std::max(P.fft_max_elems, cnt * side);
+                }
+            }
+            P.n_fft_items = int(P.fft_items_h.size());
+        }
     }
 
     // byte layout
@@ -360,6 +381,7 @@ lb_status make_plan(const lb_system_desc* s, int n, const lb_run_opts* o, std::v
     const int64_t skn = P.sk ? P.n_sites : 0;
     P.sk_sys = take(sizeof(SkSys) * (P.sk ? n : 0));
     P.sk_tw = take(sizeof(double) * 2 * P.tw_total);
+    P.fft_items = take(sizeof(int4) * P.n_fft_items);
     P.sk_acc = take(sizeof(double) * skn);
     P.sk_b0 = take(sizeof(double) * 2 * skn);
     P.sk_b1 = take(sizeof(double) * 2 * skn);
@@ -548,6 +570,23 @@ cudaError_t sample_jk(lb_ctx* c) {
     }
     for (int a = 0; a < dims; ++a) {
         double* Fa = F + 2 * ns * a;
+        if (P.sk_fft) {
+            const int4* fi = c->at<int4>(P.fft_items);
+            e = launch_sk_fft(sys, sk, fi, P.n_fft_items, 0, j + ns * a, nullptr, nullptr, tw, b0, P.fft_max_elems,
+                              c->stream);
+            if (e != cudaSuccess) return e;
+            e = launch_sk_fft(sys, sk, fi, P.n_fft_items, 1, nullptr, nullptr, b0, tw, d3 ? b1 : Fa,
+                              P.fft_max_elems, c->stream);
+            if (e != cudaSuccess) return e;
+            c->launches += 2;
+            if (d3) {
+                e = launch_sk_fft(sys, sk, fi, P.n_fft_items, 2, nullptr, nullptr, b1, tw, Fa, P.fft_max_elems,
+                                  c->stream);
+                if (e != cudaSuccess) return e;
+                c->launches += 1;
+            }
+            continue;
+        }
         e = launch_sk_x(sys, sk, items, n_items, j + ns * a, nullptr, tw, b0, c->stream);
         if (e != cudaSuccess) return e;
         e = launch_sk_pass(sk, items, n_items, 1, tw, b0, d3 ? b1 : Fa, c->stream);
@@ -579,18 +618,36 @@ cudaError_t sample_sk(lb_ctx* c, int buf, bool have_d) {
     const int4* items = c->at<int4>(P.site_items);
     double* b0 = c->at<double>(P.sk_b0);
     double* b1 = c->at<double>(P.sk_b1);
-    e = launch_sk_x(sys, sk, items, P.n_site_items, c->at<double>(P.d), c->at<double>(P.dbar),
-                    c->at<double>(P.sk_tw), b0, c->stream);
-    if (e != cudaSuccess) return e;
-    e = launch_sk_pass(sk, items, P.n_site_items, 1, c->at<double>(P.sk_tw), b0, b1, c->stream);
-    if (e != cudaSuccess) return e;
+    const double* tw = c->at<double>(P.sk_tw);
     const double* fin = b1;
-    c->launches += 2;
-    if (c->lattice == LB_D3Q19) {
-        e = launch_sk_pass(sk, items, P.n_site_items, 2, c->at<double>(P.sk_tw), b1, b0, c->stream);
+    if (P.sk_fft) {
+        const int4* fi = c->at<int4>(P.fft_items);
+        e = launch_sk_fft(sys, sk, fi, P.n_fft_items, 0, c->at<double>(P.d), c->at<double>(P.dbar), nullptr, tw, b0,
+                          P.fft_max_elems, c->stream);
         if (e != cudaSuccess) return e;
-        fin = b0;
-        c->launches += 1;
+        e = launch_sk_fft(sys, sk, fi, P.n_fft_items, 1, nullptr, nullptr, b0, tw, b1, P.fft_max_elems, c->stream);
+        if (e != cudaSuccess) return e;
+        c->launches += 2;
+        if (c->lattice == LB_D3Q19) {
+            e = launch_sk_fft(sys, sk, fi, P.n_fft_items, 2, nullptr, nullptr, b1, tw, b0, P.fft_max_elems,
+                              c->stream);
+            if (e != cudaSuccess) return e;
+            fin = b0;
+            c->launches += 1;
+        }
+    } else {
+        e = launch_sk_x(sys, sk, items, P.n_site_items, c->at<double>(P.d), c->at<double>(P.dbar), tw, b0,
+                        c->stream);
+        if (e != cudaSuccess) return e;
+        e = launch_sk_pass(sk, items, P.n_site_items, 1, tw, b0, b1, c->stream);
+        if (e != cudaSuccess) return e;
+        c->launches += 2;
+        if (c->lattice == LB_D3Q19) {
+            e = launch_sk_pass(sk, items, P.n_site_items, 2, tw, b1, b0, c->stream);
+            if (e != cudaSuccess) return e;
+            fin = b0;
+            c->launches += 1;
+        }
     }
     c->launches += 1;
     e = launch_sk_accum(sk, items, P.n_site_items, fin, c->at<double>(P.sk_acc), c->stream);
@@ -797,6 +854,9 @@ lb_status lb_create(const lb_system_desc* systems, int n_systems, const lb_run_o
                                    c->stream) == cudaSuccess;
         ok = ok && launch_sk_twiddles(c->at<double>(P.sk_tw), dmeta, dmeta + P.tw_sides.size(),
                                       int(P.tw_sides.size()), P.tw_max, c->stream) == cudaSuccess;
+        if (P.n_fft_items)
+            ok = ok && cudaMemcpyAsync(c->ws + P.fft_items, P.fft_items_h.data(), sizeof(int4) * P.n_fft_items,
+                                       cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
     }
     ok = ok && cudaMemsetAsync(c->ws + P.step, 0, sizeof(int64_t), c->stream) == cudaSuccess;
     ok = ok && reset_accumulators(c) == LB_OK;

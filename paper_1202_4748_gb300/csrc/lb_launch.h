@@ -132,6 +132,14 @@ cudaError_t launch_sk_x(const SysDev* sys, const SkSys* sk, const int4* items, i
                         const double* dbar, const double* tw, double* out, cudaStream_t st);
 cudaError_t launch_sk_pass(const SkSys* sk, const int4* items, int n_items, int axis, const double* tw,
                            const double* in, double* out, cudaStream_t st);
+// Line FFTs along `axis` for systems with equal sides 2^a 3^b (see sk.cu):
+// items (system, first line, line count, 0) with line count * side <= max_elems
+// <= kSkFftMaxElems; in == nullptr: real input from d (and dbar) as launch_sk_x.
+constexpr int kSkFftMaxElems = 2048;
+bool sk_fft_side(int n);   // n = 2^a 3^b and n <= kSkFftMaxElems
+cudaError_t launch_sk_fft(const SysDev* sys, const SkSys* sk, const int4* items, int n_items, int axis,
+                          const double* d, const double* dbar, const double* in, const double* tw, double* out,
+                          int max_elems, cudaStream_t st);
 cudaError_t launch_sk_accum(const SkSys* sk, const int4* items, int n_items, const double* F, double* acc,
                             cudaStream_t st);
 // per-shell sums of the accumulated C(k) of one system (one CTA per shell)

@@ -1,9 +1,11 @@
 // Structure factor C(k) = N^-1 |sum_r phi(r) exp(-i k.r)|^2 (Eq. 80), accumulated
 // in FP64 over samples for every k of every system.  The discrete Fourier
 // transform is taken one axis at a time (x: real -> complex, then y, z) with
-// per-side twiddle tables W_n^j = exp(-2 pi i j / n); each output element sums
-// its line directly in a fixed order.  Shell binning (j(j-1) < |n|^2 <= j(j+1))
-// happens only when the accumulated spectrum is read.
+// per-side twiddle tables W_n^j = exp(-2 pi i j / n).  Sides of the form
+// 2^a 3^b (every workload's) are transformed by a mixed-radix (4, 2, 3)
+// Stockham FFT, one CTA per group of lines in shared memory; other sides sum
+// each output element's line directly in a fixed order.  Shell binning
+// (j(j-1) < |n|^2 <= j(j+1)) happens only when the accumulated spectrum is read.
 #include "lattice_kernels.cuh"
 #include "lb_launch.h"
 
@@ -97,6 +99,115 @@ __global__ void __launch_bounds__(AUX_THREADS)
         const int64_t g = K.site_offset + e;
         const double re = F[2 * g], im = F[2 * g + 1];
         acc[g] += (re * re + im * im) * K.inv_n;
+    }
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+// -i a
+__device__ __forceinline__ double2 cmi(double2 a) { return make_double2(a.y, -a.x); }
+
+// Line FFT along `axis` (0 x, 1 y, 2 z) of systems with equal sides S = 2^a 3^b:
+// item = (system, first line, line count, unused); line l of a system is the
+// l-th line along the axis with the other two coordinates in [z][y][x] order
+// (x lines: l = y + S z; y lines: l = x + S z; z lines: l = x + S y).  REAL_IN:
+// the input is phi = (d - dbar)/(rho_c + dbar) (or d itself without dbar),
+// else the complex field `in`.  Stockham autosort: stage with radix R after
+// sub-transforms of length Ns takes, for butterfly j of a line, the R inputs
+// a[j + r S/R] times W^(k r S/(Ns R)), k = j mod Ns, and writes their R-point
+// DFT to b[(j / Ns) Ns R + k + s Ns]; after the last stage the line is in
+// natural order.  F(k) = sum_x a(x) exp(-2 pi i k x / S), as the direct sums.
+template <bool REAL_IN>
+__global__ void __launch_bounds__(AUX_THREADS)
+    sk_fft_kernel(const SysDev* __restrict__ sysv, const SkSys* __restrict__ skv, const int4* __restrict__ items,
+                  int axis, const double* __restrict__ d, const double* __restrict__ dbar,
+                  const double2* __restrict__ in, const double2* __restrict__ tw, double2* __restrict__ out) {
+    extern __shared__ double2 fft_buf[];
+    const int4 it = items[blockIdx.x];
+    const SkSys K = skv[it.x];
+    const int S = K.nx;
+    const int nl = it.z, line0 = it.y;
+    const int toff = axis == 0 ? K.tw_x : (axis == 1 ? K.tw_y : K.tw_z);
+    double2* A = fft_buf;
+    double2* B = fft_buf + nl * S;
+    auto elem = [&](int line, int t) -> int64_t {
+        if (axis == 0) return int64_t(line) * S + t;
+        const int u = line % S, v = line / S;
+        if (axis == 1) return u + int64_t(S) * (t + int64_t(S) * v);
+        return u + int64_t(S) * (v + int64_t(S) * t);
+    };
+    // element (line l, position t) <-> index: x lines contiguous per line, the
+    // other axes with consecutive lines (consecutive x) in consecutive threads
+    auto lt = [&](int idx, int& l, int& t) {
+        if (axis == 0) {
+            l = idx / S;
+            t = idx - l * S;
+        } else {
+            t = idx / nl;
+            l = idx - t * nl;
+        }
+    };
+    double db = 0.0, inv_rbar = 1.0;
+    if constexpr (REAL_IN) {
+        if (dbar) {
+            db = dbar[it.x];
+            inv_rbar = 1.0 / (sysv[it.x].rho_c + db);
+        }
+    }
+    for (int idx = threadIdx.x; idx < nl * S; idx += AUX_THREADS) {
+        int l, t;
+        lt(idx, l, t);
+        const int64_t g = K.site_offset + elem(line0 + l, t);
+        if constexpr (REAL_IN) A[l * S + t] = make_double2((d[g] - db) * inv_rbar, 0.0);
+        else A[l * S + t] = in[g];
+    }
+    __syncthreads();
+    int Ns = 1;
+    for (int m = S; m > 1;) {
+        const int R = (m % 4 == 0) ? 4 : ((m % 2 == 0) ? 2 : 3);
+        m /= R;
+        const int nb = S / R, tstep = S / (Ns * R);
+        for (int b = threadIdx.x; b < nl * nb; b += AUX_THREADS) {
+            const int l = b / nb, j = b - l * nb, k = j % Ns;
+            const double2* src = A + l * S;
+            double2* dst = B + l * S + (j / Ns) * Ns * R + k;
+            double2 v[4];
+            v[0] = src[j];
+            for (int r = 1; r < R; ++r) v[r] = cmul(src[j + r * nb], tw[toff + k * r * tstep]);
+            if (R == 4) {
+                const double2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+                const double2 s13 = cadd(v[1], v[3]), d13 = cmi(csub(v[1], v[3]));
+                dst[0] = cadd(s02, s13);
+                dst[Ns] = cadd(d02, d13);
+                dst[2 * Ns] = csub(s02, s13);
+                dst[3 * Ns] = csub(d02, d13);
+            } else if (R == 2) {
+                dst[0] = cadd(v[0], v[1]);
+                dst[Ns] = csub(v[0], v[1]);
+            } else {
+                // w = exp(-2 pi i / 3): X1,2 = v0 - (v1 + v2)/2 -+ i (sqrt(3)/2)(v1 - v2)
+                const double2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+                const double2 m0 = make_double2(v[0].x - 0.5 * t1.x, v[0].y - 0.5 * t1.y);
+                const double h = 0.86602540378443864676;
+                const double2 rt = make_double2(h * t2.y, -h * t2.x);      // -i (sqrt(3)/2) t2
+                dst[0] = cadd(v[0], t1);
+                dst[Ns] = cadd(m0, rt);
+                dst[2 * Ns] = csub(m0, rt);
+            }
+        }
+        __syncthreads();
+        double2* tmp = A;
+        A = B;
+        B = tmp;
+        Ns *= R;
+    }
+    for (int idx = threadIdx.x; idx < nl * S; idx += AUX_THREADS) {
+        int l, t;
+        lt(idx, l, t);
+        out[K.site_offset + elem(line0 + l, t)] = A[l * S + t];
     }
 }
 
@@ -241,6 +352,38 @@ cudaError_t launch_sk_pass(const SkSys* sk, const int4* items, int n_items, int 
                            const double* in, double* out, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     sk_pass_kernel<<<n_items, AUX_THREADS, 0, st>>>(sk, items, axis, tw, in, out);
+    return cudaGetLastError();
+}
+
+bool sk_fft_side(int n) {
+    if (n < 1 || n > kSkFftMaxElems) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+cudaError_t launch_sk_fft(const SysDev* sys, const SkSys* sk, const int4* items, int n_items, int axis,
+                          const double* d, const double* dbar, const double* in, const double* tw, double* out,
+                          int max_elems, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    const size_t dyn = size_t(2) * max_elems * sizeof(double2);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(sk_fft_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(2 * kSkFftMaxElems * sizeof(double2)));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(sk_fft_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(2 * kSkFftMaxElems * sizeof(double2)));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const double2* tw2 = reinterpret_cast<const double2*>(tw);
+    double2* out2 = reinterpret_cast<double2*>(out);
+    if (in == nullptr)
+        sk_fft_kernel<true><<<n_items, AUX_THREADS, dyn, st>>>(sys, sk, items, axis, d, dbar, nullptr, tw2, out2);
+    else
+        sk_fft_kernel<false><<<n_items, AUX_THREADS, dyn, st>>>(sys, sk, items, axis, nullptr, nullptr,
+                                                                reinterpret_cast<const double2*>(in), tw2, out2);
     return cudaGetLastError();
 }
 
