@@ -277,6 +277,9 @@ def main():
     ap.add_argument("--workload", default="fss_160", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-arm", action="store_true", help="skip the plain FP64 256^3 comparator")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="N > 1: weak = every rank advances the whole ensemble (its own noise streams); "
+                         "strong = the ensemble is partitioned over the ranks (shard.partition)")
     ap.add_argument("--variant", default="default",
                     help="step-kernel variant: 'default', 'auto' (autotuner, timed on this ensemble) or a row index")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
@@ -308,10 +311,17 @@ def main():
     import paper_1202_4748_gb300 as lb
 
     systems = synth.ensemble(wl["ensemble"], wl["lattice"])
+    all_systems = [dict(s) for s in systems]
     n_sys = len(systems)
-    for s in systems:                       # each rank draws its own noise streams
-        s["system_id"] += rank * n_sys
+    all_sites = synth.sites(systems)
+    if args.scaling == "strong":            # this rank's share of the one ensemble
+        from paper_1202_4748_gb300 import shard
+        systems = [systems[k] for k in shard.partition(systems, world)[rank]]
+    else:
+        for s in systems:                   # each rank draws its own noise streams
+            s["system_id"] += rank * n_sys
     sites = synth.sites(systems)
+    job_sites = all_sites if args.scaling == "strong" else all_sites * world
     q = q_of(wl["lattice"])
     es = 4 if wl["precision"] == "fp32" else 8
 
@@ -362,7 +372,7 @@ def main():
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    updates = sites * LB_STEPS_PER_STEP * args.steps * world
+    updates = job_sites * LB_STEPS_PER_STEP * args.steps
     mlups = updates / (ms_max * 1e-3) / 1e6
 
     # ---- step-kernel duration: 99 plain step launches, no observable pass ----
@@ -397,7 +407,13 @@ def main():
             d2h += 64 * len(levels) + 64
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e_mlups = sites * LB_STEPS_PER_STEP * k_e2e * world / e2e_s / 1e6
+    e2e_s_t = torch.tensor([e2e_s], device="cuda")
+    d2h_t = torch.tensor([float(d2h)], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(e2e_s_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(d2h_t, op=dist.ReduceOp.SUM)        # the job's read-back bytes
+    d2h = int(d2h_t.item())
+    e2e_mlups = job_sites * LB_STEPS_PER_STEP * k_e2e / float(e2e_s_t.item()) / 1e6
 
     ens.close()
     # ---- the plain FP64 single-system path on the 256^3 lattice of the same
@@ -452,9 +468,11 @@ def main():
             "metric": METRIC,
             "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": args.scaling, "vs_baseline": None,
             "dtype": "f32" if wl["precision"] == "fp32" else "f64", "data": "synthetic",
-            "config": dict(describe(wl, systems), step_kernel_variant=list(rows[vindex]),
+            "config": dict(describe(wl, all_systems), step_kernel_variant=list(rows[vindex]),
+                           parallelism=("ensemble partitioned over %d ranks" % world if args.scaling == "strong"
+                                        else "%d replicas of the ensemble" % world),
                            variant_choice=args.variant if args.variant in ("auto", "default") else "row"),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
@@ -463,7 +481,7 @@ def main():
                          "bytes_per_launch": bytes_per_launch,
                          "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
                          "frac_of_8TBs": round(achieved / 8000.0, 4)},
-            "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": sites * 8,
+            "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": job_sites * 8,
                     "d2h_bytes_per_step": d2h // k_e2e},
             "fp64_plain": fp64_plain,
             "gpu_launches": launches,
