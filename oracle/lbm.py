@@ -22,6 +22,14 @@ Two couplings of the non-ideal thermodynamics:
     g1  "p0 - rho lap rho"       -> p0 - kappa rho lap rho   (as in Eq. 64)
     g2  missing "+" before u_gamma d_gamma rho delta_ab restored
     g3  "w^xx kappa (d_x rho d_y rho)" -> w^xx kappa (d_x rho)^2
+  The printed square-gradient weights are one rotation-invariant expression,
+  kappa t_i [(9/2)(c_i . g)^2 + A c_i^2 |g|^2 + B |g|^2], g = grad rho, with
+  (A, B) = (-9/2, 3); in d dimensions the second-moment condition of Eq. 63
+  (these terms must contribute kappa (g_a g_b - |g|^2 delta_ab / 2)) fixes only
+  A (d + 2)/9 + B/3 = -1.  On D3Q19 (the paper prints D2Q9 only) this project
+  keeps A = -9/2, the printed set's -(9/2)|c_i x g|^2 structure, so B = 9/2;
+  the other terms of Eq. 65 carry over with the isotropic weights 3 t_i, and
+  nu is taken from the c_y^2 - c_z^2 shear mode.
 * ``guo`` (variant for the 3-D workloads; D2Q9 and D3Q19): the GL force
   -rho grad mu, mu = f0'(phi)/rho_0 - kappa lap rho, is split by the identity
   rho grad(f0'/rho_0) = grad p0.  The bulk part enters as the isotropic
@@ -172,12 +180,52 @@ def landau(rho, p):
 
 
 def kinematic_viscosity(p):
-    """nu = (tau - 1/2)/3 (below Eq. 63), tau of the c_x^2 - c_y^2 shear mode (index 4)."""
-    return (p.taus()[4] - 0.5) / 3.0
+    """nu = (tau - 1/2)/3 (below Eq. 63), tau of a shear mode: c_x^2 - c_y^2 (index 4)
+    on D2Q9, c_y^2 - c_z^2 (index 6) on D3Q19."""
+    return (p.taus()[4 if p.lattice == "D2Q9" else 6] - 0.5) / 3.0
+
+
+def modeq_gradient_coefficients(d):
+    """(A, B) of the square-gradient terms kappa t_i [(9/2)(c.g)^2 + A c^2 |g|^2 + B |g|^2]:
+    the printed D2Q9 values in 2-D, A = -9/2 and B from the second-moment
+    condition A (d + 2)/9 + B/3 = -1 in 3-D."""
+    if d == 2:
+        return -4.5, 3.0
+    A = -4.5
+    return A, -3.0 * (1.0 + A * (d + 2) / 9.0)
+
+
+def feq_modeq_d3q19(rho, u, grad, lap, p):
+    """Modified equilibrium on D3Q19: Eq. 65's structure with the isotropic
+    weights 3 t_i and the rotation-invariant square-gradient terms (module
+    docstring), shape (19, ...)."""
+    lat = _lat.d3q19()
+    nu = kinematic_viscosity(p)
+    _, _, _, p0, _ = landau(rho, p)
+    iso = p0 - p.kappa * rho * lap
+    udg = u[0] * grad[0] + u[1] * grad[1] + u[2] * grad[2]
+    g2 = grad[0] ** 2 + grad[1] ** 2 + grad[2] ** 2
+    X = [[rho * u[a] * u[b] + nu * (u[a] * grad[b] + u[b] * grad[a] + udg * (a == b)) for b in range(3)]
+         for a in range(3)]
+    A, B = modeq_gradient_coefficients(3)
+    feq = np.empty((19,) + rho.shape)
+    for i in range(1, 19):
+        c = lat.c[i].astype(np.float64)
+        cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2]
+        cg = c[0] * grad[0] + c[1] * grad[1] + c[2] * grad[2]
+        c2 = float(c @ c)
+        xcc = sum((c[a] * c[b] - (a == b) / 3.0) * X[a][b] for a in range(3) for b in range(3))
+        feq[i] = (3.0 * lat.t[i] * (iso + rho * cu + 1.5 * xcc)
+                  + p.kappa * lat.t[i] * (4.5 * cg * cg + A * c2 * g2 + B * g2))
+    feq[0] = rho - feq[1:].sum(axis=0)
+    return feq
 
 
 def feq_modeq(rho, u, grad, lap, p):
-    """Modified equilibrium on D2Q9 (Eq. 65, readings g1-g3), shape (9, ...)."""
+    """Modified equilibrium (Eq. 65, readings g1-g3): the printed D2Q9 form,
+    shape (9, ...); on D3Q19 feq_modeq_d3q19."""
+    if p.lattice == "D3Q19":
+        return feq_modeq_d3q19(rho, u, grad, lap, p)
     lat = _lat.d2q9()
     nu = kinematic_viscosity(p)
     _, _, _, p0, _ = landau(rho, p)
@@ -254,7 +302,7 @@ def noise_matrix(cs2, p):
     gamma = 1.0 - relaxation_rates(p)[nc:]
     g = 1.0 - gamma[:, None] * gamma[None, :]
     K = lat.q - nc
-    if p.coupling == "modeq":
+    if p.coupling == "modeq" and lat.name == "D2Q9":
         cs2 = np.asarray(cs2, dtype=np.float64)
         M = np.zeros(cs2.shape + (K, K))
         # printed rows/columns 4..9 of Eq. 68 -> our modes 3..8 -> local 0..5
@@ -320,8 +368,6 @@ def collide(f, t, p, sites=None):
     lam = relaxation_rates(p)
     lam_b = lam.reshape((-1,) + (1,) * rho.ndim)
     if p.coupling == "modeq":
-        if lat.name != "D2Q9":
-            raise ValueError("the modified equilibrium of Eq. 65 is defined on D2Q9 only")
         u = j / rho
         meq = lat.moments(feq_modeq(rho, u, grad, lap, p))
         src = 0.0

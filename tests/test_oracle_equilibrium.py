@@ -45,6 +45,85 @@ def test_modified_equilibrium_moments_eq62_to_64():
             assert np.allclose(got, want, rtol=0, atol=1e-14)
 
 
+def test_modified_equilibrium_d3q19_moments_eq62_to_64():
+    """The D3Q19 modified equilibrium meets the same conditions in 3-D:
+    sum f = rho, sum f c = rho u, sum f c c = P + rho u u + nu(...) with
+    P = (p0 - kappa rho lap rho - kappa/2 |grad rho|^2) 1 + kappa grad rho grad rho."""
+    taus = tuple([1.0] * 4 + list(np.linspace(0.7, 1.3, 15)))
+    p = lbm.Params(lattice="D3Q19", coupling="modeq", nx=7, ny=6, nz=5, a=-0.03, b=0.7, kappa=0.02, tau=taus)
+    lat = p.lat
+    rho, u = _smooth_fields(p.shape, seed=5)
+    grad = lbm.gradient(rho, lat)
+    lap = lbm.laplacian(rho, lat)
+    feq = lbm.feq_modeq(rho, u, grad, lap, p)
+    c = lat.c.astype(float)
+    assert np.allclose(feq.sum(0), rho, rtol=0, atol=1e-14)
+    assert np.allclose(np.tensordot(c.T, feq, 1), rho * u, atol=1e-15)
+    phi = (rho - p.rho_c) / p.rho_c
+    f0 = p.a / 2 * phi ** 2 + p.b / 4 * phi ** 4
+    p0 = rho / p.rho_c * (p.a * phi + p.b * phi ** 3) - f0
+    g2 = (grad ** 2).sum(0)
+    nu = (taus[6] - 0.5) / 3
+    udg = (u * grad).sum(0)
+    for al in range(3):
+        for be in range(3):
+            P = (p0 - p.kappa * rho * lap - p.kappa / 2 * g2) * (al == be) + p.kappa * grad[al] * grad[be]
+            hol = nu * (u[al] * grad[be] + u[be] * grad[al] + udg * (al == be))
+            got = np.tensordot(c[:, al] * c[:, be], feq, 1)
+            assert np.allclose(got, P + rho * u[al] * u[be] + hol, rtol=0, atol=1e-14)
+
+
+def _gradient_weights(lat, A, B):
+    """Per velocity, the coefficients of g_x^2, g_y^2, g_x g_y (and on 3-D g_z^2)
+    in kappa^-1 times the square-gradient terms t_i [(9/2)(c.g)^2 + A c^2 |g|^2 + B |g|^2]."""
+    c = lat.c.astype(float)
+    c2 = (c ** 2).sum(1)
+    wxx = lat.t * (4.5 * c[:, 0] ** 2 + A * c2 + B)
+    wyy = lat.t * (4.5 * c[:, 1] ** 2 + A * c2 + B)
+    wzz = lat.t * (4.5 * c[:, 2] ** 2 + A * c2 + B)
+    wxy = lat.t * 9.0 * c[:, 0] * c[:, 1]
+    wxx[0] = wyy[0] = wzz[0] = wxy[0] = 0.0          # the rest population restores the mass
+    return wxx, wyy, wzz, wxy
+
+
+def test_printed_gradient_weights_are_the_rotation_invariant_form():
+    """The printed w^xx, w^yy, w^xy of Eq. 65 (D2Q9) are exactly
+    t_i [(9/2)(c.g)^2 - (9/2) c^2 |g|^2 + 3 |g|^2] coefficient by coefficient:
+    the form the D3Q19 set generalises."""
+    A, B = lbm.modeq_gradient_coefficients(2)
+    assert (A, B) == (-4.5, 3.0)
+    wxx, wyy, _, wxy = _gradient_weights(lattice.d2q9(), A, B)
+    assert np.allclose(wxx, lattice.POOLEY_WXX, rtol=0, atol=1e-16)
+    assert np.allclose(wyy, lattice.POOLEY_WYY, rtol=0, atol=1e-16)
+    assert np.allclose(wxy, lattice.POOLEY_WXY, rtol=0, atol=1e-16)
+
+
+def test_d3q19_gradient_weights_and_the_freedom_left():
+    """D3Q19: A = -9/2, B = 9/2.  Coefficient of g_x^2 per velocity class:
+    1/4 on (+-1,0,0), 0 on the other axes and on the edges with c_x != 0, -1/8
+    on the yz edges; of g_x g_y: +-1/4 on the xy edges (as on D2Q9).  Second
+    moments: +1/2 (xx), -1/2 (yy, zz), 0 off the diagonal -- and every (A, B)
+    on the line A (d + 2)/9 + B/3 = -1 meets them (the freedom Eq. 63 leaves)."""
+    lat = lattice.d3q19()
+    A, B = lbm.modeq_gradient_coefficients(3)
+    assert (A, B) == (-4.5, 4.5)
+    wxx, wyy, wzz, wxy = _gradient_weights(lat, A, B)
+    c = lat.c.astype(float)
+    by_class = {}
+    for i in range(1, 19):
+        key = (abs(c[i, 0]), abs(c[i, 1]) + abs(c[i, 2]))
+        by_class.setdefault(key, set()).add(round(wxx[i], 15))
+    assert by_class == {(1, 0): {0.25}, (0, 1): {0.0}, (1, 1): {0.0}, (0, 2): {-0.125}}
+    assert set(np.round(wxy[7:11], 15)) == {0.25, -0.25}
+    for Aa in (A, -2.0, 0.0):
+        Bb = -3.0 * (1.0 + Aa * 5.0 / 9.0)
+        wxx, _, _, wxy = _gradient_weights(lat, Aa, Bb)
+        assert np.isclose((wxx * c[:, 0] ** 2).sum(), 0.5)
+        assert np.isclose((wxx * c[:, 1] ** 2).sum(), -0.5) and np.isclose((wxx * c[:, 2] ** 2).sum(), -0.5)
+        assert np.isclose((wxx * c[:, 0] * c[:, 1]).sum(), 0.0)
+        assert np.isclose((wxy * c[:, 0] * c[:, 1]).sum(), 1.0) and np.isclose((wxy * c[:, 0] ** 2).sum(), 0.0)
+
+
 def test_gradient_weight_sums_by_hand():
     """The three readings of Eq. 65 rest on these second moments of w^xx, w^yy, w^xy."""
     c = lattice.d2q9().c.astype(float)

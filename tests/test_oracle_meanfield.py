@@ -13,7 +13,8 @@ from scipy.optimize import curve_fit
 from oracle import lbm
 
 
-@pytest.mark.parametrize("lattice,coupling", [("D2Q9", "modeq"), ("D2Q9", "guo"), ("D3Q19", "guo")])
+@pytest.mark.parametrize("lattice,coupling", [("D2Q9", "modeq"), ("D2Q9", "guo"), ("D3Q19", "guo"),
+                                              ("D3Q19", "modeq")])
 def test_plateaus_and_interface_width(lattice, coupling):
     nx = 128
     p = lbm.Params(lattice=lattice, coupling=coupling, nx=nx, ny=1, nz=1,
