@@ -7,9 +7,11 @@
  * (arXiv:1202.4748), Sec. III A:
  *   - evolution equation Eq. 61, moments Eq. 62,
  *   - non-ideal thermodynamics through the pressure tensor Eqs. 63-64: the
- *     paper's D2Q9 modified equilibrium Eq. 65 (LB_MODEQ), or a D2Q9/D3Q19 form
- *     with the Landau pressure in the equilibrium and the square-gradient part
- *     of the chemical potential as a Guo body force (LB_GUO),
+ *     modified equilibrium Eq. 65 (LB_MODEQ; the paper's D2Q9 weights, and on
+ *     D3Q19 the same structure with the rotation-invariant form of its
+ *     square-gradient weights), or a D2Q9/D3Q19 form with the Landau pressure
+ *     in the equilibrium and the square-gradient part of the chemical
+ *     potential as a Guo body force (LB_GUO),
  *   - collision in the moment basis of Eq. 66 with per-mode relaxation rates,
  *   - local Gaussian noise with the covariance of Eq. 68 (Cholesky-factored),
  *     drawn from a counter-based Philox4x32-10 stream keyed by
@@ -73,8 +75,9 @@ enum { LB_INIT_UNIFORM_NOISE = 0, LB_INIT_FROM_RHO = 1, LB_INIT_TANH_STRIPE = 2 
  * f0 = a/2 phi^2 + b/4 phi^4, phi = (rho - rho_c)/rho_c (Eqs. 1-3; a, b are
  * the paper's r, u).  tau[a] is the relaxation time of moment a (entries of
  * conserved moments are ignored; every other must exceed 1/2).  The kinematic
- * viscosity of the Holdych term of Eq. 63 uses tau[4].  Sizes are >= 1;
- * nz must be 1 for D2Q9.  LB_MODEQ requires D2Q9.  system_id < 2^24. */
+ * viscosity of the Holdych term of Eq. 63 uses tau[4] (D2Q9, the c_x^2 - c_y^2
+ * mode) or tau[6] (D3Q19, the c_y^2 - c_z^2 mode).  Sizes are >= 1; nz must
+ * be 1 for D2Q9.  system_id < 2^24. */
 typedef struct {
     int32_t lattice;
     int32_t coupling;

@@ -82,7 +82,6 @@ lb_status validate(const lb_system_desc* s, int n, const lb_run_opts* o) {
         if (d.lattice != s[0].lattice || d.coupling != s[0].coupling) return LB_ERR_ARG;
         if (d.lattice != LB_D2Q9 && d.lattice != LB_D3Q19) return LB_ERR_ARG;
         if (d.coupling != LB_MODEQ && d.coupling != LB_GUO) return LB_ERR_ARG;
-        if (d.coupling == LB_MODEQ && d.lattice != LB_D2Q9) return LB_ERR_ARG;
         if (d.nx < 1 || d.ny < 1 || d.nz < 1) return LB_ERR_ARG;
         if (d.lattice == LB_D2Q9 && d.nz != 1) return LB_ERR_ARG;
         if (int64_t(d.nx) * d.ny * d.nz * q_of(d.lattice) >= (int64_t(1) << 31)) return LB_ERR_ARG;
@@ -438,7 +437,9 @@ SysDev to_dev(const SysHost& h) {
     s.kappa = d.kappa;
     s.kT = d.kT;
     s.inv_rho_c = 1.0 / d.rho_c;
-    s.nu = d.lattice == LB_D2Q9 ? (d.tau[4] - 0.5) / 3.0 : 0.0;
+    // kinematic viscosity of the Holdych term: tau of the c_x^2 - c_y^2 (D2Q9)
+    // or c_y^2 - c_z^2 (D3Q19) shear mode
+    s.nu = (d.tau[d.lattice == LB_D2Q9 ? 4 : 6] - 0.5) / 3.0;
     double gamma[LB_MAX_Q];
     for (int a = 0; a < q; ++a) {
         s.lam[a] = a < nc ? 0.0 : 1.0 / d.tau[a];

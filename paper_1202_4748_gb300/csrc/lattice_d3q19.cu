@@ -1,5 +1,6 @@
-// D3Q19 instantiations (3-D variant): Guo-forced form with the Landau
-// pressure in the equilibrium, FP64 and FP32-deviation storage.
+// D3Q19 instantiations (3-D variant): the Guo-forced form with the Landau
+// pressure in the equilibrium and the modified equilibrium carried to three
+// dimensions, FP64 and FP32-deviation storage.
 #include <type_traits>
 #include <utility>
 
@@ -31,23 +32,28 @@ constexpr int pair_ring(int stg) { return stg == 3 ? 4 : 8; }
 template <int CP, class Real, int I>
 cudaError_t step_variant(const StepLaunch& a, cudaStream_t st) {
     constexpr int PW = kTiles[I][4];
-    if constexpr (PW > 0 && std::is_same<Real, float>::value) {
-        if (a.bgk_only == 2) {
-            if constexpr (kTiles[I][6] == 2) {
-                if (a.pair_ok)
-                    return step_pair<kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3],
-                                     pair_ring(kTiles[I][5]), kTiles[I][5]>(a, st);
-                return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, 1, 0>(a, st);
-            } else {
-                if constexpr (kTiles[I][5] == 1) {
-                    if (a.bulk_ok)
-                        return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3], 1>(a, st);
+    if constexpr (CP == MODEQ) {      // the modified equilibrium: the radius-1 z-marching kernel of the same tile
+        return step_zm<D3Q19, Real, kTiles[I][0], kTiles[I][1], kTiles[I][2], kTiles[I][3]>(a, st);
+    } else {
+        if constexpr (PW > 0 && std::is_same<Real, float>::value) {
+            if (a.bgk_only == 2) {
+                if constexpr (kTiles[I][6] == 2) {
+                    if (a.pair_ok)
+                        return step_pair<kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3],
+                                         pair_ring(kTiles[I][5]), kTiles[I][5]>(a, st);
+                    return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, 1, 0>(a, st);
+                } else {
+                    if constexpr (kTiles[I][5] == 1) {
+                        if (a.bulk_ok)
+                            return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3], 1>(a,
+                                                                                                              st);
+                    }
+                    return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3], 0>(a, st);
                 }
-                return step_ws<D3Q19, kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3], 0>(a, st);
             }
         }
+        return step_z<D3Q19, CP, Real, kTiles[I][0], kTiles[I][1], kTiles[I][2], kTiles[I][3]>(a, st);
     }
-    return step_z<D3Q19, CP, Real, kTiles[I][0], kTiles[I][1], kTiles[I][2], kTiles[I][3]>(a, st);
 }
 
 template <int CP, class Real, int... I>
@@ -72,7 +78,7 @@ int tile_shapes_d3q19(int (*out)[kVariantCols], int max) {
 
 cudaError_t launch_step_d3q19(int coupling, int fp32, const StepLaunch& a, cudaStream_t st) {
     if (a.n_tiles == 0) return cudaSuccess;
-    if (coupling != GUO) return cudaErrorInvalidValue;   // Eq. 65 is a D2Q9 equilibrium
+    if (coupling == MODEQ) return fp32 ? step_tile<MODEQ, float>(a, st) : step_tile<MODEQ, double>(a, st);
     return fp32 ? step_tile<GUO, float>(a, st) : step_tile<GUO, double>(a, st);
 }
 

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(AUX_THREADS)
         const double p0 = rho * S.inv_rho_c * df0 - f0;
         double feq[L::Q];
         double s = 0.0;
-        if constexpr (CP == MODEQ) {
+        if constexpr (CP == MODEQ && L::D == 2) {
             double gx = 0.0, gy = 0.0, lap = 0.0;
 #pragma unroll
             for (int i = 1; i < L::Q; ++i) {
@@ -90,6 +90,25 @@ __global__ void __launch_bounds__(AUX_THREADS)
             for (int i = 1; i < L::Q; ++i) {
                 feq[i] = pooley_w(i) * iso +
                          S.kappa * (pooley_wxx(i) * gx * gx + pooley_wyy(i) * gy * gy + pooley_wxy(i) * gx * gy);
+                s += feq[i];
+            }
+        } else if constexpr (CP == MODEQ) {
+            // D3Q19 modified equilibrium at rest: 3 t_i iso + kappa t_i [(9/2)(c.g)^2 - (9/2) c^2 |g|^2 + (9/2)|g|^2]
+            double g[3] = {0.0, 0.0, 0.0}, lap = 0.0;
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i) {
+                const double rn = nb(i);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) g[a] += 3.0 * L::w(i) * L::c(i, a) * rn;
+                lap += 6.0 * L::w(i) * (rn - drho);
+            }
+            const double iso = p0 - S.kappa * rho * lap;
+            const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i) {
+                const double cg = L::c(i, 0) * g[0] + L::c(i, 1) * g[1] + L::c(i, 2) * g[2];
+                const double c2 = double(L::c(i, 0) * L::c(i, 0) + L::c(i, 1) * L::c(i, 1) + L::c(i, 2) * L::c(i, 2));
+                feq[i] = 3.0 * L::w(i) * iso + S.kappa * L::w(i) * (4.5 * cg * cg - 4.5 * c2 * g2 + 4.5 * g2);
                 s += feq[i];
             }
         } else {

@@ -4,6 +4,7 @@
 
 #include "lattice_kernels.cuh"
 #include "lb_launch.h"
+#include "step_kernel_modeq3.cuh"
 #include "step_kernel_pair.cuh"
 #include "step_kernels.cuh"
 
@@ -72,6 +73,30 @@ cudaError_t step_z(const StepLaunch& a, cudaStream_t st) {
     if (a.bgk_only == 2) return step_z_mode<L, CP, Real, TX, TY, ZC, MB, 2>(a, st);
     if (a.bgk_only == 1) return step_z_mode<L, CP, Real, TX, TY, ZC, MB, 1>(a, st);
     return step_z_mode<L, CP, Real, TX, TY, ZC, MB, 0>(a, st);
+}
+
+// z-marching launch of the D3Q19 modified equilibrium (density footprint of
+// radius 1); the FP64 instances use the natural register count.
+template <class L, class Real, int TX, int TY, int ZC, int MINB, int MODE>
+cudaError_t step_zm_mode(const StepLaunch& a, cudaStream_t st) {
+    StepArgs<Real> A;
+    A.sys = a.sys;
+    A.phys = static_cast<const SysPhys<Real>*>(a.phys);
+    A.tiles = a.tiles;
+    A.fin = static_cast<const Real*>(a.fin);
+    A.fout = static_cast<Real*>(a.fout);
+    A.step_ptr = a.step_ptr;
+    A.k = a.k;
+    A.status = a.status;
+    step_kernel_zm<L, Real, TX, TY, ZC, MINB, MODE><<<a.n_tiles, TX * TY, 0, st>>>(A);
+    return cudaGetLastError();
+}
+template <class L, class Real, int TX, int TY, int ZC, int MINB>
+cudaError_t step_zm(const StepLaunch& a, cudaStream_t st) {
+    constexpr int MB = sizeof(Real) == 4 ? (MINB < 2 ? 2 : MINB) : 1;
+    if (a.bgk_only == 2) return step_zm_mode<L, Real, TX, TY, ZC, MB, 2>(a, st);
+    if (a.bgk_only == 1) return step_zm_mode<L, Real, TX, TY, ZC, MB, 1>(a, st);
+    return step_zm_mode<L, Real, TX, TY, ZC, MB, 0>(a, st);
 }
 
 // Warp-specialised launch (fully relaxed Guo path, FP32): TX x TY consumer
@@ -151,10 +176,7 @@ cudaError_t init_feq_any(int coupling, const SysDev* sys, const int4* items, int
                          const double* dbar, void* fbuf, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     if (coupling == MODEQ) {
-        if constexpr (L::D == 2)
-            init_feq_kernel<L, MODEQ, Real><<<n_items, AUX_THREADS, 0, st>>>(sys, items, d, dbar, static_cast<Real*>(fbuf));
-        else
-            return cudaErrorInvalidValue;
+        init_feq_kernel<L, MODEQ, Real><<<n_items, AUX_THREADS, 0, st>>>(sys, items, d, dbar, static_cast<Real*>(fbuf));
     } else {
         init_feq_kernel<L, GUO, Real><<<n_items, AUX_THREADS, 0, st>>>(sys, items, d, dbar, static_cast<Real*>(fbuf));
     }

@@ -62,7 +62,7 @@ def _one(**kw):
 
 @pytest.mark.parametrize("bad", [
     dict(nx=0), dict(nz=2), dict(kT=-1.0), dict(rho_c=0.0), dict(kappa=-1e-3),
-    dict(tau=[1.0] * 3 + [0.5] + [1.0] * 5), dict(system_id=1 << 24), dict(lattice="D3Q19", coupling="modeq"),
+    dict(tau=[1.0] * 3 + [0.5] + [1.0] * 5), dict(system_id=1 << 24), dict(coupling=7),
     dict(a=float("nan")),
 ])
 def test_invalid_descriptors_rejected(bad):

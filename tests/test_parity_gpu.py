@@ -46,6 +46,7 @@ CASES = [
     ("D2Q9", "modeq", (70, 37, 1), MIXED_TAU_9),
     ("D2Q9", "guo", (45, 29, 1), MIXED_TAU_9),
     ("D3Q19", "guo", (20, 13, 11), MIXED_TAU_19),
+    ("D3Q19", "modeq", (20, 13, 11), MIXED_TAU_19),
 ]
 
 
@@ -129,7 +130,8 @@ def test_degenerate_tiny_lattices(lb, lattice, coupling, shape):
     assert rel_err(got, lbm.run(f0, 0, 5, p)) < TOL64
 
 
-@pytest.mark.parametrize("lattice,coupling", [("D2Q9", "modeq"), ("D2Q9", "guo"), ("D3Q19", "guo")])
+@pytest.mark.parametrize("lattice,coupling", [("D2Q9", "modeq"), ("D2Q9", "guo"), ("D3Q19", "guo"),
+                                              ("D3Q19", "modeq")])
 def test_init_matches_oracle(lb, lattice, coupling):
     s = synth.system(lattice, coupling, n=24 if lattice == "D2Q9" else 10, seed=9, system_id=5)
     s["ny"] = s["nx"] - 3 if lattice == "D2Q9" else s["ny"]
@@ -387,7 +389,7 @@ def test_structure_factor_matches_oracle(lb, lattice, n, obs_every):
 
 
 @pytest.mark.parametrize("lattice,coupling,shape", [("D2Q9", "modeq", (33, 18, 1)), ("D2Q9", "guo", (21, 30, 1)),
-                                                     ("D3Q19", "guo", (18, 11, 35))])
+                                                     ("D3Q19", "guo", (18, 11, 35)), ("D3Q19", "modeq", (18, 11, 35))])
 @pytest.mark.parametrize("tau", [0.8, 1.0])
 def test_single_rate_collision_paths(lb, lattice, coupling, shape, tau):
     """One relaxation rate for every non-conserved mode (the paper's BGK form):
@@ -462,13 +464,15 @@ def test_bounded_wait_reports_timeout_and_context_survives(lb):
     e.close()
 
 
-def test_fp32_fully_relaxed_path_on_odd_and_tiny_shapes(lb):
-    """The FP32 tau = 1 path (the warp-specialised default kernel) on systems with
-    sides shorter than the stencil, ragged tiles and several z-chunks, batched in
-    one launch: each step matches the oracle stepped from the GPU's own FP32
-    state, and every compiled step-kernel variant gives the same bits."""
+@pytest.mark.parametrize("coupling", ["guo", "modeq"])
+def test_fp32_fully_relaxed_path_on_odd_and_tiny_shapes(lb, coupling):
+    """The FP32 tau = 1 path (the warp-specialised default kernel; the radius-1
+    z-marching kernel for the modified equilibrium) on systems with sides
+    shorter than the stencil, ragged tiles and several z-chunks, batched in one
+    launch: each step matches the oracle stepped from the GPU's own FP32 state,
+    and every compiled step-kernel variant gives the same bits."""
     shapes = [(20, 13, 11), (9, 8, 7), (4, 4, 4), (2, 2, 2), (1, 3, 2), (17, 5, 70)]
-    systems = [_sys("D3Q19", "guo", *sh, a=-0.002 + 0.001 * k, b=0.1, kappa=0.01, kT=1e-4, tau=[1.0] * 19,
+    systems = [_sys("D3Q19", coupling, *sh, a=-0.002 + 0.001 * k, b=0.1, kappa=0.01, kT=1e-4, tau=[1.0] * 19,
                     seed=20 + k, system_id=k) for k, sh in enumerate(shapes)]
     ps = [params_of(s) for s in systems]
     f0s = [oracle_state(p, steps=2) for p in ps]

@@ -54,6 +54,7 @@ def _oracle_decay(lattice, coupling, nx, tau, a=0.1, steps=1200, every=4, ny=2, 
     ("D2Q9", "guo", 64, [1] * 3 + [0.8] * 6, 1200, (2, 1)),
     ("D2Q9", "modeq", 64, [1] * 3 + [1.2] + [0.8] * 5, 1200, (2, 1)),
     ("D3Q19", "guo", 32, [1] * 4 + [0.8] * 15, 800, (2, 2)),
+    ("D3Q19", "modeq", 32, [1] * 4 + [0.8] * 15, 800, (2, 2)),
 ])
 def test_sound_wave_decays_at_the_predicted_rate(lattice, coupling, nx, tau, steps, shape):
     fit = _oracle_decay(lattice, coupling, nx, tau, steps=steps, ny=shape[0], nz=shape[1])
