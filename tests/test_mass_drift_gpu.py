@@ -1,5 +1,5 @@
-"""Mass bookkeeping of the FP32-deviation path (the benchmark spec keeps FP64 on
-the GPU for the conserved-mass bookkeeping).
+"""Mass bookkeeping of the FP32-deviation path (populations in FP32, the
+conserved mass summed in FP64 on the GPU).
 
 The collision conserves mass exactly in exact arithmetic (Eq. 62: the density
 moment is not relaxed and the noise has no density component), so only the
