@@ -48,7 +48,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
 KERNEL_SOURCES = ["paper_1202_4748_gb300/csrc/step_kernels.cuh", "paper_1202_4748_gb300/csrc/lb_device.cuh",
                   "paper_1202_4748_gb300/csrc/step_kernel_pair.cuh", "paper_1202_4748_gb300/csrc/collide_d3q19.cuh",
-                  "paper_1202_4748_gb300/csrc/vec2.cuh"]
+                  "paper_1202_4748_gb300/csrc/vec2.cuh", "paper_1202_4748_gb300/csrc/collide_d2q9.cuh",
+                  "paper_1202_4748_gb300/csrc/step_kernel_strip_pair.cuh"]
 
 
 def kernel_source_hash():

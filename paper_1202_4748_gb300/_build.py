@@ -14,7 +14,8 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbfluct.so")
 SOURCES = ["api.cu", "obs.cu", "sk.cu", "noalloc.cu", "lattice_d2q9.cu", "lattice_d3q19.cu", "pt.cu"]
 HEADERS = ["lb_device.cuh", "lb_launch.h", "step_kernels.cuh", "lattice_kernels.cuh", "lattice_tu.cuh", "vec2.cuh",
-           "collide_d3q19.cuh", "step_kernel_pair.cuh", "step_kernel_modeq3.cuh"]
+           "collide_d3q19.cuh", "step_kernel_pair.cuh", "step_kernel_modeq3.cuh", "collide_d2q9.cuh",
+           "step_kernel_strip_pair.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 TU_FLAGS = {}                # extra nvcc flags per translation unit

@@ -6,12 +6,17 @@ namespace lbf {
 
 namespace {
 // (x, y, 1, resident CTAs per SM (0 = default), producer warps (0: none), scheme,
-// sites per thread (1)):
-// scheme 2 = row-marching warp strips of 32 sites x y rows (modified
-// equilibrium only), scheme 0 = CTA tiles of x by y sites with a density halo.
+// sites per thread):
+// scheme 2 = row-marching warp strips of x sites x y rows (modified equilibrium
+// only; with 2 sites per thread each lane holds two x-adjacent sites, in
+// paired FP32, when every mode is at tau = 1, the run is FP32 and every x side
+// is a multiple of 4; otherwise the one-site strips run the same tiles),
+// scheme 0 = CTA tiles of x by y sites with a density halo.
 // Row 0 is the default of the modified equilibrium; the Guo form takes the
 // first tile row.
-constexpr int kTiles[][kVariantCols] = {{32, 32, 1, 6, 0, 2, 1}, {32, 64, 1, 6, 0, 2, 1}, {32, 16, 1, 6, 0, 2, 1},
+constexpr int kTiles[][kVariantCols] = {{64, 32, 1, 6, 0, 2, 2}, {64, 16, 1, 6, 0, 2, 2}, {64, 64, 1, 6, 0, 2, 2},
+                                        {64, 32, 1, 5, 0, 2, 2}, {64, 32, 1, 4, 0, 2, 2},
+                                        {32, 32, 1, 6, 0, 2, 1}, {32, 64, 1, 6, 0, 2, 1}, {32, 16, 1, 6, 0, 2, 1},
                                         {32, 32, 1, 7, 0, 2, 1},
                                         {32, 8, 1, 0, 0, 0, 1},  {64, 4, 1, 0, 0, 0, 1},  {128, 2, 1, 0, 0, 0, 1},
                                         {32, 4, 1, 0, 0, 0, 1},  {32, 16, 1, 0, 0, 0, 1}, {64, 8, 1, 0, 0, 0, 1}};
@@ -22,20 +27,30 @@ cudaError_t strip_of(const StepLaunch& a, cudaStream_t st) {
     if constexpr (CP == MODEQ) return step_strip<D2Q9, CP, Real, YC, 4, MINB>(a, st);
     return cudaErrorInvalidValue;            // the plan admits strips only with Eq. 65
 }
+template <int CP, class Real, int YC, int MINB>
+cudaError_t strip2_of(const StepLaunch& a, cudaStream_t st) {
+    if constexpr (CP == MODEQ) return step_strip2<D2Q9, CP, Real, YC, 4, MINB>(a, st);
+    return cudaErrorInvalidValue;
+}
 
 template <int CP, class Real>
 cudaError_t step_tile(const StepLaunch& a, cudaStream_t st) {
     switch (a.tile_id) {
-        case 0: return strip_of<CP, Real, 32, 6>(a, st);
-        case 1: return strip_of<CP, Real, 64, 6>(a, st);
-        case 2: return strip_of<CP, Real, 16, 6>(a, st);
-        case 3: return strip_of<CP, Real, 32, 7>(a, st);
-        case 4: return step_one<D2Q9, CP, Real, 32, 8, 1>(a, st);
-        case 5: return step_one<D2Q9, CP, Real, 64, 4, 1>(a, st);
-        case 6: return step_one<D2Q9, CP, Real, 128, 2, 1>(a, st);
-        case 7: return step_one<D2Q9, CP, Real, 32, 4, 1>(a, st);
-        case 8: return step_one<D2Q9, CP, Real, 32, 16, 1>(a, st);
-        case 9: return step_one<D2Q9, CP, Real, 64, 8, 1>(a, st);
+        case 0: return strip2_of<CP, Real, 32, 6>(a, st);
+        case 1: return strip2_of<CP, Real, 16, 6>(a, st);
+        case 2: return strip2_of<CP, Real, 64, 6>(a, st);
+        case 3: return strip2_of<CP, Real, 32, 5>(a, st);
+        case 4: return strip2_of<CP, Real, 32, 4>(a, st);
+        case 5: return strip_of<CP, Real, 32, 6>(a, st);
+        case 6: return strip_of<CP, Real, 64, 6>(a, st);
+        case 7: return strip_of<CP, Real, 16, 6>(a, st);
+        case 8: return strip_of<CP, Real, 32, 7>(a, st);
+        case 9: return step_one<D2Q9, CP, Real, 32, 8, 1>(a, st);
+        case 10: return step_one<D2Q9, CP, Real, 64, 4, 1>(a, st);
+        case 11: return step_one<D2Q9, CP, Real, 128, 2, 1>(a, st);
+        case 12: return step_one<D2Q9, CP, Real, 32, 4, 1>(a, st);
+        case 13: return step_one<D2Q9, CP, Real, 32, 16, 1>(a, st);
+        case 14: return step_one<D2Q9, CP, Real, 64, 8, 1>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }

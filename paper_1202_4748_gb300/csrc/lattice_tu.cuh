@@ -6,6 +6,7 @@
 #include "lb_launch.h"
 #include "step_kernel_modeq3.cuh"
 #include "step_kernel_pair.cuh"
+#include "step_kernel_strip_pair.cuh"
 #include "step_kernels.cuh"
 
 namespace lbf {
@@ -25,9 +26,9 @@ cudaError_t step_one_mode(const StepLaunch& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Row-marching strips (D2Q9, modified equilibrium): WPC warps per CTA, one
-// tile (32 sites x YC rows) per warp.
-template <class L, int CP, class Real, int YC, int WPC, int MINB, int MODE>
+// Row-marching strips (D2Q9, modified equilibrium): WPC warps per CTA, tiles
+// of SW sites x YC rows, one warp per 32 sites of a tile.
+template <class L, int CP, class Real, int YC, int WPC, int MINB, int MODE, int SW>
 cudaError_t step_strip_mode(const StepLaunch& a, cudaStream_t st) {
     StepArgs<Real> A;
     A.sys = a.sys;
@@ -38,16 +39,41 @@ cudaError_t step_strip_mode(const StepLaunch& a, cudaStream_t st) {
     A.step_ptr = a.step_ptr;
     A.k = a.k;
     A.status = a.status;
-    const int grid = (a.n_tiles + WPC - 1) / WPC;
-    step_kernel_strip<L, CP, Real, YC, WPC, MINB, MODE><<<grid, 32 * WPC, 0, st>>>(A, a.n_tiles);
+    const int warps = a.n_tiles * (SW / 32);
+    const int grid = (warps + WPC - 1) / WPC;
+    step_kernel_strip<L, CP, Real, YC, WPC, MINB, MODE, SW><<<grid, 32 * WPC, 0, st>>>(A, a.n_tiles);
     return cudaGetLastError();
 }
-template <class L, int CP, class Real, int YC, int WPC, int MINB>
+template <class L, int CP, class Real, int YC, int WPC, int MINB, int SW = 32>
 cudaError_t step_strip(const StepLaunch& a, cudaStream_t st) {
     constexpr int MB = sizeof(Real) == 4 && MINB > 0 ? MINB : 1;   // FP64 keeps its registers
-    if (a.bgk_only == 2) return step_strip_mode<L, CP, Real, YC, WPC, MB, 2>(a, st);
-    if (a.bgk_only == 1) return step_strip_mode<L, CP, Real, YC, WPC, MB, 1>(a, st);
-    return step_strip_mode<L, CP, Real, YC, WPC, MB, 0>(a, st);
+    if (a.bgk_only == 2) return step_strip_mode<L, CP, Real, YC, WPC, MB, 2, SW>(a, st);
+    if (a.bgk_only == 1) return step_strip_mode<L, CP, Real, YC, WPC, MB, 1, SW>(a, st);
+    return step_strip_mode<L, CP, Real, YC, WPC, MB, 0, SW>(a, st);
+}
+
+// Two-site strips (D2Q9, modified equilibrium, FP32, every mode at tau = 1,
+// every x side a multiple of 4) on tiles of 64 sites x YC rows; any other run
+// of the same tiles takes the one-site strips, two warps per tile.
+template <class L, int CP, class Real, int YC, int WPC, int MINB>
+cudaError_t step_strip2(const StepLaunch& a, cudaStream_t st) {
+    if constexpr (sizeof(Real) == 4 && CP == MODEQ) {
+        if (a.bgk_only == 2 && a.pair_ok) {
+            StepArgs<float> A;
+            A.sys = a.sys;
+            A.phys = static_cast<const SysPhys<float>*>(a.phys);
+            A.tiles = a.tiles;
+            A.fin = static_cast<const float*>(a.fin);
+            A.fout = static_cast<float*>(a.fout);
+            A.step_ptr = a.step_ptr;
+            A.k = a.k;
+            A.status = a.status;
+            const int grid = (a.n_tiles + WPC - 1) / WPC;
+            step_kernel_strip_pair<YC, WPC, MINB><<<grid, 32 * WPC, 0, st>>>(A, a.n_tiles);
+            return cudaGetLastError();
+        }
+    }
+    return step_strip<L, CP, Real, YC, WPC, MINB, 64>(a, st);
 }
 
 template <class L, int CP, class Real, int TX, int TY, int ZC, int MINB, int MODE>

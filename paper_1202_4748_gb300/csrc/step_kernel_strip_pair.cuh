@@ -1,0 +1,163 @@
+// Row-marching strips of the D2Q9 modified-equilibrium step with two sites
+// per lane (FP32, every mode at tau = 1).
+//
+// A warp owns 64 consecutive sites of a row (tile (system, x0, y0), x0 a
+// multiple of 64) and walks YC rows; lane l holds the sites x0 + 2l and
+// x0 + 2l + 1 as one float2.  Per footprint row yy each lane loads, for every
+// population, the aligned pair of its own two columns at the pulled row
+// (one 8-byte load); the pull's x shift of -c_x is done in registers: the
+// column left of the pair comes from the previous lane by a warp shuffle, the
+// column right of it from the next lane.  Lanes 0 and 31 also load the pair
+// just outside the strip (columns x0 - 2, x0 - 1 and x0 + 64, x0 + 65) for the
+// outermost shifted values and the density of the halo sites x0 - 1 and
+// x0 + 64.  The density of the row is then formed for both sites, the
+// neighbours' densities come by shuffles, and three density rows stay in
+// registers.  With every mode at tau = 1 the post-collision state depends on
+// the pre-collision populations only through the density and momentum, so the
+// site of row yy - 1 collides from the (drho, j) carried over from the
+// previous iteration, two sites at once in paired FP32 (the collision of
+// collide_d2q9.cuh), and stores an aligned pair per population.
+//
+// Every x side is a multiple of 4 (checked on the host), so each pair is
+// 8-byte aligned and lies inside one row; lanes past the system's last column
+// hold the periodic image of their columns for their neighbours and do not
+// collide.  The results are bit-identical to the one-site kernels.
+#pragma once
+
+#include "collide_d2q9.cuh"
+#include "step_kernels.cuh"
+
+namespace lbf {
+
+// Density deviations of one row around a lane's two sites: l = site x - 1,
+// c = (x, x + 1), r = site x + 2.
+struct PairRow {
+    float l;
+    float2 c;
+    float r;
+};
+
+// 3 x 3 density neighbourhood of the two sites: at<cx, cy, 0>() is the pair
+// of densities at (x + cx, y + cy) and (x + 1 + cx, y + cy).
+struct PairNbr {
+    PairRow m, o, p;    // rows y - 1, y, y + 1
+    template <int CX>
+    __device__ __forceinline__ static float2 pick(const PairRow& w) {
+        if constexpr (CX == -1) return make_float2(w.l, w.c.x);
+        else if constexpr (CX == 0) return w.c;
+        else return make_float2(w.c.y, w.r);
+    }
+    template <int CX, int CY, int CZ>
+    __device__ __forceinline__ float2 at() const {
+        if constexpr (CY == -1) return pick<CX>(m);
+        else if constexpr (CY == 0) return pick<CX>(o);
+        else return pick<CX>(p);
+    }
+};
+
+template <int YC, int WPC, int MINB>
+__global__ void __launch_bounds__(32 * WPC, MINB)
+    step_kernel_strip_pair(const StepArgs<float> A, int n_tiles) {
+    using L = D2Q9;
+    const int lane = threadIdx.x & 31;
+    const int wt = blockIdx.x * WPC + int(threadIdx.x >> 5);
+    if (wt >= n_tiles) return;                       // the whole warp leaves together
+    const int4 tl = A.tiles[wt];
+    // register copies of the per-system records: read once, not again after every row's stores
+    const SysDev S = A.sys[tl.x];
+    const SysPhys<float> P = A.phys[tl.x];
+    const int nx = S.nx, ny = S.ny, N = S.ns;
+    const bool sm = S.small != 0;
+    const float* __restrict__ fb = A.fin + S.pop_offset;
+    float* __restrict__ fo = A.fout + S.pop_offset;
+    const int x = tl.y + 2 * lane;
+    const bool own = x < nx;
+    const bool edge = lane == 0 || lane == 31;
+    const bool left = lane == 0;
+    const int xs = wrapm(x, nx);                                   // even: the pair is aligned
+    const int xt = wrapm(left ? tl.y - 2 : tl.y + 64, nx);         // the pair just outside the strip
+    const NoiseKey key = noise_key(S, *A.step_ptr + A.k);
+    const int y0 = tl.z, y1 = min(y0 + YC, ny);
+
+    float2 pr = make_float2(0.f, 0.f), pjx = pr, pjy = pr;        // (drho, j) of row yy - 1
+    PairRow Rm{0.f, pr, 0.f}, R0 = Rm, Rp = Rm;                  // density rows yy - 2, yy - 1, yy
+    for (int yy = y0 - 1; yy <= y1; ++yy) {
+        // pulled rows yy - c_y for c_y = -1, 0, 1 (index 1 + c_y)
+        const int ro[3] = {(sm ? wrapm(yy + 1, ny) : wrap2(yy + 1, ny)) * nx,
+                           (sm ? wrapm(yy, ny) : wrap2(yy, ny)) * nx,
+                           (sm ? wrapm(yy - 1, ny) : wrap2(yy - 1, ny)) * nx};
+        float2 s[9];
+        sfor<0, 9>([&](auto I) {
+            constexpr int i = I;
+            s[i] = *reinterpret_cast<const float2*>(fb + i * N + ro[1 + L::c(i, 1)] + xs);
+        });
+        // edge lanes: the outermost shifted values e (lane 0: column x0 - 1 of the
+        // populations with c_x = +1; lane 31: column x0 + 64 of those with c_x = -1)
+        // and the density of the halo site (x0 - 1 or x0 + 64)
+        float rh = 0.f, e[3] = {0.f, 0.f, 0.f};
+        if (edge) {
+            float v = 0.f;
+            sfor<0, 9>([&](auto I) {
+                constexpr int i = I;
+                constexpr int cx = L::c(i, 0);
+                const float2 t = *reinterpret_cast<const float2*>(fb + i * N + ro[1 + L::c(i, 1)] + xt);
+                float h;
+                if constexpr (cx == 1) h = left ? t.x : s[i].y;
+                else if constexpr (cx == 0) h = left ? t.y : t.x;
+                else h = left ? s[i].x : t.y;
+                v = vadd(v, h);
+                // pairs of opposite x velocities (1, 2), (5, 6), (7, 8) share the slot of e
+                constexpr int ke = (i == 1 || i == 2) ? 0 : ((i == 5 || i == 6) ? 1 : 2);
+                if constexpr (cx == 1) {
+                    if (left) e[ke] = t.y;
+                } else if constexpr (cx == -1) {
+                    if (!left) e[ke] = t.x;
+                }
+            });
+            rh = v;
+        }
+        // the pull's x shift: f_i(x) = s_i(x - c_x)
+        float2 g[9];
+        sfor<0, 9>([&](auto I) {
+            constexpr int i = I;
+            constexpr int cx = L::c(i, 0);
+            constexpr int ke = (i == 1 || i == 2) ? 0 : ((i == 5 || i == 6) ? 1 : 2);
+            if constexpr (cx == 0) {
+                g[i] = s[i];
+            } else if constexpr (cx == 1) {
+                float up = __shfl_up_sync(0xffffffffu, s[i].y, 1);
+                if (lane == 0) up = e[ke];
+                g[i] = make_float2(up, s[i].x);
+            } else {
+                float dn = __shfl_down_sync(0xffffffffu, s[i].x, 1);
+                if (lane == 31) dn = e[ke];
+                g[i] = make_float2(s[i].y, dn);
+            }
+        });
+        float2 r, jx, jy;
+        moments_d2q9<float2>(g, r, jx, jy);
+        float rl = __shfl_up_sync(0xffffffffu, r.y, 1);
+        float rr = __shfl_down_sync(0xffffffffu, r.x, 1);
+        if (lane == 0) rl = rh;
+        if (lane == 31) rr = rh;
+        Rm = R0;
+        R0 = Rp;
+        Rp = PairRow{rl, r, rr};
+        if (yy > y0 && own) {
+            const int y = yy - 1;
+            const PairNbr nb{Rm, R0, Rp};
+            const uint32_t site = uint32_t(y * nx + x);
+            float2 f[9];
+            collide_d2q9_modeq<2, float2>(f, pr, pjx, pjy, nb, P, key, make_uint2(site, site + 1u), A.status);
+            sfor<0, 9>([&](auto I) {
+                constexpr int i = I;
+                *reinterpret_cast<float2*>(fo + i * N + site) = f[i];
+            });
+        }
+        pr = r;
+        pjx = jx;
+        pjy = jy;
+    }
+}
+
+}  // namespace lbf

@@ -16,6 +16,7 @@
 // otherwise each moment relaxes at its own rate in the basis of Eq. 66.
 #pragma once
 
+#include "collide_d2q9.cuh"
 #include "collide_d3q19.cuh"
 #include "lb_device.cuh"
 
@@ -600,7 +601,12 @@ __global__ void __launch_bounds__(TX* TY* TZ)
     const int64_t step = *A.step_ptr + A.k;
     const TileView<Real, SX, SY> rv{srho, cidx};
     const TileView<Real, LX, LY> lv{slap, lidx};
-    if constexpr (CP == GUO && BGK_ONLY)
+    if constexpr (CP == MODEQ && L::D == 2) {
+        Real d0, jx, jy;
+        moments_d2q9<Real>(f, d0, jx, jy);
+        collide_d2q9_modeq<MODE, Real>(f, drho, jx, jy, rv, A.phys[tl.x], noise_key(S, step), uint32_t(site),
+                                       A.status);
+    } else if constexpr (CP == GUO && BGK_ONLY)
         collide_guo_bgk<L, Real, TAU1>(f, drho, lv, S, A.phys[tl.x], uint32_t(site), step, A.status);
     else
         collide_site<L, CP, Real, BGK_ONLY, TileView<Real, SX, SY>, TileView<Real, LX, LY>, TAU1>(
@@ -621,34 +627,34 @@ struct Nbr9 {
     template <int CX, int CY, int CZ>
     __device__ __forceinline__ Real at() const { return v[1 + CY][1 + CX]; }
 };
-template <class Real>
-struct NoView {
-    template <int CX, int CY, int CZ>
-    __device__ __forceinline__ Real at() const { return Real(0); }
-};
 
 // Row-marching strips for the D2Q9 modified-equilibrium step (Eq. 65 needs
 // the density on the 3 x 3 neighbourhood only).  Each warp owns 32
-// consecutive sites of a row (tile (system, x0, y0)) and walks YC rows.  Per
-// footprint row yy a lane pulls its site's 9 populations, forms rho, and the
-// neighbours' rho comes by warp shuffles; lanes 0 and 31 also pull the halo
-// sites x0 - 1 and x0 + 32.  Three density rows live in registers as
-// (x - 1, x, x + 1) triples, and the site of row yy - 1 collides from its
-// populations pulled one iteration earlier.  No shared memory and no CTA
-// barrier: every footprint value is formed once per chunk (halo 2/32 in x,
-// 2/YC in y).  Lanes past the system's last column form the periodic image
-// of their column for their neighbours and do not collide.  (Colliding two
-// rows behind, to overlap the next row's loads, measured slower: 8 more
-// registers per thread, fewer warps in flight.)
-template <class L, int CP, class Real, int YC, int WPC, int MINB, int MODE>
+// consecutive sites of a row and walks YC rows; a tile (system, x0, y0) is SW
+// sites wide (32, or 64 for the tiles of the two-site kernel, whose one-site
+// form gives each tile two warps).  Per footprint row yy a lane pulls its
+// site's 9 populations, forms rho, and the neighbours' rho comes by warp
+// shuffles; lanes 0 and 31 also pull the halo sites x0 - 1 and x0 + 32.
+// Three density rows live in registers as (x - 1, x, x + 1) triples, and the
+// site of row yy - 1 collides from its populations pulled one iteration
+// earlier (with every mode at tau = 1, from its density and momentum only;
+// the collision is collide_d2q9_modeq for every relaxation setting).
+// No shared memory and no CTA barrier: every footprint value is formed once
+// per chunk (halo 2/32 in x, 2/YC in y).  Lanes past the system's last column
+// form the periodic image of their column for their neighbours and do not
+// collide.  (Colliding two rows behind, to overlap the next row's loads,
+// measured slower: 8 more registers per thread, fewer warps in flight.)
+template <class L, int CP, class Real, int YC, int WPC, int MINB, int MODE, int SW = 32>
 __global__ void __launch_bounds__(32 * WPC, MINB) step_kernel_strip(const StepArgs<Real> A, int n_tiles) {
     static_assert(L::D == 2 && CP == MODEQ, "row strips: D2Q9 with the modified equilibrium");
     constexpr bool BGK_ONLY = MODE >= 1;
+    constexpr bool TAU1 = MODE == 2;
     constexpr int Q = L::Q;
+    constexpr int WPT = SW / 32;                     // warps per tile
     const int lane = threadIdx.x & 31;
-    const int wt = blockIdx.x * WPC + int(threadIdx.x >> 5);
-    if (wt >= n_tiles) return;                       // the whole warp leaves together
-    const int4 tl = A.tiles[wt];
+    const int wg = blockIdx.x * WPC + int(threadIdx.x >> 5);
+    if (wg >= n_tiles * WPT) return;                 // the whole warp leaves together
+    const int4 tl = A.tiles[wg / WPT];
     // register copies of the per-system records: read once, not again after every row's stores
     const SysDev S = A.sys[tl.x];
     const SysPhys<Real> P = A.phys[tl.x];
@@ -656,21 +662,23 @@ __global__ void __launch_bounds__(32 * WPC, MINB) step_kernel_strip(const StepAr
     const bool sm = S.small != 0;
     const Real* __restrict__ fb = A.fin + S.pop_offset;
     Real* __restrict__ fo = A.fout + S.pop_offset;
-    const int x = tl.y + lane;
+    const int x0 = tl.y + 32 * (wg % WPT);
+    const int x = x0 + lane;
     const bool own = x < nx;
     const bool extra = lane == 0 || lane == 31;
     // pulled columns x - c_x for c_x = -1, 0, 1 (index 1 + c_x), of the lane's site and of its halo site
     const int xs = wrapm(x, nx);
-    const int xh = wrapm(lane == 0 ? tl.y - 1 : tl.y + 32, nx);
+    const int xh = wrapm(lane == 0 ? x0 - 1 : x0 + 32, nx);
     const int xo[3] = {wrap1(xs + 1, nx), xs, wrap1(xs - 1, nx)};
     const int ho[3] = {wrap1(xh + 1, nx), xh, wrap1(xh - 1, nx)};
     const int64_t step = *A.step_ptr + A.k;
     const int y0 = tl.z, y1 = min(y0 + YC, ny);
 
-    Real fp[Q];                                      // pulled populations of row yy - 1
+    Real fp[TAU1 ? 1 : Q];                           // pulled populations of row yy - 1
+    Real pr = Real(0), pjx = Real(0), pjy = Real(0); // tau = 1: (drho, j) of row yy - 1
     Real Rm[3] = {Real(0), Real(0), Real(0)}, R0[3] = {Real(0), Real(0), Real(0)},
          Rp[3] = {Real(0), Real(0), Real(0)};        // rho rows yy - 2, yy - 1, yy
-    sfor<0, Q>([&](auto I) { fp[decltype(I)::value] = Real(0); });
+    if constexpr (!TAU1) sfor<0, Q>([&](auto I) { fp[decltype(I)::value] = Real(0); });
     for (int yy = y0 - 1; yy <= y1; ++yy) {
         // pulled rows yy - c_y for c_y = -1, 0, 1 (index 1 + c_y)
         const int ro[3] = {(sm ? wrapm(yy + 1, ny) : wrap2(yy + 1, ny)) * nx,
@@ -688,10 +696,10 @@ __global__ void __launch_bounds__(32 * WPC, MINB) step_kernel_strip(const StepAr
                 constexpr int i = I;
                 g[i] = fb[i * N + ro[1 + L::c(i, 1)] + ho[1 + L::c(i, 0)]];
             });
-            sfor<0, Q>([&](auto I) { re += g[decltype(I)::value]; });
+            sfor<0, Q>([&](auto I) { re = vadd(re, g[decltype(I)::value]); });
         }
-        Real rc = Real(0);
-        sfor<0, Q>([&](auto I) { rc += fc[decltype(I)::value]; });
+        Real rc, jx, jy;
+        moments_d2q9<Real>(fc, rc, jx, jy);
         Real rl = __shfl_up_sync(0xffffffffu, rc, 1);
         Real rr = __shfl_down_sync(0xffffffffu, rc, 1);
         if (lane == 0) rl = re;
@@ -707,16 +715,24 @@ __global__ void __launch_bounds__(32 * WPC, MINB) step_kernel_strip(const StepAr
         if (yy > y0 && own) {
             const int y = yy - 1;
             const Nbr9<Real> nb{{{Rm[0], Rm[1], Rm[2]}, {R0[0], R0[1], R0[2]}, {Rp[0], Rp[1], Rp[2]}}};
-            const NoView<Real> nl;
             const int site = y * nx + x;
-            collide_site<L, CP, Real, BGK_ONLY, Nbr9<Real>, NoView<Real>, MODE == 2>(fp, R0[1], nb, nl, S, P,
-                                                                                  uint32_t(site), step, A.status);
+            Real fr[Q];
+            if constexpr (TAU1) {
+                collide_d2q9_modeq<2, Real>(fr, pr, pjx, pjy, nb, P, noise_key(S, step), uint32_t(site), A.status);
+            } else {
+                sfor<0, Q>([&](auto I) { fr[decltype(I)::value] = fp[decltype(I)::value]; });
+                collide_d2q9_modeq<MODE, Real>(fr, R0[1], pjx, pjy, nb, P, noise_key(S, step), uint32_t(site),
+                                               A.status);
+            }
             sfor<0, Q>([&](auto I) {
                 constexpr int i = I;
-                fo[i * N + site] = fp[i];
+                fo[i * N + site] = fr[i];
             });
         }
-        sfor<0, Q>([&](auto I) { fp[decltype(I)::value] = fc[decltype(I)::value]; });
+        pr = rc;
+        pjx = jx;
+        pjy = jy;
+        if constexpr (!TAU1) sfor<0, Q>([&](auto I) { fp[decltype(I)::value] = fc[decltype(I)::value]; });
     }
 }
 

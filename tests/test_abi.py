@@ -167,11 +167,13 @@ def test_kernel_variant_table():
             assert x > 0 and y > 0 and z > 0 and occ >= 0 and pw >= 0 and stg in (0, 1, 2, 3) and spt in (1, 2)
             assert x % 16 == 0
             assert stg != 1 or pw > 0                    # bulk staging is done by producer warps
-            if spt == 2:                                 # paired sites: the D3Q19 warp-specialised kernel
-                assert lat == "D3Q19" and pw > 0 and stg in (0, 3) and (x * y // 2) % 32 == 0
+            if spt == 2 and lat == "D3Q19":              # paired sites: the warp-specialised kernel
+                assert pw > 0 and stg in (0, 3) and (x * y // 2) % 32 == 0
+            if spt == 2 and lat == "D2Q9":               # paired sites: two-site row strips
+                assert stg == 2
             assert stg != 3 or spt == 2                  # cp.async staging: the paired kernel's producers
-            if stg == 2:                                 # row strips: one warp per 32-site tile
-                assert lat == "D2Q9" and x == 32 and pw == 0
+            if stg == 2:                                 # row strips: one warp per 32 sites x spt of a row
+                assert lat == "D2Q9" and x == 32 * spt and pw == 0
             else:
                 assert x * y // spt + 32 * pw <= 1024
                 assert x * y + 32 * pw <= 1024           # the one-site fallback of the same tile
