@@ -49,7 +49,8 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
 KERNEL_SOURCES = ["paper_1202_4748_gb300/csrc/step_kernels.cuh", "paper_1202_4748_gb300/csrc/lb_device.cuh",
                   "paper_1202_4748_gb300/csrc/step_kernel_pair.cuh", "paper_1202_4748_gb300/csrc/collide_d3q19.cuh",
                   "paper_1202_4748_gb300/csrc/vec2.cuh", "paper_1202_4748_gb300/csrc/collide_d2q9.cuh",
-                  "paper_1202_4748_gb300/csrc/step_kernel_strip_pair.cuh"]
+                  "paper_1202_4748_gb300/csrc/step_kernel_strip_pair.cuh", "paper_1202_4748_gb300/csrc/lattice_tu.cuh",
+                  "paper_1202_4748_gb300/csrc/lattice_d2q9.cu", "paper_1202_4748_gb300/csrc/lattice_d3q19.cu"]
 
 
 def kernel_source_hash():
@@ -333,11 +334,12 @@ def main():
         best, _ = autotune.tune(systems, wl["precision"], cache=None)
         vindex = rows.index(best)
     elif args.variant == "default":
-        vindex = 0
+        vindex = -1                         # the library's choice, read back below
     else:
         vindex = int(args.variant)
     ens = lb.Ensemble(systems, precision=wl["precision"], obs_every=LB_STEPS_PER_STEP,
                       graph_chunk=LB_STEPS_PER_STEP, variant=vindex + 1)
+    vindex = ens.kernel_variant()
     ens.init(amplitude=0.01)
     for _ in range(args.warmup):
         ens.step(LB_STEPS_PER_STEP)

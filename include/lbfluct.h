@@ -108,7 +108,9 @@ typedef struct {
  *               compiled variant, else LB_ERR_UNSUPPORTED.
  *   variant     if > 0, selects compiled step-kernel variant number
  *               variant - 1 of lb_kernel_variants() directly (overrides
- *               tile and occupancy); 0 = by tile / occupancy / default.
+ *               tile and occupancy); 0 = by tile / occupancy / default
+ *               (the default's z-chunk adapts to the ensemble, see
+ *               lb_kernel_variant).
  *   hist_bins   order-parameter histograms P_L(m) (Sec. II D): every
  *               observable sample also bins each block value m of every
  *               level into hist_bins equal bins on [-hist_range, hist_range)
@@ -369,13 +371,15 @@ lb_status lb_load(lb_ctx* ctx, const char* path);
  * loads, 1 = (D3Q19) producers stage the footprint rows with bulk copies
  * (cp.async.bulk) into shared memory, when every system has nx % 4 == 0,
  * nx >= 8 and all sides >= 3, else the scheme-0 kernel of the same tile runs,
- * 2 = (D2Q9, modified equilibrium only) row-marching strips: one warp per tile
- * of 32 sites x y rows, densities in registers and warp shuffles, 3 = (paired
- * D3Q19 kernel) producers stage their 16-byte quads of pulled populations in
- * shared memory with cp.async instead of holding them in registers; sites per
- * consumer thread: 1, or 2 = (D3Q19, warp-specialised) two x-adjacent sites
- * per consumer thread with paired FP32 arithmetic, when every system has
- * nx % 4 == 0, else the one-site warp-specialised kernel of the same tile runs)
+ * 2 = (D2Q9, modified equilibrium only) row-marching strips: one warp per 32
+ * sites (x sites per tile) of y rows, densities in registers and warp
+ * shuffles, 3 = (paired D3Q19 kernel) producers stage their 16-byte quads of
+ * pulled populations in shared memory with cp.async instead of holding them
+ * in registers; sites per thread: 1, or 2 = two x-adjacent sites per thread
+ * with paired FP32 arithmetic (D3Q19: per consumer thread of the
+ * warp-specialised kernel; D2Q9: per lane of 64-site strips, every mode at
+ * tau = 1), when the run is FP32 and every system has nx % 4 == 0, else the
+ * one-site kernel of the same tile runs)
  * into out (nullable) and returns the number of variants (negative lb_status
  * on error).
  * Row 0 is the default; where the coupling cannot run it (scheme 2 with the
@@ -383,6 +387,14 @@ lb_status lb_load(lb_ctx* ctx, const char* path);
  * run gives LB_ERR_UNSUPPORTED.  Used by the autotuner; no device call. */
 #define LB_VARIANT_COLS 7
 int lb_kernel_variants(int lattice, int32_t* out, int max_rows);
+
+/* The row of lb_kernel_variants() (0-based) that ctx's step kernel runs.
+ * With variant = 0 and no tile or occupancy given, lb_create takes the
+ * default row, or a row that differs from it only in a longer z-chunk when
+ * the ensemble still has at least twice as many tiles as the GPU holds
+ * resident CTAs (fewer halo planes per site, no idle SMs in the last wave).
+ * Errors: LB_ERR_ARG. */
+lb_status lb_kernel_variant(lb_ctx* ctx, int* row);
 
 /* Host-armed fault injection for testing the error paths without faulting a
  * GPU (the paper has no counterpart).  kind:

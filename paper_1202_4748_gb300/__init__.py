@@ -108,6 +108,7 @@ _SIG = {
     "lb_inject_fault": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
     "lb_selftest_wait_timeout": (ctypes.c_int, [_P, _P]),
     "lb_kernel_variants": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int]),
+    "lb_kernel_variant": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "lb_block_moments_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
                                                 ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P, _P]),
     "lb_destroy": (None, [_P]),
@@ -386,6 +387,12 @@ class Ensemble:
         f = np.ascontiguousarray(f, dtype=np.float64)
         assert f.shape == (self.q,) + self.shape(k)
         check(lb_write_fields(self.ctx, k, f.ctypes.data_as(_P)), "lb_write_fields")
+
+    def kernel_variant(self):
+        """The row of kernel_variants() this context's step kernel runs."""
+        v = ctypes.c_int()
+        check(lb_kernel_variant(self.ctx, ctypes.byref(v)), "lb_kernel_variant")
+        return v.value
 
     def kernel_launches(self):
         v = ctypes.c_int64()

@@ -164,6 +164,46 @@ lb_status choose_tile(int lattice, int coupling, const lb_run_opts* o, int& tile
     return LB_OK;
 }
 
+// Number of step tiles (CTAs) of a tile shape over the ensemble.
+int64_t tiles_of(const lb_system_desc* s, int n, const int tdim[3]) {
+    int64_t c = 0;
+    for (int k = 0; k < n; ++k)
+        c += int64_t((s[k].nx + tdim[0] - 1) / tdim[0]) * ((s[k].ny + tdim[1] - 1) / tdim[1]) *
+             ((s[k].nz + tdim[2] - 1) / tdim[2]);
+    return c;
+}
+
+// Default variant: among the rows that differ from the default row only in
+// the z-chunk, the longest chunk whose CTAs still fill the GPU at least twice
+// over (resident CTAs per SM x SMs of the current device; 152 SMs when no
+// device is visible), else the default row.  Longer chunks re-read fewer
+// halo planes (4 per chunk), but too few CTAs leave SMs idle in the last
+// wave: on GB300 the 64-plane chunks win on the 160-system ensemble (1,184
+// CTAs) and on 256^3 (1,024), the 32-plane ones on 32 systems of 64^3 (512).
+void prefer_longer_chunk(const lb_system_desc* s, int n, int& tile_id, int tdim[3]) {
+    int t[32][kVariantCols];
+    const int nt = tile_table(s[0].lattice, t);
+    int sms = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    const int* d = t[tile_id];
+    int best = tile_id;
+    for (int k = 0; k < nt; ++k) {
+        bool same = true;
+        for (int c = 0; c < kVariantCols; ++c)
+            if (c != 2 && t[k][c] != d[c]) same = false;
+        if (!same || t[k][2] <= t[best][2]) continue;
+        const int occ = t[k][3] > 0 ? t[k][3] : 1;
+        if (tiles_of(s, n, t[k]) >= int64_t(2) * occ * sms) best = k;
+    }
+    tile_id = best;
+    for (int k = 0; k < 3; ++k) tdim[k] = t[best][k];
+}
+
 lb_status make_plan(const lb_system_desc* s, int n, const lb_run_opts* o, std::vector<SysHost>& sys, Plan& P,
                     int& tile_id) {
     lb_status st = validate(s, n, o);
@@ -171,6 +211,7 @@ lb_status make_plan(const lb_system_desc* s, int n, const lb_run_opts* o, std::v
     int tdim[3];
     st = choose_tile(s[0].lattice, s[0].coupling, o, tile_id, tdim);
     if (st != LB_OK) return st;
+    if (o->variant == 0 && o->tile[0] <= 0 && o->occupancy <= 0) prefer_longer_chunk(s, n, tile_id, tdim);
     const int q = q_of(s[0].lattice);
     const size_t es = o->precision == LB_FP64 ? 8 : 4;
     sys.assign(n, SysHost());
@@ -1526,6 +1567,12 @@ lb_status lb_selftest_wait_timeout(int* d_status, void* stream) {
     if (cudaStreamSynchronize(st) != cudaSuccess) return LB_ERR_CUDA;
     if (h & (1 << 30)) return LB_ERR_STATE;
     return (h & ST_TIMEOUT) ? LB_ERR_TIMEOUT : LB_ERR_STATE;
+}
+
+lb_status lb_kernel_variant(lb_ctx* ctx, int* row) {
+    if (!ctx || !row) return LB_ERR_ARG;
+    *row = ctx->tile_id;
+    return LB_OK;
 }
 
 int lb_kernel_variants(int lattice, int32_t* out, int max_rows) {

@@ -14,8 +14,8 @@ namespace {
 // scheme 0 = CTA tiles of x by y sites with a density halo.
 // Row 0 is the default of the modified equilibrium; the Guo form takes the
 // first tile row.
-constexpr int kTiles[][kVariantCols] = {{64, 32, 1, 6, 0, 2, 2}, {64, 16, 1, 6, 0, 2, 2}, {64, 64, 1, 6, 0, 2, 2},
-                                        {64, 32, 1, 5, 0, 2, 2}, {64, 32, 1, 4, 0, 2, 2},
+constexpr int kTiles[][kVariantCols] = {{64, 32, 1, 3, 0, 2, 2}, {64, 16, 1, 3, 0, 2, 2}, {64, 64, 1, 3, 0, 2, 2},
+                                        {64, 32, 1, 4, 0, 2, 2},
                                         {32, 32, 1, 6, 0, 2, 1}, {32, 64, 1, 6, 0, 2, 1}, {32, 16, 1, 6, 0, 2, 1},
                                         {32, 32, 1, 7, 0, 2, 1},
                                         {32, 8, 1, 0, 0, 0, 1},  {64, 4, 1, 0, 0, 0, 1},  {128, 2, 1, 0, 0, 0, 1},
@@ -36,21 +36,20 @@ cudaError_t strip2_of(const StepLaunch& a, cudaStream_t st) {
 template <int CP, class Real>
 cudaError_t step_tile(const StepLaunch& a, cudaStream_t st) {
     switch (a.tile_id) {
-        case 0: return strip2_of<CP, Real, 32, 6>(a, st);
-        case 1: return strip2_of<CP, Real, 16, 6>(a, st);
-        case 2: return strip2_of<CP, Real, 64, 6>(a, st);
-        case 3: return strip2_of<CP, Real, 32, 5>(a, st);
-        case 4: return strip2_of<CP, Real, 32, 4>(a, st);
-        case 5: return strip_of<CP, Real, 32, 6>(a, st);
-        case 6: return strip_of<CP, Real, 64, 6>(a, st);
-        case 7: return strip_of<CP, Real, 16, 6>(a, st);
-        case 8: return strip_of<CP, Real, 32, 7>(a, st);
-        case 9: return step_one<D2Q9, CP, Real, 32, 8, 1>(a, st);
-        case 10: return step_one<D2Q9, CP, Real, 64, 4, 1>(a, st);
-        case 11: return step_one<D2Q9, CP, Real, 128, 2, 1>(a, st);
-        case 12: return step_one<D2Q9, CP, Real, 32, 4, 1>(a, st);
-        case 13: return step_one<D2Q9, CP, Real, 32, 16, 1>(a, st);
-        case 14: return step_one<D2Q9, CP, Real, 64, 8, 1>(a, st);
+        case 0: return strip2_of<CP, Real, 32, 3>(a, st);
+        case 1: return strip2_of<CP, Real, 16, 3>(a, st);
+        case 2: return strip2_of<CP, Real, 64, 3>(a, st);
+        case 3: return strip2_of<CP, Real, 32, 4>(a, st);
+        case 4: return strip_of<CP, Real, 32, 6>(a, st);
+        case 5: return strip_of<CP, Real, 64, 6>(a, st);
+        case 6: return strip_of<CP, Real, 16, 6>(a, st);
+        case 7: return strip_of<CP, Real, 32, 7>(a, st);
+        case 8: return step_one<D2Q9, CP, Real, 32, 8, 1>(a, st);
+        case 9: return step_one<D2Q9, CP, Real, 64, 4, 1>(a, st);
+        case 10: return step_one<D2Q9, CP, Real, 128, 2, 1>(a, st);
+        case 11: return step_one<D2Q9, CP, Real, 32, 4, 1>(a, st);
+        case 12: return step_one<D2Q9, CP, Real, 32, 16, 1>(a, st);
+        case 13: return step_one<D2Q9, CP, Real, 64, 8, 1>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -15,7 +15,8 @@ namespace {
 // the fully relaxed FP32 path; the other paths run the plain kernel with the
 // same tile), whose producers stage the footprint with plain loads (staging 0)
 // or with bulk copies into shared memory (staging 1; systems that do not allow
-// it run the staging-0 kernel of the same tile).  Two sites per consumer
+// it run the staging-0 kernel of the same tile); the paired kernel stages
+// aligned quads in registers (0) or with cp.async in shared memory (3).  Two sites per consumer
 // thread: the paired kernel (x-adjacent site pairs, paired FP32 arithmetic;
 // ensembles with an odd nx run the one-site warp-specialised kernel of the
 // same tile).  The first entry is the default.
@@ -26,7 +27,7 @@ constexpr int kTiles[][kVariantCols] = {
     {16, 16, 32, 4, 0, 0, 1}};
 constexpr int kNumTiles = int(sizeof(kTiles) / sizeof(kTiles[0]));
 // ring planes of the paired kernel: 8 with register staging (2 CTAs per SM),
-// 4 with cp.async staging (3 CTAs per SM share the shared memory)
+// 4 with cp.async staging (the staging areas share the shared memory)
 constexpr int pair_ring(int stg) { return stg == 3 ? 4 : 8; }
 
 template <int CP, class Real, int I>

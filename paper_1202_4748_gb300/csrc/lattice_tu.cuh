@@ -183,7 +183,7 @@ cudaError_t step_pair(const StepLaunch& a, cudaStream_t st) {
         // shared memory, and the producers' load misses are staged in L1)
         if (e != cudaSuccess) return e;
         // the register split must balance against the launch count it assumes
-        state = (!PairRegs<TX, TY, PW, MINB>::split || fa.numRegs == PairRegs<TX, TY, PW, MINB>::launch) ? 1 : -1;
+        state = (!PairRegs<TX, TY, PW, MINB, STG>::split || fa.numRegs == PairRegs<TX, TY, PW, MINB, STG>::launch) ? 1 : -1;
     }
     if (state < 0) return step_ws<D3Q19, TX, TY, ZC, PW, 1, 0>(a, st);
     step_kernel_pair<TX, TY, ZC, PW, MINB, R, STG><<<a.n_tiles, TX * TY / 2 + 32 * PW, dyn, st>>>(A);

@@ -107,28 +107,34 @@ struct PairLapView {
     }
 };
 
-// Register split between the warpgroups: the producers' batched loads want
-// about twice the registers of the collision, so when consumers and producers
-// are whole warpgroups of equal size the consumers give up registers
-// (setmaxnreg.dec) and the producers take them (setmaxnreg.inc).  The launch
-// count is the budget of MINB resident CTAs; the host checks that the compiled
-// kernel has exactly that many registers before it launches the kernel (an
-// increase that the decreases do not cover would wait forever).
-template <int TX, int TY, int PW, int MINB>
+// Register split between the warpgroups, when consumers and producers are
+// whole warpgroups of equal size: with register staging the producers'
+// batched loads want about twice the registers of the collision, so the
+// consumers give up registers (setmaxnreg.dec) and the producers take them
+// (setmaxnreg.inc); with cp.async staging it is the other way round.  The
+// launch count is the budget of MINB resident CTAs; the host checks that the
+// compiled kernel has exactly that many registers before it launches the
+// kernel (an increase that the decreases do not cover would wait forever).
+template <int TX, int TY, int PW, int MINB, int STG>
 struct PairRegs {
     static constexpr int NC = TX * TY / 2, NP = 32 * PW, NT = NC + NP;
     static constexpr int raw = 65536 / (MINB * NT);
     static constexpr int launch = (raw > 255 ? 255 : raw) & ~7;
-    static constexpr int cons = 80;
-    static constexpr bool split = NC % 128 == 0 && NC == NP && launch > cons;
+    // register staging: the consumers keep 80 and the producers take the rest;
+    // cp.async staging: the producers hold no loads in registers and need
+    // about 48, so the collision takes the rest (112 of 2 x 80 at 3 CTAs per
+    // SM: 0.516 -> 0.475 ms on the 160-system ensemble, no spills)
+    static constexpr int cons = STG == 3 ? 2 * launch - 48 : 80;
+    static constexpr bool split = NC % 128 == 0 && NC == NP && launch != cons && cons <= 256 && 2 * launch - cons >= 24;
     static constexpr int prod = split ? 2 * launch - cons : launch;
-    static_assert(!split || (prod <= 256 && prod % 8 == 0), "register split");
+    static_assert(!split || (prod <= 256 && prod % 8 == 0 && cons <= 256 && cons % 8 == 0), "register split");
 };
 
 // STG: 0 = each producer lane loads its quads into registers (in flight one
 // plane ahead); 3 = cp.async copies them into a per-lane staging area in
 // shared memory (no registers held by loads in flight), which leaves room
-// for more resident CTAs.
+// for more resident CTAs.  (Two staging areas, so that the copies run two
+// planes ahead, need 2 CTAs per SM and measured slower.)
 template <int TX, int TY, int PW, int R, int STG>
 struct PairSmem {
     static constexpr size_t stage = STG == 3 ? size_t(19) * 32 * PW * 16 : 0;   // [19][producers] float4
@@ -137,7 +143,7 @@ struct PairSmem {
 
 template <int TX, int TY, int ZC, int PW, int MINB, int R, int STG>
 __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(const StepArgs<float> A) {
-    using RG = PairRegs<TX, TY, PW, MINB>;
+    using RG = PairRegs<TX, TY, PW, MINB, STG>;
     using L = D3Q19;
     using LY_ = PairLayout<TX, TY, R>;
     constexpr int H = 2;
@@ -170,7 +176,8 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
 
     if (tid >= NC) {
         // ---------------- producers ----------------
-        if constexpr (RG::split) regs_inc<RG::prod>();
+        if constexpr (RG::split && RG::prod > RG::launch) regs_inc<RG::prod>();
+        if constexpr (RG::split && RG::prod < RG::launch) regs_dec<RG::prod>();
         const float* __restrict__ fb = A.fin + S.pop_offset;
         const int ptid = tid - NC;
         static_assert(PW >= LY_::PWN, "producer warps cover the footprint rows");
@@ -193,9 +200,10 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
         // summed (and, staged, its density stored: every staged value has been
         // read back before the copies that overwrite it are issued), so they
         // are in flight across the barrier and the Laplacian
-        float4 g[STG == 3 ? 1 : 19];
+        constexpr bool CPA = STG == 3;                   // staged by cp.async
+        float4 g[CPA ? 1 : 19];
         float4* const stage = reinterpret_cast<float4*>(ring + R * PLANE) + ptid;   // [19][NP], this lane's column
-        if constexpr (STG != 3)
+        if constexpr (!CPA)
             sfor<0, 19>([&](auto I) { g[decltype(I)::value] = make_float4(0.0f, 0.0f, 0.0f, 0.0f); });
         auto pull = [&](int zz) {
             // source planes z - c_z for c_z = -1, 0, +1
@@ -207,14 +215,14 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
                     constexpr int i = I;
                     constexpr int cy = L::c(i, 1), cz = L::c(i, 2);
                     const float* src = rowp[1 + cy] + (i * N + zo[1 + cz]);
-                    if constexpr (STG == 3) cp_async16(stage + i * NP, src);
+                    if constexpr (CPA) cp_async16(stage + i * NP, src);
                     else g[i] = *reinterpret_cast<const float4*>(src);
                 });
             }
-            if constexpr (STG == 3) cp_async_commit();
+            if constexpr (CPA) cp_async_commit();
         };
         auto pulled = [&](auto I) -> float4 {
-            if constexpr (STG == 3) return stage[decltype(I)::value * NP];
+            if constexpr (CPA) return stage[decltype(I)::value * NP];
             else return g[decltype(I)::value];
         };
         pull(z0 - H);
@@ -226,7 +234,7 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
             // c_x = +1 (-1) direction pulls x - 1 (x + 1), one of which lives in
             // the neighbouring lane.  Density and momentum are summed in the
             // order of the one-site kernels (from 0, direction by direction).
-            if constexpr (STG == 3) cp_async_wait_all();     // this lane's copies of plane zz have landed
+            if constexpr (CPA) cp_async_wait_all();      // this lane's copies of plane zz have landed
             float2 r01 = make_float2(0.0f, 0.0f), r23 = r01;
             float2 j01[3] = {r01, r01, r01}, j23[3] = {r01, r01, r01};
             sfor<0, 19>([&](auto I) {
@@ -294,7 +302,8 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
         }
     } else {
         // ---------------- consumers ----------------
-        if constexpr (RG::split) regs_dec<RG::cons>();
+        if constexpr (RG::split && RG::cons < RG::launch) regs_dec<RG::cons>();
+        if constexpr (RG::split && RG::cons > RG::launch) regs_inc<RG::cons>();
         float* __restrict__ fo = A.fout + S.pop_offset;
         const int64_t step = *A.step_ptr + A.k;
         const SysPhys<float> P = A.phys[tl.x];

@@ -5,7 +5,7 @@
 // multiple of 64) and walks YC rows; lane l holds the sites x0 + 2l and
 // x0 + 2l + 1 as one float2.  Per footprint row yy each lane loads, for every
 // population, the aligned pair of its own two columns at the pulled row
-// (one 8-byte load); the pull's x shift of -c_x is done in registers: the
+// (one 8-byte load, issued one row ahead); the pull's x shift of -c_x is done in registers: the
 // column left of the pair comes from the previous lane by a warp shuffle, the
 // column right of it from the next lane.  Lanes 0 and 31 also load the pair
 // just outside the strip (columns x0 - 2, x0 - 1 and x0 + 64, x0 + 65) for the
@@ -79,18 +79,42 @@ __global__ void __launch_bounds__(32 * WPC, MINB)
     const NoiseKey key = noise_key(S, *A.step_ptr + A.k);
     const int y0 = tl.z, y1 = min(y0 + YC, ny);
 
+    // pulled rows yy - c_y for c_y = -1, 0, 1 (index 1 + c_y), as offsets
+    auto rows_of = [&](int yy, int (&ro)[3]) {
+        ro[0] = (sm ? wrapm(yy + 1, ny) : wrap2(yy + 1, ny)) * nx;
+        ro[1] = (sm ? wrapm(yy, ny) : wrap2(yy, ny)) * nx;
+        ro[2] = (sm ? wrapm(yy - 1, ny) : wrap2(yy - 1, ny)) * nx;
+    };
+    // the loads of row yy + 1 (the lane's pairs and, on lanes 0 and 31, the pair
+    // outside the strip) are issued before row yy is summed and row yy - 1
+    // collided, so they are in flight across that work
+    float2 sn[9], tn[9];
+    auto load_row = [&](int yy) {
+        int ro[3];
+        rows_of(yy, ro);
+        sfor<0, 9>([&](auto I) {
+            constexpr int i = I;
+            sn[i] = *reinterpret_cast<const float2*>(fb + i * N + ro[1 + L::c(i, 1)] + xs);
+        });
+        if (edge) {
+            sfor<0, 9>([&](auto I) {
+                constexpr int i = I;
+                tn[i] = *reinterpret_cast<const float2*>(fb + i * N + ro[1 + L::c(i, 1)] + xt);
+            });
+        }
+    };
+    sfor<0, 9>([&](auto I) { tn[decltype(I)::value] = make_float2(0.f, 0.f); });
+    load_row(y0 - 1);
+
     float2 pr = make_float2(0.f, 0.f), pjx = pr, pjy = pr;        // (drho, j) of row yy - 1
     PairRow Rm{0.f, pr, 0.f}, R0 = Rm, Rp = Rm;                  // density rows yy - 2, yy - 1, yy
     for (int yy = y0 - 1; yy <= y1; ++yy) {
-        // pulled rows yy - c_y for c_y = -1, 0, 1 (index 1 + c_y)
-        const int ro[3] = {(sm ? wrapm(yy + 1, ny) : wrap2(yy + 1, ny)) * nx,
-                           (sm ? wrapm(yy, ny) : wrap2(yy, ny)) * nx,
-                           (sm ? wrapm(yy - 1, ny) : wrap2(yy - 1, ny)) * nx};
-        float2 s[9];
+        float2 s[9], tt[9];
         sfor<0, 9>([&](auto I) {
-            constexpr int i = I;
-            s[i] = *reinterpret_cast<const float2*>(fb + i * N + ro[1 + L::c(i, 1)] + xs);
+            s[decltype(I)::value] = sn[decltype(I)::value];
+            tt[decltype(I)::value] = tn[decltype(I)::value];
         });
+        if (yy < y1) load_row(yy + 1);
         // edge lanes: the outermost shifted values e (lane 0: column x0 - 1 of the
         // populations with c_x = +1; lane 31: column x0 + 64 of those with c_x = -1)
         // and the density of the halo site (x0 - 1 or x0 + 64)
@@ -100,7 +124,7 @@ __global__ void __launch_bounds__(32 * WPC, MINB)
             sfor<0, 9>([&](auto I) {
                 constexpr int i = I;
                 constexpr int cx = L::c(i, 0);
-                const float2 t = *reinterpret_cast<const float2*>(fb + i * N + ro[1 + L::c(i, 1)] + xt);
+                const float2 t = tt[i];
                 float h;
                 if constexpr (cx == 1) h = left ? t.x : s[i].y;
                 else if constexpr (cx == 0) h = left ? t.y : t.x;

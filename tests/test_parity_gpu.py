@@ -584,6 +584,28 @@ def test_d2q9_strips_and_tiles_on_odd_and_tiny_shapes(lb, tau):
             assert all(np.array_equal(a, b) for a, b in zip(runs[0], r))
 
 
+def test_default_z_chunk_adapts_to_the_ensemble(lb):
+    """With no variant, tile or occupancy given, the default D3Q19 kernel takes
+    the longer z-chunk only when the ensemble keeps at least two waves of
+    resident CTAs (row 1 differs from row 0 only in the chunk)."""
+    import torch
+    rows = lb.kernel_variants("D3Q19")
+    assert rows[1][2] > rows[0][2] and rows[1][:2] == rows[0][:2] and rows[1][3:] == rows[0][3:]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    few = [synth.system("D3Q19", "guo", n=64, seed=1 + k, system_id=k) for k in range(32)]
+    many = [synth.system("D3Q19", "guo", n=32, seed=1 + k, system_id=k) for k in range(8 * sms // 4 + 4)]
+    for systems, want in ((few, 0), (many, 1)):
+        tiles = sum(-(-s["nx"] // rows[1][0]) * -(-s["ny"] // rows[1][1]) * -(-s["nz"] // rows[1][2])
+                    for s in systems)
+        assert (tiles >= 2 * rows[1][3] * sms) == (want == 1)
+        e = lb.Ensemble(systems, precision="fp32")
+        assert e.kernel_variant() == want
+        e.close()
+        e = lb.Ensemble(systems, precision="fp32", variant=1)
+        assert e.kernel_variant() == 0
+        e.close()
+
+
 def test_d2q9_paired_strips_on_even_shapes(lb):
     """The two-site row strips (lane pairs of x-adjacent sites, paired FP32,
     64-site strips) run when every nx is a multiple of 4 and every mode is at
