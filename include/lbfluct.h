@@ -67,7 +67,7 @@ typedef enum {
 enum { LB_D2Q9 = 0, LB_D3Q19 = 1 };
 enum { LB_MODEQ = 0, LB_GUO = 1 };
 enum { LB_FP64 = 0, LB_FP32_DEVIATION = 1 };
-enum { LB_INIT_UNIFORM_NOISE = 0, LB_INIT_FROM_RHO = 1, LB_INIT_TANH_STRIPE = 2 };
+enum { LB_INIT_UNIFORM_NOISE = 0, LB_INIT_FROM_RHO = 1, LB_INIT_TANH_STRIPE = 2, LB_INIT_FROM_DEVICE_RHO = 3 };
 #define LB_MAX_Q 19
 #define LB_MAX_LEVELS 32
 
@@ -176,7 +176,12 @@ lb_status lb_create(const lb_system_desc* systems, int n_systems, const lb_run_o
  *   LB_INIT_FROM_RHO       rho from h_rho: float64, all systems concatenated in
  *                          descriptor order, each [nz][ny][nx];
  *   LB_INIT_TANH_STRIPE    the two-interface mean-field stripe of
- *                          lb_stripe_density (h_rho and amplitude unused).
+ *                          lb_stripe_density (h_rho and amplitude unused);
+ *   LB_INIT_FROM_DEVICE_RHO  as LB_INIT_FROM_RHO with h_rho a device pointer
+ *                          (caller-owned, read in stream order on the
+ *                          context's stream), so that a caller can stage the
+ *                          next input on another stream while the context
+ *                          steps.
  * Clears observables and the sticky error.  Synchronises the stream.
  * Errors: LB_ERR_ARG (mode, missing h_rho, a stripe for a system without
  * a < 0 < b), LB_ERR_CUDA. */

@@ -28,7 +28,7 @@ LB_ERR_UNSUPPORTED, LB_ERR_STATE, LB_ERR_IO, LB_ERR_NO_ROOT, LB_ERR_TIMEOUT = -7
 LB_D2Q9, LB_D3Q19 = 0, 1
 LB_MODEQ, LB_GUO = 0, 1
 LB_FP64, LB_FP32_DEVIATION = 0, 1
-LB_INIT_UNIFORM_NOISE, LB_INIT_FROM_RHO, LB_INIT_TANH_STRIPE = 0, 1, 2
+LB_INIT_UNIFORM_NOISE, LB_INIT_FROM_RHO, LB_INIT_TANH_STRIPE, LB_INIT_FROM_DEVICE_RHO = 0, 1, 2, 3
 LB_MAX_Q = 19
 LB_MAX_LEVELS = 32
 LB_MAX_HIST_BINS = 4096
@@ -271,6 +271,7 @@ class Ensemble:
         self.systems = [dict(s) for s in systems]
         self.q = 9 if self.systems[0]["lattice"] in ("D2Q9", LB_D2Q9) else 19
         self._desc = make_desc(self.systems)
+        self.n_sites = sum(int(s["nx"]) * int(s["ny"]) * int(s["nz"]) for s in self.systems)
         self._opts = make_opts(**opts)
         n = ctypes.c_size_t()
         check(lb_workspace_bytes(self._desc, len(systems), ctypes.byref(self._opts), ctypes.byref(n)),
@@ -289,12 +290,22 @@ class Ensemble:
         s = self.systems[k]
         return (int(s["nz"]), int(s["ny"]), int(s["nx"]))
 
-    def init(self, mode=LB_INIT_UNIFORM_NOISE, amplitude=0.01, rho=None):
+    def init(self, mode=LB_INIT_UNIFORM_NOISE, amplitude=0.01, rho=None, rho_device=None):
+        """rho: host densities (numpy, float64, systems concatenated); rho_device:
+        the same as a contiguous float64 CUDA tensor, read on the context's stream."""
         ptr = None
         if rho is not None:
             self._rho = np.ascontiguousarray(rho, dtype=np.float64)
             ptr = self._rho.ctypes.data_as(_P)
             mode = LB_INIT_FROM_RHO
+        elif rho_device is not None:
+            import torch
+            if rho_device.dtype != torch.float64 or not rho_device.is_cuda or not rho_device.is_contiguous():
+                raise ValueError("rho_device: a contiguous float64 CUDA tensor")
+            if rho_device.numel() != self.n_sites:
+                raise ValueError("rho_device: %d values for %d sites" % (rho_device.numel(), self.n_sites))
+            ptr = _P(rho_device.data_ptr())
+            mode = LB_INIT_FROM_DEVICE_RHO
         check(lb_init(self.ctx, mode, float(amplitude), ptr), "lb_init")
 
     def step(self, n):

@@ -935,8 +935,10 @@ lb_status lb_stripe_density(const lb_system_desc* s, int n, double* out) {
 
 lb_status lb_init(lb_ctx* c, int mode, double amplitude, const double* h_rho) {
     if (!c) return LB_ERR_ARG;
-    if (mode != LB_INIT_UNIFORM_NOISE && mode != LB_INIT_FROM_RHO && mode != LB_INIT_TANH_STRIPE) return LB_ERR_ARG;
-    if (mode == LB_INIT_FROM_RHO && !h_rho) return LB_ERR_ARG;
+    if (mode != LB_INIT_UNIFORM_NOISE && mode != LB_INIT_FROM_RHO && mode != LB_INIT_TANH_STRIPE &&
+        mode != LB_INIT_FROM_DEVICE_RHO)
+        return LB_ERR_ARG;
+    if ((mode == LB_INIT_FROM_RHO || mode == LB_INIT_FROM_DEVICE_RHO) && !h_rho) return LB_ERR_ARG;
     std::vector<double> stripe;
     if (mode == LB_INIT_TANH_STRIPE) {
         std::vector<lb_system_desc> desc;
@@ -963,7 +965,8 @@ lb_status lb_init(lb_ctx* c, int mode, double amplitude, const double* h_rho) {
         LB_CHECK(launch_obs_globals(sys, c->n_sys, c->at<double>(P.red4), c->at<double>(P.dbar),
                                     c->at<double>(P.glob), 1, 0, c->stream));
     } else {
-        LB_CHECK(cudaMemcpyAsync(c->at<double>(P.d), h_rho, sizeof(double) * P.n_sites, cudaMemcpyHostToDevice,
+        LB_CHECK(cudaMemcpyAsync(c->at<double>(P.d), h_rho, sizeof(double) * P.n_sites,
+                                 mode == LB_INIT_FROM_DEVICE_RHO ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                  c->stream));
         LB_CHECK(launch_set_dbar(sys, c->n_sys, c->at<double>(P.dbar), c->stream));
     }

@@ -21,7 +21,8 @@ namespace {
 // ensembles with an odd nx run the one-site warp-specialised kernel of the
 // same tile).  The first entry is the default.
 constexpr int kTiles[][kVariantCols] = {
-    {32, 8, 32, 3, 4, 3, 2}, {32, 8, 64, 3, 4, 3, 2}, {16, 16, 32, 3, 4, 3, 2}, {32, 8, 32, 2, 4, 0, 2}, {16, 16, 32, 2, 4, 0, 2},
+    {32, 8, 32, 3, 4, 3, 2}, {32, 8, 64, 3, 4, 3, 2}, {16, 16, 32, 3, 4, 3, 2}, {16, 16, 64, 3, 4, 3, 2},
+    {32, 8, 32, 2, 4, 0, 2}, {16, 16, 32, 2, 4, 0, 2},
     {32, 8, 64, 2, 4, 0, 2}, {16, 8, 32, 3, 4, 0, 1},  {16, 8, 64, 3, 4, 0, 1},  {16, 8, 16, 3, 4, 0, 1},
     {16, 8, 32, 3, 4, 1, 1}, {16, 8, 16, 6, 0, 0, 1},  {16, 8, 32, 6, 0, 0, 1},  {16, 16, 16, 4, 0, 0, 1},
     {16, 16, 32, 4, 0, 0, 1}};

@@ -63,11 +63,12 @@ __global__ void __launch_bounds__(AUX_THREADS)
         if (site >= it.z) break;
         int x, y, z;
         site_coords(site, nx, ny, x, y, z);
-        auto nb = [&](int i) {
-            const int sx = wrapm(x + L::c(i, 0), nx), sy = wrapm(y + L::c(i, 1), ny);
-            const int sz = L::D == 3 ? wrapm(z + L::c(i, 2), nz) : 0;
-            return ds[sx + nx * (sy + ny * sz)] - db;
-        };
+        // wrapped neighbour coordinates x + d (d = -1, 0, 1) and their offsets
+        const int X[3] = {wrap1(x - 1, nx), x, wrap1(x + 1, nx)};
+        const int Y[3] = {wrap1(y - 1, ny) * nx, y * nx, wrap1(y + 1, ny) * nx};
+        const int Z[3] = {L::D == 3 ? wrap1(z - 1, nz) * nx * ny : 0, z * nx * ny,
+                          L::D == 3 ? wrap1(z + 1, nz) * nx * ny : 0};
+        auto nb = [&](int i) { return ds[X[1 + L::c(i, 0)] + Y[1 + L::c(i, 1)] + Z[1 + L::c(i, 2)]] - db; };
         const double drho = ds[site] - db;
         const double rho = S.rho_c + drho;
         const double phi = drho * S.inv_rho_c;
@@ -120,11 +121,9 @@ __global__ void __launch_bounds__(AUX_THREADS)
         }
         feq[0] = drho - s;
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-            const int sx = wrapm(x - L::c(i, 0), nx), sy = wrapm(y - L::c(i, 1), ny);
-            const int sz = L::D == 3 ? wrapm(z - L::c(i, 2), nz) : 0;
-            fbuf[S.pop_offset + int64_t(i) * N + (sx + nx * (sy + ny * sz))] = Real(feq[i]);
-        }
+        for (int i = 0; i < L::Q; ++i)
+            fbuf[S.pop_offset + int64_t(i) * N + (X[1 - L::c(i, 0)] + Y[1 - L::c(i, 1)] + Z[1 - L::c(i, 2)])] =
+                Real(feq[i]);
     }
 }
 

@@ -197,19 +197,23 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
         const int pl = nx * ny;
         const bool sm = S.small != 0;
         // the loads of plane zz + 1 are issued as soon as plane zz has been
-        // summed (and, staged, its density stored: every staged value has been
-        // read back before the copies that overwrite it are issued), so they
-        // are in flight across the barrier and the Laplacian
+        // summed (staged by cp.async: direction by direction, each right after
+        // the staged value it overwrites has been read back and used), so they
+        // are in flight across the sums, the barrier and the Laplacian
         constexpr bool CPA = STG == 3;                   // staged by cp.async
         float4 g[CPA ? 1 : 19];
         float4* const stage = reinterpret_cast<float4*>(ring + R * PLANE) + ptid;   // [19][NP], this lane's column
         if constexpr (!CPA)
             sfor<0, 19>([&](auto I) { g[decltype(I)::value] = make_float4(0.0f, 0.0f, 0.0f, 0.0f); });
+        // source planes z - c_z for c_z = -1, 0, +1 of plane zz
+        auto planes_of = [&](int zz, int (&zo)[3]) {
+            zo[0] = (sm ? wrapm(zz + 1, nz) : wrap2(zz + 1, nz)) * pl;
+            zo[1] = (sm ? wrapm(zz, nz) : wrap2(zz, nz)) * pl;
+            zo[2] = (sm ? wrapm(zz - 1, nz) : wrap2(zz - 1, nz)) * pl;
+        };
         auto pull = [&](int zz) {
-            // source planes z - c_z for c_z = -1, 0, +1
-            const int zo[3] = {(sm ? wrapm(zz + 1, nz) : wrap2(zz + 1, nz)) * pl,
-                               (sm ? wrapm(zz, nz) : wrap2(zz, nz)) * pl,
-                               (sm ? wrapm(zz - 1, nz) : wrap2(zz - 1, nz)) * pl};
+            int zo[3];
+            planes_of(zz, zo);
             if (act) {
                 sfor<0, 19>([&](auto I) {
                     constexpr int i = I;
@@ -235,6 +239,9 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
             // the neighbouring lane.  Density and momentum are summed in the
             // order of the one-site kernels (from 0, direction by direction).
             if constexpr (CPA) cp_async_wait_all();      // this lane's copies of plane zz have landed
+            const bool more = zz + 1 < z1 + H;
+            int zn[3];
+            planes_of(zz + 1, zn);
             float2 r01 = make_float2(0.0f, 0.0f), r23 = r01;
             float2 j01[3] = {r01, r01, r01}, j23[3] = {r01, r01, r01};
             sfor<0, 19>([&](auto I) {
@@ -256,6 +263,11 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
                 }
                 r01 = vadd(r01, a01);
                 r23 = vadd(r23, a23);
+                if constexpr (CPA) {
+                    // v has been used, so the read of this staged slot is complete
+                    constexpr int cy = L::c(i, 1), cz = L::c(i, 2);
+                    if (more && act) cp_async16(stage + i * NP, rowp[1 + cy] + (i * N + zn[1 + cz]));
+                }
                 if constexpr (i > 0) {
                     if (tile) {
                         sfor<0, 3>([&](auto C) {
@@ -280,7 +292,11 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
                     *reinterpret_cast<float2*>(rp + jdst + 6 + 2 * c) = j23[c];
                 });
             }
-            if (zz + 1 < z1 + H) pull(zz + 1);
+            if constexpr (CPA) {
+                if (more) cp_async_commit();
+            } else {
+                if (more) pull(zz + 1);
+            }
             named_barrier(1, NP);                        // density plane zz complete (producers)
             const int zl = zz - 1;                       // Laplacian plane (needs density zl-1 .. zl+1)
             if (zl >= z0 - 1) {
@@ -289,7 +305,18 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
                 float* lo = ring + slot(zl) * PLANE + LY_::O_LO;
                 float* le = ring + slot(zl) * PLANE + LY_::O_LE;
                 for (int lq = ptid; lq < LY_::NLP; lq += NP) {
-                    const int lpx = 2 * (lq % LX2), lpy = lq / LX2;
+                    // with 16 pairs per tile row a half warp takes one Laplacian row
+                    // (conflict-free 64-bit shared loads) and the last pair of every
+                    // row comes after all rows
+                    int lpx, lpy;
+                    if constexpr (NPR == 16) {
+                        constexpr int MAIN = 16 * LY_::LY;
+                        lpy = lq < MAIN ? lq >> 4 : lq - MAIN;
+                        lpx = lq < MAIN ? 2 * (lq & 15) : 32;
+                    } else {
+                        lpx = 2 * (lq % LX2);
+                        lpy = lq / LX2;
+                    }
                     // Laplacian column lpx <-> footprint column lpx + 3, row lpy <-> lpy + 1
                     rv.c = (lpy + 1) * SXP + lpx + 2;
                     const float2 lap = lap_d3q19<float2>(rv);

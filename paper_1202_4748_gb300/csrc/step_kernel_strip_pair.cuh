@@ -85,10 +85,15 @@ __global__ void __launch_bounds__(32 * WPC, MINB)
         ro[1] = (sm ? wrapm(yy, ny) : wrap2(yy, ny)) * nx;
         ro[2] = (sm ? wrapm(yy - 1, ny) : wrap2(yy - 1, ny)) * nx;
     };
-    // the loads of row yy + 1 (the lane's pairs and, on lanes 0 and 31, the pair
-    // outside the strip) are issued before row yy is summed and row yy - 1
-    // collided, so they are in flight across that work
-    float2 sn[9], tn[9];
+    // the loads of row yy + 1 (the lane's pairs and, on lanes 0 and 31, the
+    // values outside the strip) are issued before row yy is summed and row
+    // yy - 1 collided, so they are in flight across that work.  Outside the
+    // strip lane 0 needs columns x0 - 2, x0 - 1 of the populations with
+    // c_x = +1 (1, 5, 7) and column x0 - 1 of those with c_x = 0 (0, 3, 4);
+    // lane 31 columns x0 + 64, x0 + 65 of those with c_x = -1 (2, 6, 8) and
+    // column x0 + 64 of those with c_x = 0.
+    float2 sn[9], ewn[3];
+    float ezn[3];
     auto load_row = [&](int yy) {
         int ro[3];
         rows_of(yy, ro);
@@ -97,55 +102,64 @@ __global__ void __launch_bounds__(32 * WPC, MINB)
             sn[i] = *reinterpret_cast<const float2*>(fb + i * N + ro[1 + L::c(i, 1)] + xs);
         });
         if (edge) {
-            sfor<0, 9>([&](auto I) {
-                constexpr int i = I;
-                tn[i] = *reinterpret_cast<const float2*>(fb + i * N + ro[1 + L::c(i, 1)] + xt);
+            sfor<0, 3>([&](auto K) {
+                constexpr int k = K;
+                constexpr int ip = k == 0 ? 1 : (k == 1 ? 5 : 7), im = ip + 1;   // c_x = +1 and -1 of group k
+                const int i = left ? ip : im;
+                const int r = left ? ro[1 + L::c(ip, 1)] : ro[1 + L::c(im, 1)];
+                ewn[k] = *reinterpret_cast<const float2*>(fb + i * N + r + xt);
+                constexpr int i0 = k == 0 ? 0 : (k == 1 ? 3 : 4);                 // the c_x = 0 populations
+                ezn[k] = fb[i0 * N + ro[1 + L::c(i0, 1)] + xt + (left ? 1 : 0)];
             });
         }
     };
-    sfor<0, 9>([&](auto I) { tn[decltype(I)::value] = make_float2(0.f, 0.f); });
+    sfor<0, 3>([&](auto K) {
+        ewn[decltype(K)::value] = make_float2(0.f, 0.f);
+        ezn[decltype(K)::value] = 0.f;
+    });
     load_row(y0 - 1);
 
     float2 pr = make_float2(0.f, 0.f), pjx = pr, pjy = pr;        // (drho, j) of row yy - 1
     PairRow Rm{0.f, pr, 0.f}, R0 = Rm, Rp = Rm;                  // density rows yy - 2, yy - 1, yy
     for (int yy = y0 - 1; yy <= y1; ++yy) {
-        float2 s[9], tt[9];
-        sfor<0, 9>([&](auto I) {
-            s[decltype(I)::value] = sn[decltype(I)::value];
-            tt[decltype(I)::value] = tn[decltype(I)::value];
+        float2 s[9], ew[3];
+        float ez[3];
+        sfor<0, 9>([&](auto I) { s[decltype(I)::value] = sn[decltype(I)::value]; });
+        sfor<0, 3>([&](auto K) {
+            ew[decltype(K)::value] = ewn[decltype(K)::value];
+            ez[decltype(K)::value] = ezn[decltype(K)::value];
         });
         if (yy < y1) load_row(yy + 1);
         // edge lanes: the outermost shifted values e (lane 0: column x0 - 1 of the
         // populations with c_x = +1; lane 31: column x0 + 64 of those with c_x = -1)
-        // and the density of the halo site (x0 - 1 or x0 + 64)
+        // and the density of the halo site (x0 - 1 or x0 + 64), summed in
+        // population order
         float rh = 0.f, e[3] = {0.f, 0.f, 0.f};
         if (edge) {
             float v = 0.f;
             sfor<0, 9>([&](auto I) {
                 constexpr int i = I;
                 constexpr int cx = L::c(i, 0);
-                const float2 t = tt[i];
+                constexpr int k = (i == 1 || i == 2) ? 0 : ((i == 5 || i == 6) ? 1 : 2);   // x-pair group
+                constexpr int m = i == 0 ? 0 : (i == 3 ? 1 : 2);                            // c_x = 0 slot
                 float h;
-                if constexpr (cx == 1) h = left ? t.x : s[i].y;
-                else if constexpr (cx == 0) h = left ? t.y : t.x;
-                else h = left ? s[i].x : t.y;
+                if constexpr (cx == 1) h = left ? ew[k].x : s[i].y;
+                else if constexpr (cx == 0) h = ez[m];
+                else h = left ? s[i].x : ew[k].y;
                 v = vadd(v, h);
-                // pairs of opposite x velocities (1, 2), (5, 6), (7, 8) share the slot of e
-                constexpr int ke = (i == 1 || i == 2) ? 0 : ((i == 5 || i == 6) ? 1 : 2);
-                if constexpr (cx == 1) {
-                    if (left) e[ke] = t.y;
-                } else if constexpr (cx == -1) {
-                    if (!left) e[ke] = t.x;
-                }
             });
             rh = v;
+            sfor<0, 3>([&](auto K) {
+                constexpr int k = K;
+                e[k] = left ? ew[k].y : ew[k].x;
+            });
         }
         // the pull's x shift: f_i(x) = s_i(x - c_x)
         float2 g[9];
         sfor<0, 9>([&](auto I) {
             constexpr int i = I;
             constexpr int cx = L::c(i, 0);
-            constexpr int ke = (i == 1 || i == 2) ? 0 : ((i == 5 || i == 6) ? 1 : 2);
+            constexpr int ke = (i == 1 || i == 2) ? 0 : ((i == 5 || i == 6) ? 1 : 2);   // x-pair group
             if constexpr (cx == 0) {
                 g[i] = s[i];
             } else if constexpr (cx == 1) {

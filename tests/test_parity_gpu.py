@@ -584,6 +584,27 @@ def test_d2q9_strips_and_tiles_on_odd_and_tiny_shapes(lb, tau):
             assert all(np.array_equal(a, b) for a, b in zip(runs[0], r))
 
 
+def test_init_from_device_density_equals_host_density(lb):
+    """LB_INIT_FROM_DEVICE_RHO reads the same float64 densities from device
+    memory (stream-ordered) and gives the bits of LB_INIT_FROM_RHO."""
+    import torch
+    systems = [synth.system("D3Q19", "guo", n=n, seed=3 + k, system_id=k) for k, n in enumerate((12, 16))]
+    rho = np.concatenate([synth.random_density((s["nz"], s["ny"], s["nx"]), seed=9 + k).ravel()
+                          for k, s in enumerate(systems)])
+    a = lb.Ensemble(systems, precision="fp32")
+    a.init(rho=rho)
+    a.step(3)
+    b = lb.Ensemble(systems, precision="fp32")
+    b.init(rho_device=torch.from_numpy(rho).cuda())
+    b.step(3)
+    for k in range(len(systems)):
+        assert np.array_equal(a.read_fields(k), b.read_fields(k))
+    with pytest.raises(ValueError):
+        b.init(rho_device=torch.from_numpy(rho[:-1]).cuda())
+    a.close()
+    b.close()
+
+
 def test_default_z_chunk_adapts_to_the_ensemble(lb):
     """With no variant, tile or occupancy given, the default D3Q19 kernel takes
     the longer z-chunk only when the ensemble keeps at least two waves of
