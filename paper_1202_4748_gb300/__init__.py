@@ -333,8 +333,10 @@ class Ensemble:
                     momentum=tuple(g.momentum), rho_mean=g.rho_mean)
         return levels, glob
 
-    def observables_all(self):
-        """[(levels, global)] for every system, read with one copy and one synchronisation."""
+    def observables_all_raw(self):
+        """The lb_obs_level / lb_obs_global records of every system, read with one
+        copy and one synchronisation: (levels, first, globals) as ctypes arrays,
+        levels[first[k]:first[k + 1]] belonging to system k."""
         n = len(self.systems)
         first = (ctypes.c_int * (n + 1))()
         check(lb_observables_all(self.ctx, None, 0, first, None), "lb_observables_all")
@@ -342,6 +344,13 @@ class Ensemble:
         lv = (lb_obs_level * max(total, 1))()
         gl = (lb_obs_global * n)()
         check(lb_observables_all(self.ctx, lv, total, first, gl), "lb_observables_all")
+        return lv, first, gl
+
+    def observables_all(self, raw=None):
+        """[(levels, global)] for every system (from observables_all_raw, or a
+        record of it taken earlier)."""
+        n = len(self.systems)
+        lv, first, gl = raw if raw is not None else self.observables_all_raw()
         out = []
         for k in range(n):
             levels = []

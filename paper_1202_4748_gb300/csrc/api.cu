@@ -952,7 +952,10 @@ lb_status lb_init(lb_ctx* c, int mode, double amplitude, const double* h_rho) {
     if (mode == LB_INIT_UNIFORM_NOISE && !(amplitude >= 0 && std::isfinite(amplitude))) return LB_ERR_ARG;
     const Plan& P = c->P;
     const SysDev* sys = c->at<SysDev>(P.sys);
-    drop_graphs(c);
+    // the cached step graphs stay valid: they read the step counter on the
+    // device and address only the context's fixed workspace regions, and a
+    // chunk's schedule of observable passes depends on the step only modulo
+    // the chunk length
     c->step = 0;
     LB_CHECK(cudaMemsetAsync(c->ws + P.step, 0, sizeof(int64_t), c->stream));
     if (reset_accumulators(c) != LB_OK) return LB_ERR_CUDA;

@@ -344,6 +344,11 @@ def test_graph_replay_equals_plain_launches_and_is_deterministic(lb):
         e.step(3)        # unaligned start: plain launches to the chunk boundary
         e.step(37)
         runs.append(([e.read_fields(k) for k in range(len(systems))], e.observables(2)))
+        if chunk:        # a new start on the same context replays the graphs it has cached
+            e.init()
+            e.step(3)
+            e.step(37)
+            runs.append(([e.read_fields(k) for k in range(len(systems))], e.observables(2)))
         e.close()
     for r in runs[1:]:
         assert all(np.array_equal(a, b) for a, b in zip(runs[0][0], r[0]))
