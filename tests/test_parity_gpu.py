@@ -253,6 +253,37 @@ def test_large_256_sampled_parity_and_observables(lb):
     ens.close()
 
 
+def test_large_256_d2q9_sampled_parity(lb):
+    """The one-system 4096^2 D2Q9 FP32 workload (the paper's lattice, modified
+    equilibrium) in the benchmark's launch configuration (the paired row
+    strips): after one step, sampled sites on the corners, the edges, the
+    strip seams (x = 63, 64, 4095) and the interior match the oracle's update
+    of each site from the same state (its radius-3 cut-out, noise keyed by the
+    global site index)."""
+    s = synth.ensemble("large_256", "D2Q9")[0]
+    p = params_of(s)
+    n = p.nx
+    ens = lb.Ensemble([s], precision="fp32", graph_chunk=0)
+    assert lb.kernel_variants("D2Q9")[ens.kernel_variant()][6] == 2
+    ens.init(amplitude=0.01)
+    before = ens.read_fields(0)
+    ens.step(1)
+    ens.sync()
+    after = ens.read_fields(0)
+    ens.close()
+    fmax = np.abs(before).max()
+    c = p.lat.c
+    picks = [(0, 0), (n - 1, n - 1), (63, 31), (64, 32), (4095, 17), (0, 4095), (2048, 2047), (127, 1000),
+             (128, 33), (3001, 64)]
+    for (x, y) in picks:
+        ix, iy = [(np.arange(-3, 4) + v) % n for v in (x, y)]
+        blk = before[:, :1][:, :, iy][:, :, :, ix]
+        gid = iy[:, None] * n + ix[None, :]
+        fs = lbm.collide(blk, 0, dataclasses.replace(p, nx=7, ny=7, nz=1), sites=gid.ravel())
+        want = np.array([fs[i, 0, 3 - c[i, 1], 3 - c[i, 0]] for i in range(p.lat.q)])
+        assert np.abs(after[:, 0, y, x] - want).max() < TOL32 * fmax, (x, y)
+
+
 @pytest.mark.parametrize("lattice,coupling", [("D2Q9", "modeq"), ("D3Q19", "guo")])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_tanh_stripe_init_is_the_stripe_density(lb, lattice, coupling, precision):
