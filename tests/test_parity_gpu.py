@@ -315,6 +315,35 @@ def test_tanh_stripe_init_is_the_stripe_density(lb, lattice, coupling, precision
     eb.close()
 
 
+@pytest.mark.parametrize("lattice,coupling", [("D2Q9", "modeq"), ("D3Q19", "guo"), ("D3Q19", "modeq")])
+def test_fp32_default_kernels_report_device_errors(lb, lattice, coupling):
+    """The FP32 default kernels (paired strips on D2Q9, the paired warp-specialised
+    kernel on D3Q19, the radius-1 kernel of the D3Q19 modified equilibrium) set
+    the status bits themselves: a non-positive density and an indefinite noise
+    covariance (c_s^2 = rho a = 0.7) are reported by lb_sync."""
+    nz = 1 if lattice == "D2Q9" else 16
+    q = 9 if lattice == "D2Q9" else 19
+    s = _sys(lattice, coupling, 16, 16, nz, kT=1e-4, tau=[1.0] * q)
+    p = params_of(s)
+    f = lbm.equilibrium_at_rest(np.ones(p.shape), p)
+    f[0, 0, 5, 6] = -5.0
+    ens = lb.Ensemble([s], precision="fp32")
+    ens.write_fields(0, f)
+    ens.step(1)
+    with pytest.raises(lb.LBError) as e:
+        ens.sync()
+    assert e.value.status == lb.LB_ERR_NONPOSITIVE_DENSITY
+    ens.close()
+    s2 = _sys(lattice, coupling, 16, 16, nz, a=0.7, b=0.0, kT=1e-4, tau=[1.0] * q)
+    ens = lb.Ensemble([s2], precision="fp32")
+    ens.init(amplitude=0.0)
+    ens.step(1)
+    with pytest.raises(lb.LBError) as e:
+        ens.sync()
+    assert e.value.status == lb.LB_ERR_NOISE_NOT_PD
+    ens.close()
+
+
 def test_errors_are_reported_and_sticky(lb):
     s = _sys("D2Q9", "modeq", 16, 16, kT=1e-4, tau=[1.0] * 9)
     p = params_of(s)
