@@ -43,6 +43,7 @@ WORKLOADS = {
     "fss_160_64": dict(ensemble="fss_160_64", lattice="D3Q19", precision="fp32"),
     "fss_60": dict(ensemble="fss_60", lattice="D3Q19", precision="fp32"),
     "fss_160_64_fp64": dict(ensemble="fss_160_64", lattice="D3Q19", precision="fp64"),
+    "fss_160_modeq": dict(ensemble="fss_160", lattice="D3Q19", precision="fp32", coupling="modeq"),
 }
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
@@ -150,7 +151,7 @@ def bounded_system(s):
 def oracle_sample_systems(wl):
     """One system per size class of the workload (the bounded CPU sample)."""
     import synth
-    systems = synth.ensemble(wl["ensemble"], wl["lattice"])
+    systems = synth.ensemble(wl["ensemble"], wl["lattice"], wl.get("coupling"))
     seen, out = set(), []
     for s in systems:
         if s["nx"] not in seen:
@@ -211,7 +212,7 @@ def run_oracle_all_cores(wl, steps, warmup, nproc=None):
     import multiprocessing as mp
     import synth
     nproc = nproc or host_cores()
-    systems = synth.ensemble(wl["ensemble"], wl["lattice"])
+    systems = synth.ensemble(wl["ensemble"], wl["lattice"], wl.get("coupling"))
     picks = [systems[(k * len(systems)) // nproc] if len(systems) >= nproc else dict(systems[k % len(systems)],
              system_id=k) for k in range(nproc)]
     picks = [bounded_system(s) for s in picks]
@@ -312,7 +313,7 @@ def main():
     __graft_entry__.build()
     import paper_1202_4748_gb300 as lb
 
-    systems = synth.ensemble(wl["ensemble"], wl["lattice"])
+    systems = synth.ensemble(wl["ensemble"], wl["lattice"], wl.get("coupling"))
     all_systems = [dict(s) for s in systems]
     n_sys = len(systems)
     all_sites = synth.sites(systems)

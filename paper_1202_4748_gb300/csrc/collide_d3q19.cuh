@@ -189,63 +189,17 @@ __device__ __forceinline__ void grad_lap12_d3q19(const LapV& lv, V& gx, V& gy, V
     }
 }
 
-// f[i] <- post-collision deviations of the site(s) with density deviation
-// drho and momentum j = sum_i c_i f_i; lv views the Laplacian of the density
-// around the site(s).
-template <class V, class LapV>
-__device__ __forceinline__ void collide_d3q19_tau1(V (&f)[19], const V drho, const V jx, const V jy, const V jz,
-                                                   const LapV& lv, const SysPhys<typename VT<V>::S>& P,
-                                                   const NoiseKey& key, const typename SiteIdx<V>::type site,
-                                                   int* status) {
+// The part every fully relaxed D3Q19 collision shares: given h_a = w_a /
+// (36 N_a) of the equilibrium moments (h[0..9] and h[16]; h[10..15], h[17],
+// h[18] are set here), adds the noise of Eq. 68 in its lattice-general form
+// (rate 1 on every mode) and forms f_i = 36 t_i sum_a T_ai h_a.
+template <class V>
+__device__ __forceinline__ void d3q19_tau1_noise_and_populations(V (&h)[19], V (&f)[19], const V rho, const V cs2,
+                                                                 const SysPhys<typename VT<V>::S>& P,
+                                                                 const NoiseKey& key,
+                                                                 const typename SiteIdx<V>::type site, int* status) {
     using S = typename VT<V>::S;
     constexpr int W = VT<V>::W;
-    const V rho = vadd(vbc<V>(P.rho_c), drho);
-    bool bad_rho = false;
-#pragma unroll
-    for (int l = 0; l < W; ++l) bad_rho |= !(lane(rho, l) > S(0));
-    if (bad_rho) atomicOr(status, ST_RHO);
-
-    // thermodynamics (Eq. 3 and below Eq. 64), phi = drho / rho_c
-    const V phi = vmul(drho, vbc<V>(P.inv_rho_c));
-    const V phi2 = vmul(phi, phi);
-    const V df0 = vmul(phi, vfma(vbc<V>(P.b), phi2, vbc<V>(P.a)));
-    const V f0 = vmul(phi2, vfma(vbc<V>(S(0.25) * P.b), phi2, vbc<V>(S(0.5) * P.a)));
-    const V rr = vmul(rho, vbc<V>(P.inv_rho_c));
-    const V p0 = vsub(vmul(rr, df0), f0);
-    const V cs2 = vmul(vmul(rr, vbc<V>(P.inv_rho_c)), vfma(vbc<V>(S(3) * P.b), phi2, vbc<V>(P.a)));
-    const V iso = vfma(p0, vk<V>(-3.0), drho);
-
-    // Guo force F = kappa rho grad(lap rho); u = (j + F / 2) / rho
-    V gx, gy, gz;
-    grad_lap12_d3q19<V>(lv, gx, gy, gz);
-    const V kr = vmul(rho, vbc<V>(P.kappa * S(1.0 / 12.0)));
-    const V Fx = vmul(kr, gx), Fy = vmul(kr, gy), Fz = vmul(kr, gz);
-    const V ir = vmap(rho, [](S x) { return fast_rcp(x); });
-    const V ux = vmul(vfma(Fx, vk<V>(0.5), jx), ir);
-    const V uy = vmul(vfma(Fy, vk<V>(0.5), jy), ir);
-    const V uz = vmul(vfma(Fz, vk<V>(0.5), jz), ir);
-    // A_bc with V_b = rho u_b + F_b:  A_bb = u_b V_b,  2 A_bc = u_b V_c + u_c V_b
-    const V Vx = vfma(rho, ux, Fx), Vy = vfma(rho, uy, Fy), Vz = vfma(rho, uz, Fz);
-    const V Axx = vmul(ux, Vx), Ayy = vmul(uy, Vy), Azz = vmul(uz, Vz);
-    const V Axy2 = vfma(ux, Vy, vmul(uy, Vx));
-    const V Ayz2 = vfma(uy, Vz, vmul(uz, Vy));
-    const V Azx2 = vfma(uz, Vx, vmul(ux, Vz));
-    const V tr = vadd(vadd(Axx, Ayy), Azz);
-
-    // h_a = w_a / (36 N_a); N = (1, 1/3 x3, 2/3, 4/3, 4/9, 1/9 x3, 2/3 x3, 2/9 x3, 2, 4/3, 4/9)
-    V h[19];
-    h[0] = vmul(drho, vk<V>(1.0 / 36.0));
-    h[1] = vmul(vadd(jx, Fx), vk<V>(1.0 / 12.0));
-    h[2] = vmul(vadd(jy, Fy), vk<V>(1.0 / 12.0));
-    h[3] = vmul(vadd(jz, Fz), vk<V>(1.0 / 12.0));
-    h[4] = vmul(vsub(tr, iso), vk<V>(1.0 / 24.0));
-    h[5] = vmul(vfma(Axx, vk<V>(3.0), vsub(vk<V>(0.0), tr)), vk<V>(1.0 / 48.0));
-    h[6] = vmul(vsub(Ayy, Azz), vk<V>(1.0 / 16.0));
-    h[7] = vmul(Axy2, vk<V>(1.0 / 8.0));
-    h[8] = vmul(Ayz2, vk<V>(1.0 / 8.0));
-    h[9] = vmul(Azx2, vk<V>(1.0 / 8.0));
-    h[16] = vmul(iso, vk<V>(1.0 / 72.0));
-
     if (P.kT > S(0)) {
         // scale sqrt(3 rho kT) (Eq. 68 with Delta V = Delta t = 1) and the
         // Cholesky factor of the coupled pair (modes c^2 - 1, 3c^4 - 6c^2 + 1):
@@ -342,6 +296,156 @@ __device__ __forceinline__ void collide_d3q19_tau1(V (&f)[19], const V drho, con
         E = vadd(Byz, h[8]); O = vadd(Yp, Zm); f[15] = vadd(E, O); f[16] = vsub(E, O);
         E = vsub(Byz, h[8]); O = vsub(Yp, Zm); f[17] = vadd(E, O); f[18] = vsub(E, O);
     }
+}
+
+// f[i] <- post-collision deviations of the site(s) with density deviation
+// drho and momentum j = sum_i c_i f_i; lv views the Laplacian of the density
+// around the site(s).
+template <class V, class LapV>
+__device__ __forceinline__ void collide_d3q19_tau1(V (&f)[19], const V drho, const V jx, const V jy, const V jz,
+                                                   const LapV& lv, const SysPhys<typename VT<V>::S>& P,
+                                                   const NoiseKey& key, const typename SiteIdx<V>::type site,
+                                                   int* status) {
+    using S = typename VT<V>::S;
+    constexpr int W = VT<V>::W;
+    const V rho = vadd(vbc<V>(P.rho_c), drho);
+    bool bad_rho = false;
+#pragma unroll
+    for (int l = 0; l < W; ++l) bad_rho |= !(lane(rho, l) > S(0));
+    if (bad_rho) atomicOr(status, ST_RHO);
+
+    // thermodynamics (Eq. 3 and below Eq. 64), phi = drho / rho_c
+    const V phi = vmul(drho, vbc<V>(P.inv_rho_c));
+    const V phi2 = vmul(phi, phi);
+    const V df0 = vmul(phi, vfma(vbc<V>(P.b), phi2, vbc<V>(P.a)));
+    const V f0 = vmul(phi2, vfma(vbc<V>(S(0.25) * P.b), phi2, vbc<V>(S(0.5) * P.a)));
+    const V rr = vmul(rho, vbc<V>(P.inv_rho_c));
+    const V p0 = vsub(vmul(rr, df0), f0);
+    const V cs2 = vmul(vmul(rr, vbc<V>(P.inv_rho_c)), vfma(vbc<V>(S(3) * P.b), phi2, vbc<V>(P.a)));
+    const V iso = vfma(p0, vk<V>(-3.0), drho);
+
+    // Guo force F = kappa rho grad(lap rho); u = (j + F / 2) / rho
+    V gx, gy, gz;
+    grad_lap12_d3q19<V>(lv, gx, gy, gz);
+    const V kr = vmul(rho, vbc<V>(P.kappa * S(1.0 / 12.0)));
+    const V Fx = vmul(kr, gx), Fy = vmul(kr, gy), Fz = vmul(kr, gz);
+    const V ir = vmap(rho, [](S x) { return fast_rcp(x); });
+    const V ux = vmul(vfma(Fx, vk<V>(0.5), jx), ir);
+    const V uy = vmul(vfma(Fy, vk<V>(0.5), jy), ir);
+    const V uz = vmul(vfma(Fz, vk<V>(0.5), jz), ir);
+    // A_bc with V_b = rho u_b + F_b:  A_bb = u_b V_b,  2 A_bc = u_b V_c + u_c V_b
+    const V Vx = vfma(rho, ux, Fx), Vy = vfma(rho, uy, Fy), Vz = vfma(rho, uz, Fz);
+    const V Axx = vmul(ux, Vx), Ayy = vmul(uy, Vy), Azz = vmul(uz, Vz);
+    const V Axy2 = vfma(ux, Vy, vmul(uy, Vx));
+    const V Ayz2 = vfma(uy, Vz, vmul(uz, Vy));
+    const V Azx2 = vfma(uz, Vx, vmul(ux, Vz));
+    const V tr = vadd(vadd(Axx, Ayy), Azz);
+
+    // h_a = w_a / (36 N_a); N = (1, 1/3 x3, 2/3, 4/3, 4/9, 1/9 x3, 2/3 x3, 2/9 x3, 2, 4/3, 4/9)
+    V h[19];
+    h[0] = vmul(drho, vk<V>(1.0 / 36.0));
+    h[1] = vmul(vadd(jx, Fx), vk<V>(1.0 / 12.0));
+    h[2] = vmul(vadd(jy, Fy), vk<V>(1.0 / 12.0));
+    h[3] = vmul(vadd(jz, Fz), vk<V>(1.0 / 12.0));
+    h[4] = vmul(vsub(tr, iso), vk<V>(1.0 / 24.0));
+    h[5] = vmul(vfma(Axx, vk<V>(3.0), vsub(vk<V>(0.0), tr)), vk<V>(1.0 / 48.0));
+    h[6] = vmul(vsub(Ayy, Azz), vk<V>(1.0 / 16.0));
+    h[7] = vmul(Axy2, vk<V>(1.0 / 8.0));
+    h[8] = vmul(Ayz2, vk<V>(1.0 / 8.0));
+    h[9] = vmul(Azx2, vk<V>(1.0 / 8.0));
+    h[16] = vmul(iso, vk<V>(1.0 / 72.0));
+
+    d3q19_tau1_noise_and_populations<V>(h, f, rho, cs2, P, key, site, status);
+}
+
+// The modified equilibrium carried to D3Q19 (Eq. 65's structure with the
+// isotropic weights 3 t_i and the rotation-invariant square-gradient terms),
+// fully relaxed.  Its moments on this basis (deviation form) are
+//   m_0 = drho, m_a = j_a,
+//   m_4 = tr X + 3 iso - drho - (kappa/2)|g|^2,
+//   m_5 = 2 X_xx - X_yy - X_zz + kappa (2 g_x^2 - g_y^2 - g_z^2),
+//   m_6 = X_yy - X_zz + kappa (g_y^2 - g_z^2),
+//   m_7 = X_xy + kappa g_x g_y,  m_8 = X_yz + kappa g_y g_z,  m_9 = X_zx + kappa g_z g_x,
+//   m_16 = drho - (3 kappa/2)|g|^2 - 3 iso,  the third- and fourth-order ghosts 0,
+// with g = grad rho, iso = p0 - kappa rho lap rho and X_ab = rho u_a u_b +
+// nu (u_a g_b + u_b g_a + u.g delta_ab); rv.at<cx, cy, cz>() is the density
+// deviation at r + c.
+template <class V, class RhoV>
+__device__ __forceinline__ void collide_d3q19_modeq_tau1(V (&f)[19], const V drho, const V jx, const V jy,
+                                                         const V jz, const RhoV& rv,
+                                                         const SysPhys<typename VT<V>::S>& P, const NoiseKey& key,
+                                                         const typename SiteIdx<V>::type site, int* status) {
+    using S = typename VT<V>::S;
+    constexpr int W = VT<V>::W;
+    const V rho = vadd(vbc<V>(P.rho_c), drho);
+    bool bad_rho = false;
+#pragma unroll
+    for (int l = 0; l < W; ++l) bad_rho |= !(lane(rho, l) > S(0));
+    if (bad_rho) atomicOr(status, ST_RHO);
+
+    // thermodynamics (Eq. 3 and below Eq. 64), phi = drho / rho_c
+    const V phi = vmul(drho, vbc<V>(P.inv_rho_c));
+    const V phi2 = vmul(phi, phi);
+    const V df0 = vmul(phi, vfma(vbc<V>(P.b), phi2, vbc<V>(P.a)));
+    const V f0 = vmul(phi2, vfma(vbc<V>(S(0.25) * P.b), phi2, vbc<V>(S(0.5) * P.a)));
+    const V rr = vmul(rho, vbc<V>(P.inv_rho_c));
+    const V p0 = vsub(vmul(rr, df0), f0);
+    const V cs2 = vmul(vmul(rr, vbc<V>(P.inv_rho_c)), vfma(vbc<V>(S(3) * P.b), phi2, vbc<V>(P.a)));
+
+    // g_a = 3 sum_i t_i c_ia rho(r + c_i) = (face difference) / 6 + (edge differences) / 12
+    V g[3];
+    {
+        const V dfx = vsub(rv.template at<1, 0, 0>(), rv.template at<-1, 0, 0>());
+        const V dfy = vsub(rv.template at<0, 1, 0>(), rv.template at<0, -1, 0>());
+        const V dfz = vsub(rv.template at<0, 0, 1>(), rv.template at<0, 0, -1>());
+        const V exy = vsub(rv.template at<1, 1, 0>(), rv.template at<-1, -1, 0>());
+        const V exm = vsub(rv.template at<1, -1, 0>(), rv.template at<-1, 1, 0>());
+        const V exz = vsub(rv.template at<1, 0, 1>(), rv.template at<-1, 0, -1>());
+        const V ezm = vsub(rv.template at<1, 0, -1>(), rv.template at<-1, 0, 1>());
+        const V eyz = vsub(rv.template at<0, 1, 1>(), rv.template at<0, -1, -1>());
+        const V eym = vsub(rv.template at<0, 1, -1>(), rv.template at<0, -1, 1>());
+        // x: (1,1,0), (1,-1,0), (1,0,1), (1,0,-1) minus their opposites
+        g[0] = vfma(dfx, vk<V>(1.0 / 6.0), vmul(vadd(vadd(exy, exm), vadd(exz, ezm)), vk<V>(1.0 / 12.0)));
+        // y: (1,1,0), (-1,1,0) = -exm, (0,1,1), (0,1,-1)
+        g[1] = vfma(dfy, vk<V>(1.0 / 6.0), vmul(vadd(vsub(exy, exm), vadd(eyz, eym)), vk<V>(1.0 / 12.0)));
+        // z: (1,0,1), (-1,0,1) = -ezm, (0,1,1), (0,-1,1) = -eym
+        g[2] = vfma(dfz, vk<V>(1.0 / 6.0), vmul(vadd(vsub(exz, ezm), vsub(eyz, eym)), vk<V>(1.0 / 12.0)));
+    }
+    const V lap = lap_d3q19<V>(rv);
+
+    const V ir = vmap(rho, [](S x) { return fast_rcp(x); });
+    const V ux = vmul(jx, ir), uy = vmul(jy, ir), uz = vmul(jz, ir);
+    const V iso = vfma(vmul(rho, vbc<V>(-P.kappa)), lap, p0);          // p0 - kappa rho lap rho
+    const V nu = vbc<V>(P.nu);
+    const V udg = vfma(ux, g[0], vfma(uy, g[1], vmul(uz, g[2])));
+    const V Xxx = vfma(jx, ux, vmul(nu, vfma(vadd(ux, ux), g[0], udg)));
+    const V Xyy = vfma(jy, uy, vmul(nu, vfma(vadd(uy, uy), g[1], udg)));
+    const V Xzz = vfma(jz, uz, vmul(nu, vfma(vadd(uz, uz), g[2], udg)));
+    const V Xxy = vfma(jx, uy, vmul(nu, vfma(ux, g[1], vmul(uy, g[0]))));
+    const V Xyz = vfma(jy, uz, vmul(nu, vfma(uy, g[2], vmul(uz, g[1]))));
+    const V Xzx = vfma(jz, ux, vmul(nu, vfma(uz, g[0], vmul(ux, g[2]))));
+    const V kgx = vmul(vbc<V>(P.kappa), g[0]), kgy = vmul(vbc<V>(P.kappa), g[1]), kgz = vmul(vbc<V>(P.kappa), g[2]);
+    const V Kxx = vmul(kgx, g[0]), Kyy = vmul(kgy, g[1]), Kzz = vmul(kgz, g[2]);
+    const V Ksum = vadd(vadd(Kxx, Kyy), Kzz);
+    const V trX = vadd(vadd(Xxx, Xyy), Xzz);
+
+    // h_a = m_a / (36 N_a); N = (1, 1/3 x3, 2/3, 4/3, 4/9, 1/9 x3, ..., 2 for mode 16)
+    V h[19];
+    h[0] = vmul(drho, vk<V>(1.0 / 36.0));
+    h[1] = vmul(jx, vk<V>(1.0 / 12.0));
+    h[2] = vmul(jy, vk<V>(1.0 / 12.0));
+    h[3] = vmul(jz, vk<V>(1.0 / 12.0));
+    h[4] = vmul(vfma(Ksum, vk<V>(-0.5), vfma(iso, vk<V>(3.0), vsub(trX, drho))), vk<V>(1.0 / 24.0));
+    h[5] = vmul(vadd(vfma(Xxx, vk<V>(2.0), vsub(vk<V>(0.0), vadd(Xyy, Xzz))),
+                     vfma(Kxx, vk<V>(2.0), vsub(vk<V>(0.0), vadd(Kyy, Kzz)))),
+                vk<V>(1.0 / 48.0));
+    h[6] = vmul(vadd(vsub(Xyy, Xzz), vsub(Kyy, Kzz)), vk<V>(1.0 / 16.0));
+    h[7] = vmul(vfma(kgx, g[1], Xxy), vk<V>(1.0 / 4.0));
+    h[8] = vmul(vfma(kgy, g[2], Xyz), vk<V>(1.0 / 4.0));
+    h[9] = vmul(vfma(kgz, g[0], Xzx), vk<V>(1.0 / 4.0));
+    h[16] = vmul(vfma(Ksum, vk<V>(-1.5), vfma(iso, vk<V>(-3.0), drho)), vk<V>(1.0 / 72.0));
+
+    d3q19_tau1_noise_and_populations<V>(h, f, rho, cs2, P, key, site, status);
 }
 
 }  // namespace lbf

@@ -14,7 +14,9 @@
 // equilibrium, whose linearisation is the Landau-pressure one).
 //
 // The coupling needs the density on the 3 x 3 x 3 neighbourhood only, so the
-// z-marching kernel keeps one footprint ring of radius 1.
+// z-marching kernel keeps one footprint ring of radius 1.  With every mode at
+// tau = 1 the collision is the closed form collide_d3q19_modeq_tau1 (its
+// moments on the D3Q19 basis); the other settings take collide_modeq3 below.
 #pragma once
 
 #include "step_kernels.cuh"
@@ -216,7 +218,11 @@ __global__ void __launch_bounds__(TX* TY, MINB) step_kernel_zm(const StepArgs<Re
                 momentum_of<L, Real>(f, jc);
             }
             const int site = site_index(x, y, zc, nx, ny);
-            collide_modeq3<L, Real, MODE>(f, drho, jc, rv, S, A.phys[tl.x], uint32_t(site), step, A.status);
+            if constexpr (MODE == 2)
+                collide_d3q19_modeq_tau1<Real>(f, drho, jc[0], jc[1], jc[2], rv, A.phys[tl.x], noise_key(S, step),
+                                               uint32_t(site), A.status);
+            else
+                collide_modeq3<L, Real, MODE>(f, drho, jc, rv, S, A.phys[tl.x], uint32_t(site), step, A.status);
             sfor<0, Q>([&](auto I) {
                 constexpr int i = I;
                 fo[i * N + site] = f[i];
