@@ -140,18 +140,21 @@ int tile_table(int lattice, int (*t)[kVariantCols]) {
 // The variant given by index, else the first compiled variant matching the
 // requested shape (and occupancy, if given), else the default: the first
 // variant the coupling runs (row-marching strips, scheme 2, are compiled for
-// the modified equilibrium only).  The modified equilibrium on D3Q19 runs the
-// radius-1 z-marching kernel whatever the row, so its default is the first
-// row of the plain z-marching kernel (no producer warps), whose tile shape
-// and budget suit it best (16 x 8 columns at 6 CTAs per SM: 0.563 ms on the
-// 160-system ensemble against 0.645 ms with the paired kernel's row).
-lb_status choose_tile(int lattice, int coupling, const lb_run_opts* o, int& tile_id, int tdim[3]) {
+// the modified equilibrium only).  zm_default: the modified equilibrium on
+// D3Q19 where the paired kernel cannot run (FP64, a rate other than 1, an nx
+// that is not a multiple of 4) runs the radius-1 z-marching kernel whatever
+// the row, so its default is the first row of the plain z-marching kernel
+// (no producer warps), whose tile shape and budget suit it best (16 x 8
+// columns at 6 CTAs per SM: 0.563 ms on the 160-system ensemble against
+// 0.645 ms with the paired kernel's tile).
+lb_status choose_tile(int lattice, int coupling, const lb_run_opts* o, int& tile_id, int tdim[3],
+                      bool zm_default = false) {
     int t[32][kVariantCols];
     const int nt = tile_table(lattice, t);
     auto runs = [&](int k) { return t[k][5] != 2 || coupling == LB_MODEQ; };
     const bool defaults = o->tile[0] <= 0 && o->occupancy <= 0;
     auto preferred = [&](int k) {
-        if (!defaults || lattice != LB_D3Q19 || coupling != LB_MODEQ) return true;
+        if (!defaults || !zm_default || lattice != LB_D3Q19 || coupling != LB_MODEQ) return true;
         return t[k][4] == 0 && t[k][5] == 0 && t[k][6] == 1;
     };
     tile_id = 0;
@@ -219,7 +222,13 @@ lb_status make_plan(const lb_system_desc* s, int n, const lb_run_opts* o, std::v
     lb_status st = validate(s, n, o);
     if (st != LB_OK) return st;
     int tdim[3];
-    st = choose_tile(s[0].lattice, s[0].coupling, o, tile_id, tdim);
+    bool paired_runs = o->precision == LB_FP32_DEVIATION;
+    for (int k = 0; k < n; ++k) {
+        if (s[k].nx % 4 != 0) paired_runs = false;
+        for (int a = s[k].lattice == LB_D2Q9 ? 3 : 4; a < q_of(s[k].lattice); ++a)
+            if (s[k].tau[a] != 1.0) paired_runs = false;
+    }
+    st = choose_tile(s[0].lattice, s[0].coupling, o, tile_id, tdim, !paired_runs);
     if (st != LB_OK) return st;
     if (o->variant == 0 && o->tile[0] <= 0 && o->occupancy <= 0) prefer_longer_chunk(s, n, tile_id, tdim);
     const int q = q_of(s[0].lattice);

@@ -34,7 +34,15 @@ constexpr int pair_ring(int stg) { return stg == 3 ? 4 : 8; }
 template <int CP, class Real, int I>
 cudaError_t step_variant(const StepLaunch& a, cudaStream_t st) {
     constexpr int PW = kTiles[I][4];
-    if constexpr (CP == MODEQ) {      // the modified equilibrium: the radius-1 z-marching kernel of the same tile
+    if constexpr (CP == MODEQ) {
+        // the modified equilibrium: the paired kernel on the paired rows (FP32,
+        // every mode at tau = 1, every nx a multiple of 4), else the radius-1
+        // z-marching kernel of the same tile
+        if constexpr (PW > 0 && kTiles[I][5] == 3 && kTiles[I][6] == 2 && std::is_same<Real, float>::value) {
+            if (a.bgk_only == 2 && a.pair_ok)
+                return step_pair<kTiles[I][0], kTiles[I][1], kTiles[I][2], PW, kTiles[I][3], pair_ring(kTiles[I][5]),
+                                 kTiles[I][5], MODEQ>(a, st);
+        }
         return step_zm<D3Q19, Real, kTiles[I][0], kTiles[I][1], kTiles[I][2], kTiles[I][3]>(a, st);
     } else {
         if constexpr (PW > 0 && std::is_same<Real, float>::value) {

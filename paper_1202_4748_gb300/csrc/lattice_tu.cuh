@@ -157,11 +157,12 @@ cudaError_t step_ws(const StepLaunch& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Paired-site warp-specialised launch (fully relaxed Guo path on D3Q19, FP32,
-// every nx a multiple of 4): TX TY / 2 consumer threads and PW producer warps
+// Paired-site warp-specialised launch (fully relaxed path on D3Q19, FP32,
+// every nx a multiple of 4; the Guo form, or CP = MODEQ the modified
+// equilibrium): TX TY / 2 consumer threads and PW producer warps
 // per CTA, rings of R planes (and, STG = 3, the producers' staging area) in
 // dynamic shared memory.
-template <int TX, int TY, int ZC, int PW, int MINB, int R, int STG>
+template <int TX, int TY, int ZC, int PW, int MINB, int R, int STG, int CP = GUO>
 cudaError_t step_pair(const StepLaunch& a, cudaStream_t st) {
     StepArgs<float> A;
     A.sys = a.sys;
@@ -175,7 +176,7 @@ cudaError_t step_pair(const StepLaunch& a, cudaStream_t st) {
     constexpr size_t dyn = PairSmem<TX, TY, PW, R, STG>::bytes;
     static int state = 0;                      // once per instantiation: 1 usable, -1 not
     if (state == 0) {
-        auto k = step_kernel_pair<TX, TY, ZC, PW, MINB, R, STG>;
+        auto k = step_kernel_pair<TX, TY, ZC, PW, MINB, R, STG, CP>;
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, k);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn));
@@ -185,8 +186,11 @@ cudaError_t step_pair(const StepLaunch& a, cudaStream_t st) {
         // the register split must balance against the launch count it assumes
         state = (!PairRegs<TX, TY, PW, MINB, STG>::split || fa.numRegs == PairRegs<TX, TY, PW, MINB, STG>::launch) ? 1 : -1;
     }
-    if (state < 0) return step_ws<D3Q19, TX, TY, ZC, PW, 1, 0>(a, st);
-    step_kernel_pair<TX, TY, ZC, PW, MINB, R, STG><<<a.n_tiles, TX * TY / 2 + 32 * PW, dyn, st>>>(A);
+    if (state < 0) {
+        if constexpr (CP == MODEQ) return step_zm<D3Q19, float, TX, TY, ZC, MINB>(a, st);
+        else return step_ws<D3Q19, TX, TY, ZC, PW, 1, 0>(a, st);
+    }
+    step_kernel_pair<TX, TY, ZC, PW, MINB, R, STG, CP><<<a.n_tiles, TX * TY / 2 + 32 * PW, dyn, st>>>(A);
     return cudaGetLastError();
 }
 

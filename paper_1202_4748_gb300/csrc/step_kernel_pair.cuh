@@ -32,6 +32,13 @@
 // before its waiter looks and the parity of the use count names the phase.
 // Every wait is bounded (mbar_wait): a timeout flags the CTA and the status
 // word, and every thread keeps the same control flow.
+//
+// CP = MODEQ runs the modified equilibrium carried to D3Q19
+// (collide_d3q19_modeq_tau1): no Laplacian planes are formed (full[...] of
+// plane zl completes once density plane zl + 1 is written), the consumers
+// read the density of the planes zc - 1 .. zc + 1 around their pair, and so
+// the producers reuse the slots of plane zz - R + 1 (whose collision no
+// longer reads them) instead of zz - R.
 #pragma once
 
 #include "collide_d3q19.cuh"
@@ -90,6 +97,29 @@ struct PairRhoView {
     }
 };
 
+// Density pairs around a consumer pair (sites at footprint columns fx, fx + 1
+// with fx even; c = footprint row * SXP + fx): the c_x = 0 neighbour pair is
+// the aligned pair at fx, the c_x = -1 and +1 pairs straddle it and its
+// aligned neighbours at fx - 2 and fx + 2.
+template <int SXP>
+struct PairRhoViewEven {
+    const float* p[3];      // density planes z - 1, z, z + 1
+    int c;
+    template <int CX, int CY, int CZ>
+    __device__ __forceinline__ float2 at() const {
+        const float* q = p[1 + CZ] + c + SXP * CY;
+        if constexpr (CX == 0) {
+            return *reinterpret_cast<const float2*>(q);
+        } else if constexpr (CX == -1) {
+            const float2 m = *reinterpret_cast<const float2*>(q - 2), o = *reinterpret_cast<const float2*>(q);
+            return make_float2(m.y, o.x);
+        } else {
+            const float2 o = *reinterpret_cast<const float2*>(q), n = *reinterpret_cast<const float2*>(q + 2);
+            return make_float2(o.y, n.x);
+        }
+    }
+};
+
 // Laplacian pairs around a consumer pair (sites at Laplacian columns 2k + 1,
 // 2k + 2; c = (row + 1) * LXP + 2k): c_x = 0 from copy E (the value of column
 // px sits at px + 1, lap_e floats after copy O), c_x = +-1 from copy O.
@@ -141,7 +171,7 @@ struct PairSmem {
     static constexpr size_t bytes = PairLayout<TX, TY, R>::bytes + stage;
 };
 
-template <int TX, int TY, int ZC, int PW, int MINB, int R, int STG>
+template <int TX, int TY, int ZC, int PW, int MINB, int R, int STG, int CP = GUO>
 __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(const StepArgs<float> A) {
     using RG = PairRegs<TX, TY, PW, MINB, STG>;
     using L = D3Q19;
@@ -231,7 +261,10 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
         };
         pull(z0 - H);
         for (int zz = z0 - H; zz < z1 + H; ++zz) {
-            const int zw = zz - R;                       // plane whose slots this iteration reuses
+            // plane whose slots this iteration reuses: the modified equilibrium's
+            // consumers read the density of the planes on both sides of the one
+            // they collide, so its producers also wait for the plane after it
+            const int zw = zz - R + (CP == MODEQ ? 1 : 0);
             if (zw >= z0) mbar_wait(&empty[(zw - z0) & (R - 1)], unsigned(((zw - z0) / R) & 1), &abort_flag, A.status);
             float* const rp = ring + slot(zz) * PLANE;
             // per direction, the pulled values of the quad's four sites: the
@@ -299,7 +332,11 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
             }
             named_barrier(1, NP);                        // density plane zz complete (producers)
             const int zl = zz - 1;                       // Laplacian plane (needs density zl-1 .. zl+1)
-            if (zl >= z0 - 1) {
+            if (zl >= z0 - 1 && CP == MODEQ) {
+                // the modified equilibrium needs no Laplacian planes: density
+                // planes up to zl + 1 are complete (same hand-off as below)
+                mbar_arrive(&full[(zl - z0 + 1) & (R - 1)]);
+            } else if (zl >= z0 - 1) {
                 PairRhoView<SXP> rv{{ring + slot(zl - 1) * PLANE, ring + slot(zl) * PLANE, ring + slot(zl + 1) * PLANE},
                                     0};
                 float* lo = ring + slot(zl) * PLANE + LY_::O_LO;
@@ -361,15 +398,22 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
                 const float2 jx = *reinterpret_cast<const float2*>(cp + j_off);
                 const float2 jy = *reinterpret_cast<const float2*>(cp + j_off + 2);
                 const float2 jz = *reinterpret_cast<const float2*>(cp + j_off + 4);
-                PairLapView<LXP> lv;
-                lv.o[0] = ring + slot(zc - 1) * PLANE + LY_::O_LO;
-                lv.o[1] = cp + LY_::O_LO;
-                lv.o[2] = ring + slot(zc + 1) * PLANE + LY_::O_LO;
-                lv.c = lap_c;
-                lv.lap_e = LY_::LAP;
                 const int site = site_index(x, y, zc, nx, ny);
                 float2 f[19];
-                collide_d3q19_tau1<float2>(f, drho, jx, jy, jz, lv, P, key, make_uint2(site, site + 1), A.status);
+                if constexpr (CP == MODEQ) {
+                    const PairRhoViewEven<SXP> rv{{ring + slot(zc - 1) * PLANE, cp, ring + slot(zc + 1) * PLANE},
+                                                  rho_off};
+                    collide_d3q19_modeq_tau1<float2>(f, drho, jx, jy, jz, rv, P, key, make_uint2(site, site + 1),
+                                                     A.status);
+                } else {
+                    PairLapView<LXP> lv;
+                    lv.o[0] = ring + slot(zc - 1) * PLANE + LY_::O_LO;
+                    lv.o[1] = cp + LY_::O_LO;
+                    lv.o[2] = ring + slot(zc + 1) * PLANE + LY_::O_LO;
+                    lv.c = lap_c;
+                    lv.lap_e = LY_::LAP;
+                    collide_d3q19_tau1<float2>(f, drho, jx, jy, jz, lv, P, key, make_uint2(site, site + 1), A.status);
+                }
                 sfor<0, 19>([&](auto I) {
                     constexpr int i = I;
                     *reinterpret_cast<float2*>(fo + (i * N + site)) = f[i];

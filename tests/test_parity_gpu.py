@@ -565,17 +565,19 @@ def test_fp32_fully_relaxed_path_on_odd_and_tiny_shapes(lb, coupling):
         assert all(np.array_equal(a, b) for a, b in zip(runs[0], r))
 
 
-def test_fp32_paired_kernel_on_even_shapes(lb):
+@pytest.mark.parametrize("coupling", ["guo", "modeq"])
+def test_fp32_paired_kernel_on_even_shapes(lb, coupling):
     """The paired-site kernel (two x-adjacent sites per consumer thread, paired
     FP32 arithmetic, producers pulling aligned quads of sites) runs when every
-    nx is a multiple of 4: ragged tiles in x and y, several z-chunks, sides
-    shorter than the stencil, batched in one launch.  Each FP32 step matches
-    the oracle stepped from the GPU's own state, the achieved one-step error
-    is far inside the bar (FP32 rounding of the stored deviations and of the
-    collision: a few 1e-8 of max |f|), and every compiled D3Q19 variant
-    (one-site kernels included) gives the same bits."""
+    nx is a multiple of 4, for the Guo form and for the modified equilibrium:
+    ragged tiles in x and y, several z-chunks, sides shorter than the stencil,
+    batched in one launch.  Each FP32 step matches the oracle stepped from the
+    GPU's own state, the achieved one-step error is far inside the bar (FP32
+    rounding of the stored deviations and of the collision: a few 1e-8 of
+    max |f|), and every compiled D3Q19 variant (one-site kernels included)
+    gives the same bits."""
     shapes = [(20, 13, 11), (8, 8, 7), (4, 4, 4), (4, 2, 2), (4, 3, 2), (12, 5, 70), (48, 24, 6), (36, 40, 3)]
-    systems = [_sys("D3Q19", "guo", *sh, a=-0.002 + 0.001 * k, b=0.1, kappa=0.01, kT=1e-4, tau=[1.0] * 19,
+    systems = [_sys("D3Q19", coupling, *sh, a=-0.002 + 0.001 * k, b=0.1, kappa=0.01, kT=1e-4, tau=[1.0] * 19,
                     seed=60 + k, system_id=k) for k, sh in enumerate(shapes)]
     rows = lb.kernel_variants("D3Q19")
     assert rows[0][6] == 2                               # the default pairs sites
