@@ -53,6 +53,32 @@ struct SiteIdx<float2> {
     using type = uint2;
 };
 
+// Special-function-unit approximations (the PTX .approx instructions) with
+// subnormal operands flushed: every operand they get here is a normal number
+// or zero (uniforms U >= 2^-33, -2 ln U clamped at 1e-30, angles in [-pi, pi)
+// with a spacing of 2^-24 pi, noise variances of order kT), where flushing
+// changes no result and saves the subnormal handling around each instruction.
+__device__ __forceinline__ float sfu_lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sfu_rsqrt(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sfu_sin(float x) {
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sfu_cos(float x) {
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Four normals of draw d for every lane, multiplied by the lane's noise scale
 // sc (n = sc R cos, sc R sin from the words (w0, w1), (w2, w3)).  need3 = false
 // skips the sine of the second pair (its normal is not used).
@@ -64,25 +90,16 @@ __device__ __forceinline__ void draw4(const NoiseKey& k, uint32_t site, uint32_t
     const float ub0 = vfma(float(w.y), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     const float ua1 = vfma(float(w.z), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     const float ub1 = vfma(float(w.w), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const float r20 = fmaxf(vmul(__log2f(ua0), -1.3862943611198906f), 1e-30f);
-    const float r21 = fmaxf(vmul(__log2f(ua1), -1.3862943611198906f), 1e-30f);
-    const float rr0 = vmul(vmul(r20, rsqrtf(r20)), nsc);
-    const float rr1 = vmul(vmul(r21, rsqrtf(r21)), nsc);
+    const float r20 = fmaxf(vmul(sfu_lg2(ua0), -1.3862943611198906f), 1e-30f);
+    const float r21 = fmaxf(vmul(sfu_lg2(ua1), -1.3862943611198906f), 1e-30f);
+    const float rr0 = vmul(vmul(r20, sfu_rsqrt(r20)), nsc);
+    const float rr1 = vmul(vmul(r21, sfu_rsqrt(r21)), nsc);
     const float t0 = vfma(ub0, 6.2831853071795865f, -3.1415926535897932f);
     const float t1 = vfma(ub1, 6.2831853071795865f, -3.1415926535897932f);
-    float s0, c0;
-    __sincosf(t0, &s0, &c0);
-    n[0] = vmul(rr0, c0);
-    n[1] = vmul(rr0, s0);
-    if (need3) {
-        float s1, c1;
-        __sincosf(t1, &s1, &c1);
-        n[2] = vmul(rr1, c1);
-        n[3] = vmul(rr1, s1);
-    } else {
-        n[2] = vmul(rr1, __cosf(t1));
-        n[3] = 0.0f;
-    }
+    n[0] = vmul(rr0, sfu_cos(t0));
+    n[1] = vmul(rr0, sfu_sin(t0));
+    n[2] = vmul(rr1, sfu_cos(t1));
+    n[3] = need3 ? vmul(rr1, sfu_sin(t1)) : 0.0f;
 }
 
 // Two sites: the same sequence lane by lane, the lane-independent arithmetic paired.
@@ -97,30 +114,19 @@ __device__ __forceinline__ void draw4(const NoiseKey& k, uint2 site, uint32_t d,
     const float2 ua1 = vfma(make_float2(float(wa.z), float(wb.z)), sA, sB);
     const float2 ub1 = vfma(make_float2(float(wa.w), float(wb.w)), sA, sB);
     const float2 m2ln2 = vk<float2>(-1.3862943611198906);
-    float2 r20 = vmul(make_float2(__log2f(ua0.x), __log2f(ua0.y)), m2ln2);
-    float2 r21 = vmul(make_float2(__log2f(ua1.x), __log2f(ua1.y)), m2ln2);
+    float2 r20 = vmul(make_float2(sfu_lg2(ua0.x), sfu_lg2(ua0.y)), m2ln2);
+    float2 r21 = vmul(make_float2(sfu_lg2(ua1.x), sfu_lg2(ua1.y)), m2ln2);
     r20 = make_float2(fmaxf(r20.x, 1e-30f), fmaxf(r20.y, 1e-30f));
     r21 = make_float2(fmaxf(r21.x, 1e-30f), fmaxf(r21.y, 1e-30f));
-    const float2 rr0 = vmul(vmul(r20, make_float2(rsqrtf(r20.x), rsqrtf(r20.y))), nsc);
-    const float2 rr1 = vmul(vmul(r21, make_float2(rsqrtf(r21.x), rsqrtf(r21.y))), nsc);
+    const float2 rr0 = vmul(vmul(r20, make_float2(sfu_rsqrt(r20.x), sfu_rsqrt(r20.y))), nsc);
+    const float2 rr1 = vmul(vmul(r21, make_float2(sfu_rsqrt(r21.x), sfu_rsqrt(r21.y))), nsc);
     const float2 tw = vk<float2>(6.2831853071795865), tp = vk<float2>(-3.1415926535897932);
     const float2 t0 = vfma(ub0, tw, tp);
     const float2 t1 = vfma(ub1, tw, tp);
-    float2 s0, c0;
-    __sincosf(t0.x, &s0.x, &c0.x);
-    __sincosf(t0.y, &s0.y, &c0.y);
-    n[0] = vmul(rr0, c0);
-    n[1] = vmul(rr0, s0);
-    if (need3) {
-        float2 s1, c1;
-        __sincosf(t1.x, &s1.x, &c1.x);
-        __sincosf(t1.y, &s1.y, &c1.y);
-        n[2] = vmul(rr1, c1);
-        n[3] = vmul(rr1, s1);
-    } else {
-        n[2] = vmul(rr1, make_float2(__cosf(t1.x), __cosf(t1.y)));
-        n[3] = make_float2(0.0f, 0.0f);
-    }
+    n[0] = vmul(rr0, make_float2(sfu_cos(t0.x), sfu_cos(t0.y)));
+    n[1] = vmul(rr0, make_float2(sfu_sin(t0.x), sfu_sin(t0.y)));
+    n[2] = vmul(rr1, make_float2(sfu_cos(t1.x), sfu_cos(t1.y)));
+    n[3] = need3 ? vmul(rr1, make_float2(sfu_sin(t1.x), sfu_sin(t1.y))) : make_float2(0.0f, 0.0f);
 }
 
 // FP64: U = (x + 1/2) 2^-32 exactly, R = sqrt(-2 ln U), angle 2 pi U_b, with
@@ -138,9 +144,9 @@ __device__ __forceinline__ void draw4(const NoiseKey& k, uint32_t site, uint32_t
 }
 
 // sqrt(x) for x >= 0 in the lane precision (0 at 0): x rsqrt(x) in float.
-__device__ __forceinline__ float lane_sqrt(float x) { return x > 0.0f ? vmul(x, rsqrtf(x)) : 0.0f; }
+__device__ __forceinline__ float lane_sqrt(float x) { return x > 0.0f ? vmul(x, sfu_rsqrt(x)) : 0.0f; }
 __device__ __forceinline__ double lane_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float lane_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float lane_rsqrt(float x) { return sfu_rsqrt(x); }
 __device__ __forceinline__ double lane_rsqrt(double x) { return rsqrt(x); }
 
 // Laplacian of the density, lap rho = 6 sum_i t_i (rho(r + c_i) - rho(r))
