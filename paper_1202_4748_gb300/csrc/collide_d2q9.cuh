@@ -130,40 +130,45 @@ __device__ __forceinline__ void collide_d2q9_modeq(V (&f)[9], const V drho, cons
     }
 
     if (P.kT > S(0)) {
-        // scale sqrt(3 rho kT) (Eq. 68 with Delta V = Delta t = 1) and the
+        // scale sqrt(3 rho kT) (Eq. 68 with Delta V = Delta t = 1; the variance
+        // carries the factor the draws of the lane precision expect) and the
         // Cholesky factor of the coupled pair (modes 3c^2 - 2 and 9c^4 - 15c^2 + 2,
         // rest components -2 and 2): M = [[(4 + 4 om) g_33, -4 om g_38],
-        // [-4 om g_38, (16 + 4 om) g_88]], om = 1 - 3 c_s^2, g = 1 at tau = 1
-        V sc, k11, k21, k22;
+        // [-4 om g_38, (16 + 4 om) g_88]], om = 1 - 3 c_s^2, g = 1 at tau = 1,
+        // where the determinant is 64 + 80 om (positive only where 4 + 4 om is
+        // too); paired arithmetic, the special functions lane by lane
+        const V sc = vsqrt_pos(vmul(vbc<V>(vmul(S(3.0 * DrawScale<S>::v), P.kT)), rho));
+        const V om = vfma(cs2, vk<V>(-3.0), vk<V>(1.0));
+        V mpp, det, mpr;
+        if constexpr (MODE == 2) {
+            mpp = vfma(om, vk<V>(4.0), vk<V>(4.0));
+            mpr = vmul(om, vk<V>(-4.0));
+            det = vfma(om, vk<V>(80.0), vk<V>(64.0));
+        } else {
+            mpp = vmul(vfma(om, vk<V>(4.0), vk<V>(4.0)), vbc<V>(P.g_diag[3]));
+            mpr = vmul(vmul(om, vk<V>(-4.0)), vbc<V>(P.g_pair));
+            det = vfma(mpp, vmul(vfma(om, vk<V>(4.0), vk<V>(16.0)), vbc<V>(P.g_diag[8])),
+                       vmul(vmul(mpr, mpr), vk<V>(-1.0)));
+        }
+        const V q = vrsqrt(mpp);
+        V k11 = vmul(vmul(mpp, q), vk<V>(1.0 / 144.0));
+        V k21 = vmul(vmul(mpr, q), vk<V>(1.0 / 576.0));
+        V k22 = vmul(vmul(det, vrsqrt(vmul(det, mpp))), vk<V>(1.0 / 576.0));
+        auto bad = [&](int l) { return !(lane(det, l) > S(0)) || (MODE != 2 && !(lane(mpp, l) > S(0))); };
         bool bad_noise = false;
 #pragma unroll
-        for (int l = 0; l < W; ++l) {
-            const S r = lane(rho, l);
-            set_lane(sc, l, lane_sqrt(vmul(S(3) * P.kT, r > S(0) ? r : S(0))));
-            const S om = vfma(lane(cs2, l), S(-3), S(1));
-            S mpp, det, mpr;
-            if constexpr (MODE == 2) {
-                mpp = vfma(om, S(4), S(4));
-                mpr = vmul(om, S(-4));
-                det = vfma(mpp, vfma(om, S(4), S(16)), -vmul(vmul(om, om), S(16)));
-            } else {
-                mpp = vmul(vfma(om, S(4), S(4)), P.g_diag[3]);
-                mpr = vmul(vmul(om, S(-4)), P.g_pair);
-                det = vfma(mpp, vmul(vfma(om, S(4), S(16)), P.g_diag[8]), -vmul(mpr, mpr));
+        for (int l = 0; l < W; ++l) bad_noise = bad_noise || bad(l);
+        if (bad_noise) {
+#pragma unroll
+            for (int l = 0; l < W; ++l) {
+                if (bad(l)) {
+                    set_lane(k11, l, S(0));
+                    set_lane(k21, l, S(0));
+                    set_lane(k22, l, S(0));
+                }
             }
-            if (mpp > S(0) && det > S(0)) {
-                const S q = lane_rsqrt(mpp);
-                set_lane(k11, l, vmul(vmul(mpp, q), S(1.0 / 144.0)));
-                set_lane(k21, l, vmul(vmul(mpr, q), S(1.0 / 576.0)));
-                set_lane(k22, l, vmul(vmul(lane_sqrt(det), q), S(1.0 / 576.0)));
-            } else {
-                bad_noise = true;
-                set_lane(k11, l, S(0));
-                set_lane(k21, l, S(0));
-                set_lane(k22, l, S(0));
-            }
+            atomicOr(status, ST_NOISE);
         }
-        if (bad_noise) atomicOr(status, ST_NOISE);
         // the normal of mode a is number a - 3 in draw order; its amplitude over
         // 36 N_a: sqrt(N_a g_aa) / (36 N_a)
         V c4, c5, c67a, c67b;
@@ -178,13 +183,13 @@ __device__ __forceinline__ void collide_d2q9_modeq(V (&f)[9], const V drho, cons
             c67b = vbc<V>(vmul(P.namp[7], S(1.0 / 24.0)));
         }
         V n[4];
-        draw4(key, site, 0u, sc, n, true);
+        draw4(key, site, 0u, sc, sc, n, true);
         const V n3 = n[0];
         k[3] = vfma(k11, n3, k[3]);
         k[4] = vfma(n[1], c4, k[4]);
         k[5] = vfma(n[2], c5, k[5]);
         k[6] = vfma(n[3], c67a, k[6]);
-        draw4(key, site, 1u, sc, n, false);
+        draw4(key, site, 1u, sc, sc, n, false);
         k[7] = vfma(n[0], c67b, k[7]);
         k[8] = vfma(k22, n[1], vfma(k21, n3, k[8]));
     }

@@ -27,11 +27,20 @@
 
 namespace lbf {
 
-// Philox counter words shared by the sites of one step of one system.
+// Philox counter words shared by the sites of one step of one system, and the
+// parts of rounds 1 and 2 of Philox4x32-10 on the counter (site, step low
+// word, step high word, tag | d) that depend on neither the site nor the draw
+// d: the step words enter those rounds' products only through counter words 1
+// and 2, so noise_key forms them once per kernel and a draw starts from one
+// product of the site (shared by the site's draws) and one of its own.
 struct NoiseKey {
     uint32_t k0, k1;      // key: the seed
     uint32_t slo, shi;    // step
     uint32_t tag;         // system_id << 8 (the draw index fills the low byte)
+    uint32_t t1;          // tag ^ k1: round 1 gives word 2 = hi(M0 site) ^ t1 ^ d
+    uint32_t y1k;         // lo(M1 shi) ^ (k0 + W0): round 2 gives word 0 = hi(M1 z1) ^ y1k
+    uint32_t z2k, w2;     // hi(M0 x1) ^ (k1 + W1) and lo(M0 x1), x1 = hi(M1 shi) ^ slo ^ k0:
+                          // round 2 gives word 2 = z2k ^ lo(M0 site) and word 3 = w2
 };
 __device__ __forceinline__ NoiseKey noise_key(const SysDev& S, int64_t step) {
     NoiseKey k;
@@ -40,7 +49,33 @@ __device__ __forceinline__ NoiseKey noise_key(const SysDev& S, int64_t step) {
     k.slo = uint32_t(uint64_t(step) & 0xffffffffu);
     k.shi = uint32_t(uint64_t(step) >> 32);
     k.tag = S.system_id << 8;
+    k.t1 = k.tag ^ k.k1;
+    const uint64_t q1 = uint64_t(kPhiloxM1) * k.shi;
+    const uint32_t x1 = uint32_t(q1 >> 32) ^ k.slo ^ k.k0;
+    k.y1k = uint32_t(q1) ^ (k.k0 + kPhiloxW0);
+    const uint64_t q2 = uint64_t(kPhiloxM0) * x1;
+    k.z2k = uint32_t(q2 >> 32) ^ (k.k1 + kPhiloxW1);
+    k.w2 = uint32_t(q2);
     return k;
+}
+
+// philox4x32_10((site, slo, shi, tag | d), k0, k1) for a draw d < 256, with
+// rounds 1 and 2 completed from the words noise_key formed.
+__device__ __forceinline__ uint4 philox_draw(const NoiseKey& k, uint32_t site, uint32_t d) {
+    const uint64_t p0 = uint64_t(kPhiloxM0) * site;                // round 1
+    const uint32_t z1 = uint32_t(p0 >> 32) ^ k.t1 ^ d;
+    const uint64_t p1 = uint64_t(kPhiloxM1) * z1;                  // round 2
+    uint4 c = make_uint4(uint32_t(p1 >> 32) ^ k.y1k, uint32_t(p1), k.z2k ^ uint32_t(p0), k.w2);
+    uint32_t k0 = k.k0 + kPhiloxW0, k1 = k.k1 + kPhiloxW1;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+        const uint64_t pa = uint64_t(kPhiloxM0) * c.x;
+        const uint64_t pb = uint64_t(kPhiloxM1) * c.z;
+        c = make_uint4(uint32_t(pb >> 32) ^ c.y ^ k0, uint32_t(pb), uint32_t(pa >> 32) ^ c.w ^ k1, uint32_t(pa));
+    }
+    return c;
 }
 
 // Site indices of the lanes: one per lane.
@@ -55,9 +90,9 @@ struct SiteIdx<float2> {
 
 // Special-function-unit approximations (the PTX .approx instructions) with
 // subnormal operands flushed: every operand they get here is a normal number
-// or zero (uniforms U >= 2^-33, -2 ln U clamped at 1e-30, angles in [-pi, pi)
-// with a spacing of 2^-24 pi, noise variances of order kT), where flushing
-// changes no result and saves the subnormal handling around each instruction.
+// or zero (uniforms U >= 2^-33, -log2 U >= 0, angles in [-pi, pi] with a
+// spacing of 2^-24 pi, noise variances of order kT), where flushing changes
+// no result and saves the subnormal handling around each instruction.
 __device__ __forceinline__ float sfu_lg2(float x) {
     float y;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -78,24 +113,45 @@ __device__ __forceinline__ float sfu_cos(float x) {
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float sfu_sqrt(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
-// Four normals of draw d for every lane, multiplied by the lane's noise scale
-// sc (n = sc R cos, sc R sin from the words (w0, w1), (w2, w3)).  need3 = false
-// skips the sine of the second pair (its normal is not used).
-__device__ __forceinline__ void draw4(const NoiseKey& k, uint32_t site, uint32_t d, float sc, float (&n)[4],
-                                      bool need3) {
-    const uint4 w = philox4x32_10(make_uint4(site, k.slo, k.shi, k.tag | d), k.k0, k.k1);
-    const float nsc = -sc;     // the angle is taken as 2 pi U - pi: cos and sin change sign
-    const float ua0 = vfma(float(w.x), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const float ub0 = vfma(float(w.y), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const float ua1 = vfma(float(w.z), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const float ub1 = vfma(float(w.w), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const float r20 = fmaxf(vmul(sfu_lg2(ua0), -1.3862943611198906f), 1e-30f);
-    const float r21 = fmaxf(vmul(sfu_lg2(ua1), -1.3862943611198906f), 1e-30f);
-    const float rr0 = vmul(vmul(r20, sfu_rsqrt(r20)), nsc);
-    const float rr1 = vmul(vmul(r21, sfu_rsqrt(r21)), nsc);
-    const float t0 = vfma(ub0, 6.2831853071795865f, -3.1415926535897932f);
-    const float t1 = vfma(ub1, 6.2831853071795865f, -3.1415926535897932f);
+// Factor that the draws of a lane precision expect in the variance from which
+// their scale is formed (draw4): 2 ln 2 in float, 1 in double.
+template <class S>
+struct DrawScale;
+template <>
+struct DrawScale<float> {
+    static constexpr double v = 1.3862943611198906;
+};
+template <>
+struct DrawScale<double> {
+    static constexpr double v = 1.0;
+};
+
+// Four normals of draw d for every lane: n0, n1 from the words (w0, w1)
+// scaled by sc0, n2, n3 from (w2, w3) scaled by sc1 (two scales, so that a
+// mode's constant can ride on its pair's scale).  Float: the scales carry
+// the factor sqrt(2 ln 2) of the Box-Muller radius sqrt(-2 ln U) =
+// sqrt(2 ln 2) sqrt(-log2 U), so the radius is formed from -log2 U directly,
+// and the angle 2 pi U_b - pi (in [-pi, pi], where the hardware sine and
+// cosine are accurate; the half turn flips the signs of both, which the
+// negated scales undo) is formed from the word in one rounding.
+// need3 = false skips the sine of the second pair (its normal is not used).
+__device__ __forceinline__ void draw4(const NoiseKey& k, uint32_t site, uint32_t d, float sc0, float sc1,
+                                      float (&n)[4], bool need3) {
+    const uint4 w = philox_draw(k, site, d);
+    constexpr float kU = 2.3283064365386963e-10f, kU0 = 1.1641532182693481e-10f;   // U = (w + 1/2) 2^-32
+    constexpr float kT = 1.4629180792671596e-09f, kT0 = -3.1415926528583340f;      // 2 pi U - pi
+    const float ua0 = vfma(float(w.x), kU, kU0);
+    const float ua1 = vfma(float(w.z), kU, kU0);
+    const float rr0 = vmul(sfu_sqrt(fmaxf(-sfu_lg2(ua0), 0.0f)), -sc0);
+    const float rr1 = vmul(sfu_sqrt(fmaxf(-sfu_lg2(ua1), 0.0f)), -sc1);
+    const float t0 = vfma(float(w.y), kT, kT0);
+    const float t1 = vfma(float(w.w), kT, kT0);
     n[0] = vmul(rr0, sfu_cos(t0));
     n[1] = vmul(rr0, sfu_sin(t0));
     n[2] = vmul(rr1, sfu_cos(t1));
@@ -103,26 +159,20 @@ __device__ __forceinline__ void draw4(const NoiseKey& k, uint32_t site, uint32_t
 }
 
 // Two sites: the same sequence lane by lane, the lane-independent arithmetic paired.
-__device__ __forceinline__ void draw4(const NoiseKey& k, uint2 site, uint32_t d, float2 sc, float2 (&n)[4],
-                                      bool need3) {
-    const uint4 wa = philox4x32_10(make_uint4(site.x, k.slo, k.shi, k.tag | d), k.k0, k.k1);
-    const uint4 wb = philox4x32_10(make_uint4(site.y, k.slo, k.shi, k.tag | d), k.k0, k.k1);
-    const float2 nsc = make_float2(-sc.x, -sc.y);
-    const float2 sA = vk<float2>(2.3283064365386963e-10), sB = vk<float2>(1.1641532182693481e-10);
-    const float2 ua0 = vfma(make_float2(float(wa.x), float(wb.x)), sA, sB);
-    const float2 ub0 = vfma(make_float2(float(wa.y), float(wb.y)), sA, sB);
-    const float2 ua1 = vfma(make_float2(float(wa.z), float(wb.z)), sA, sB);
-    const float2 ub1 = vfma(make_float2(float(wa.w), float(wb.w)), sA, sB);
-    const float2 m2ln2 = vk<float2>(-1.3862943611198906);
-    float2 r20 = vmul(make_float2(sfu_lg2(ua0.x), sfu_lg2(ua0.y)), m2ln2);
-    float2 r21 = vmul(make_float2(sfu_lg2(ua1.x), sfu_lg2(ua1.y)), m2ln2);
-    r20 = make_float2(fmaxf(r20.x, 1e-30f), fmaxf(r20.y, 1e-30f));
-    r21 = make_float2(fmaxf(r21.x, 1e-30f), fmaxf(r21.y, 1e-30f));
-    const float2 rr0 = vmul(vmul(r20, make_float2(sfu_rsqrt(r20.x), sfu_rsqrt(r20.y))), nsc);
-    const float2 rr1 = vmul(vmul(r21, make_float2(sfu_rsqrt(r21.x), sfu_rsqrt(r21.y))), nsc);
-    const float2 tw = vk<float2>(6.2831853071795865), tp = vk<float2>(-3.1415926535897932);
-    const float2 t0 = vfma(ub0, tw, tp);
-    const float2 t1 = vfma(ub1, tw, tp);
+__device__ __forceinline__ void draw4(const NoiseKey& k, uint2 site, uint32_t d, float2 sc0, float2 sc1,
+                                      float2 (&n)[4], bool need3) {
+    const uint4 wa = philox_draw(k, site.x, d);
+    const uint4 wb = philox_draw(k, site.y, d);
+    const float2 kU = vk<float2>(2.3283064365386963e-10), kU0 = vk<float2>(1.1641532182693481e-10);
+    const float2 kT = vk<float2>(1.4629180792671596e-09), kT0 = vk<float2>(-3.1415926528583340);
+    const float2 ua0 = vfma(make_float2(float(wa.x), float(wb.x)), kU, kU0);
+    const float2 ua1 = vfma(make_float2(float(wa.z), float(wb.z)), kU, kU0);
+    const float2 r0 = make_float2(sfu_sqrt(fmaxf(-sfu_lg2(ua0.x), 0.0f)), sfu_sqrt(fmaxf(-sfu_lg2(ua0.y), 0.0f)));
+    const float2 r1 = make_float2(sfu_sqrt(fmaxf(-sfu_lg2(ua1.x), 0.0f)), sfu_sqrt(fmaxf(-sfu_lg2(ua1.y), 0.0f)));
+    const float2 rr0 = vmul(r0, make_float2(-sc0.x, -sc0.y));
+    const float2 rr1 = vmul(r1, make_float2(-sc1.x, -sc1.y));
+    const float2 t0 = vfma(make_float2(float(wa.y), float(wb.y)), kT, kT0);
+    const float2 t1 = vfma(make_float2(float(wa.w), float(wb.w)), kT, kT0);
     n[0] = vmul(rr0, make_float2(sfu_cos(t0.x), sfu_cos(t0.y)));
     n[1] = vmul(rr0, make_float2(sfu_sin(t0.x), sfu_sin(t0.y)));
     n[2] = vmul(rr1, make_float2(sfu_cos(t1.x), sfu_cos(t1.y)));
@@ -131,23 +181,30 @@ __device__ __forceinline__ void draw4(const NoiseKey& k, uint2 site, uint32_t d,
 
 // FP64: U = (x + 1/2) 2^-32 exactly, R = sqrt(-2 ln U), angle 2 pi U_b, with
 // the library's correctly rounded functions.
-__device__ __forceinline__ void draw4(const NoiseKey& k, uint32_t site, uint32_t d, double sc, double (&n)[4],
-                                      bool need3) {
-    const uint4 w = philox4x32_10(make_uint4(site, k.slo, k.shi, k.tag | d), k.k0, k.k1);
+__device__ __forceinline__ void draw4(const NoiseKey& k, uint32_t site, uint32_t d, double sc0, double sc1,
+                                      double (&n)[4], bool need3) {
+    const uint4 w = philox_draw(k, site, d);
     double a, b;
     box_muller(w.x, w.y, a, b);
-    n[0] = vmul(sc, a);
-    n[1] = vmul(sc, b);
+    n[0] = vmul(sc0, a);
+    n[1] = vmul(sc0, b);
     box_muller(w.z, w.w, a, b);
-    n[2] = vmul(sc, a);
-    n[3] = need3 ? vmul(sc, b) : 0.0;
+    n[2] = vmul(sc1, a);
+    n[3] = need3 ? vmul(sc1, b) : 0.0;
 }
 
-// sqrt(x) for x >= 0 in the lane precision (0 at 0): x rsqrt(x) in float.
-__device__ __forceinline__ float lane_sqrt(float x) { return x > 0.0f ? vmul(x, sfu_rsqrt(x)) : 0.0f; }
-__device__ __forceinline__ double lane_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float lane_rsqrt(float x) { return sfu_rsqrt(x); }
-__device__ __forceinline__ double lane_rsqrt(double x) { return rsqrt(x); }
+// 1 / sqrt(x) lane by lane.
+__device__ __forceinline__ float vrsqrt(float x) { return sfu_rsqrt(x); }
+__device__ __forceinline__ float2 vrsqrt(float2 x) { return make_float2(sfu_rsqrt(x.x), sfu_rsqrt(x.y)); }
+__device__ __forceinline__ double vrsqrt(double x) { return rsqrt(x); }
+
+// Noise scale sqrt(max(x, 0)) lane by lane: the special-function square root
+// in float, the library's in double.
+__device__ __forceinline__ float vsqrt_pos(float x) { return sfu_sqrt(fmaxf(x, 0.0f)); }
+__device__ __forceinline__ float2 vsqrt_pos(float2 x) {
+    return make_float2(sfu_sqrt(fmaxf(x.x, 0.0f)), sfu_sqrt(fmaxf(x.y, 0.0f)));
+}
+__device__ __forceinline__ double vsqrt_pos(double x) { return sqrt(x > 0.0 ? x : 0.0); }
 
 // Laplacian of the density, lap rho = 6 sum_i t_i (rho(r + c_i) - rho(r))
 // = (1/3) (sum of the 6 face neighbours) + (1/6) (sum of the 12 edge
@@ -207,52 +264,56 @@ __device__ __forceinline__ void d3q19_tau1_noise_and_populations(V (&h)[19], V (
     using S = typename VT<V>::S;
     constexpr int W = VT<V>::W;
     if (P.kT > S(0)) {
-        // scale sqrt(3 rho kT) (Eq. 68 with Delta V = Delta t = 1) and the
+        // scale sqrt(3 rho kT) (Eq. 68 with Delta V = Delta t = 1; the variance
+        // carries the factor the draws of the lane precision expect) and the
         // Cholesky factor of the coupled pair (modes c^2 - 1, 3c^4 - 6c^2 + 1):
-        // M = [[2/3 + om, -om], [-om, 2 + om]], om = 1 - 3 c_s^2
-        V sc, k11, k21, k22;
+        // M = [[2/3 + om, -om], [-om, 2 + om]], om = 1 - 3 c_s^2, whose
+        // determinant is 4/3 + 8/3 om (positive only where 2/3 + om is too);
+        // paired arithmetic, the special functions lane by lane
+        const V sc = vsqrt_pos(vmul(vbc<V>(vmul(S(3.0 * DrawScale<S>::v), P.kT)), rho));
+        const V om = vfma(cs2, vk<V>(-3.0), vk<V>(1.0));
+        const V mpp = vadd(vk<V>(2.0 / 3.0), om);
+        const V det = vfma(om, vk<V>(8.0 / 3.0), vk<V>(4.0 / 3.0));
+        const V q = vrsqrt(mpp);
+        V k11 = vmul(vmul(mpp, q), vk<V>(1.0 / 24.0));
+        V k21 = vmul(vmul(om, q), vk<V>(-1.0 / 72.0));
+        V k22 = vmul(vmul(det, vrsqrt(vmul(det, mpp))), vk<V>(1.0 / 72.0));
         bool bad_noise = false;
 #pragma unroll
-        for (int l = 0; l < W; ++l) {
-            const S r = lane(rho, l);
-            set_lane(sc, l, lane_sqrt(vmul(S(3) * P.kT, r > S(0) ? r : S(0))));
-            const S om = vfma(lane(cs2, l), S(-3), S(1));
-            const S mpp = vadd(S(2.0 / 3.0), om);
-            const S det = vfma(mpp, vadd(S(2), om), -vmul(om, om));
-            if (mpp > S(0) && det > S(0)) {
-                const S q = lane_rsqrt(mpp);
-                set_lane(k11, l, vmul(vmul(mpp, q), S(1.0 / 24.0)));
-                set_lane(k21, l, vmul(vmul(-om, q), S(1.0 / 72.0)));
-                set_lane(k22, l, vmul(vmul(lane_sqrt(det), q), S(1.0 / 72.0)));
-            } else {
-                bad_noise = true;
-                set_lane(k11, l, S(0));
-                set_lane(k21, l, S(0));
-                set_lane(k22, l, S(0));
+        for (int l = 0; l < W; ++l) bad_noise = bad_noise || !(lane(det, l) > S(0));
+        if (bad_noise) {
+#pragma unroll
+            for (int l = 0; l < W; ++l) {
+                if (!(lane(det, l) > S(0))) {
+                    set_lane(k11, l, S(0));
+                    set_lane(k21, l, S(0));
+                    set_lane(k22, l, S(0));
+                }
             }
+            atomicOr(status, ST_NOISE);
         }
-        if (bad_noise) atomicOr(status, ST_NOISE);
-        // the normal of mode a is number a - 4 in draw order; c_a = 1 / (36 sqrt(N_a))
+        // the normal of mode a is number a - 4 in draw order; c_a = 1 / (36 sqrt(N_a)),
+        // carried by the pair's scale where both normals of a pair share it
         const double c5 = 1.0 / (36.0 * 1.1547005383792515), c6 = 1.0 / 24.0, c7 = 1.0 / 12.0;
         const double c10 = 1.0 / (36.0 * 0.81649658092772603), c13 = 1.0 / (12.0 * 1.4142135623730951);
         V n[4];
-        draw4(key, site, 0u, sc, n, true);
+        draw4(key, site, 0u, sc, sc, n, true);
         const V n4 = n[0];
         h[4] = vfma(k11, n4, h[4]);
         h[5] = vfma(n[1], vk<V>(c5), h[5]);
         h[6] = vfma(n[2], vk<V>(c6), h[6]);
         h[7] = vfma(n[3], vk<V>(c7), h[7]);
-        draw4(key, site, 1u, sc, n, true);
+        draw4(key, site, 1u, sc, vmul(sc, vk<V>(c10)), n, true);
         h[8] = vfma(n[0], vk<V>(c7), h[8]);
         h[9] = vfma(n[1], vk<V>(c7), h[9]);
-        h[10] = vmul(n[2], vk<V>(c10));
-        h[11] = vmul(n[3], vk<V>(c10));
-        draw4(key, site, 2u, sc, n, true);
+        h[10] = n[2];
+        h[11] = n[3];
+        draw4(key, site, 2u, sc, vmul(sc, vk<V>(c13)), n, true);
         h[12] = vmul(n[0], vk<V>(c10));
         h[13] = vmul(n[1], vk<V>(c13));
-        h[14] = vmul(n[2], vk<V>(c13));
-        h[15] = vmul(n[3], vk<V>(c13));
-        draw4(key, site, 3u, sc, n, false);
+        h[14] = n[2];
+        h[15] = n[3];
+        draw4(key, site, 3u, sc, sc, n, false);
         h[16] = vfma(k22, n[0], vfma(k21, n4, h[16]));
         h[17] = vmul(n[1], vk<V>(c5));
         h[18] = vmul(n[2], vk<V>(c6));

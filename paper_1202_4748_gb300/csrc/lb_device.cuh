@@ -191,18 +191,21 @@ struct SysPhys {
 };
 
 // ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): round multipliers M0, M1
+// and key increments W0, W1
 // ---------------------------------------------------------------------------
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
 __device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         if (r) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
+            k0 += kPhiloxW0;
+            k1 += kPhiloxW1;
         }
         // one 32 x 32 -> 64-bit product per multiplier (high and low words together)
-        const uint64_t pa = uint64_t(0xD2511F53u) * ctr.x;
-        const uint64_t pb = uint64_t(0xCD9E8D57u) * ctr.z;
+        const uint64_t pa = uint64_t(kPhiloxM0) * ctr.x;
+        const uint64_t pb = uint64_t(kPhiloxM1) * ctr.z;
         ctr = make_uint4(uint32_t(pb >> 32) ^ ctr.y ^ k0, uint32_t(pb), uint32_t(pa >> 32) ^ ctr.w ^ k1,
                          uint32_t(pa));
     }
