@@ -44,6 +44,7 @@ WORKLOADS = {
     "fss_60": dict(ensemble="fss_60", lattice="D3Q19", precision="fp32"),
     "fss_160_64_fp64": dict(ensemble="fss_160_64", lattice="D3Q19", precision="fp64"),
     "fss_160_modeq": dict(ensemble="fss_160", lattice="D3Q19", precision="fp32", coupling="modeq"),
+    "fss_160_64_modeq": dict(ensemble="fss_160_64", lattice="D3Q19", precision="fp32", coupling="modeq"),
 }
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
