@@ -173,7 +173,7 @@ cudaError_t step_pair(const StepLaunch& a, cudaStream_t st) {
     A.step_ptr = a.step_ptr;
     A.k = a.k;
     A.status = a.status;
-    constexpr size_t dyn = PairSmem<TX, TY, PW, R, STG>::bytes;
+    constexpr size_t dyn = PairSmem<TX, TY, PW, R, STG, CP>::bytes;
     static int state = 0;                      // once per instantiation: 1 usable, -1 not
     if (state == 0) {
         auto k = step_kernel_pair<TX, TY, ZC, PW, MINB, R, STG, CP>;

@@ -4,7 +4,8 @@
 // Per CTA a TX x TY column of sites walks a chunk of ZC planes.  PW producer
 // warps stage each plane into shared-memory rings of R planes:
 //   * density deviation on the footprint (columns x0 - 4 .. x0 + TX + 3, rows
-//     y0 - 2 .. y0 + TY + 1), from the 19 populations pulled to each footprint
+//     y0 - 2 .. y0 + TY + 1; y0 - 1 .. y0 + TY for the modified equilibrium,
+//     which reads radius 1), from the 19 populations pulled to each footprint
 //     site (pull streaming, f_i(r) = f*_i(r - c_i)).  A producer lane owns four
 //     consecutive footprint sites: each direction is one aligned 128-bit load
 //     of the source row, and the c_x = +-1 directions take the value that
@@ -51,11 +52,12 @@ namespace lbf {
 // Laplacian copies, momentum pairs.  Row pitches: when a half warp of
 // consumers spans two rows (8 pairs per row) they read rows r and r + 2, so a
 // pitch of 8 (mod 16) floats keeps the two rows' 64-bit loads on disjoint banks.
-template <int TX, int TY, int R>
+// HR: halo rows of the density footprint (2 for the Guo form's gradient of
+// the Laplacian, 1 for the modified equilibrium).
+template <int TX, int TY, int R, int HR = 2>
 struct PairLayout {
-    static constexpr int H = 2;
     static constexpr int NPR = TX / 2;                 // site pairs per tile row
-    static constexpr int SXQ = TX + 8, SY = TY + 2 * H;   // footprint columns x0 - 4 .. x0 + TX + 3
+    static constexpr int SXQ = TX + 8, SY = TY + 2 * HR;  // footprint columns x0 - 4 .. x0 + TX + 3
     static constexpr int NQ = SXQ / 4;                 // producer quads per footprint row
     static constexpr int RPW = 32 / NQ;                // footprint rows per producer warp
     static constexpr int PWN = (SY + RPW - 1) / RPW;   // producer warps needed
@@ -165,18 +167,19 @@ struct PairRegs {
 // shared memory (no registers held by loads in flight), which leaves room
 // for more resident CTAs.  (Two staging areas, so that the copies run two
 // planes ahead, need 2 CTAs per SM and measured slower.)
-template <int TX, int TY, int PW, int R, int STG>
+template <int TX, int TY, int PW, int R, int STG, int CP = GUO>
 struct PairSmem {
     static constexpr size_t stage = STG == 3 ? size_t(19) * 32 * PW * 16 : 0;   // [19][producers] float4
-    static constexpr size_t bytes = PairLayout<TX, TY, R>::bytes + stage;
+    static constexpr size_t bytes = PairLayout<TX, TY, R, CP == MODEQ ? 1 : 2>::bytes + stage;
 };
 
 template <int TX, int TY, int ZC, int PW, int MINB, int R, int STG, int CP = GUO>
 __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(const StepArgs<float> A) {
     using RG = PairRegs<TX, TY, PW, MINB, STG>;
     using L = D3Q19;
-    using LY_ = PairLayout<TX, TY, R>;
-    constexpr int H = 2;
+    constexpr int H = 2;                              // halo planes of a chunk
+    constexpr int HR = CP == MODEQ ? 1 : 2;           // halo rows of the density footprint
+    using LY_ = PairLayout<TX, TY, R, HR>;
     constexpr int NPR = LY_::NPR;
     constexpr int LX2 = LY_::LX / 2;
     constexpr int NC = TX * TY / 2;                   // consumer threads
@@ -216,14 +219,14 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
         const int rw = (ptid & 31) / NQ, q = (ptid & 31) % NQ;
         const int py = (ptid >> 5) * RPW + rw;
         const bool act = rw < RPW && py < LY_::SY;
-        const bool tile = act && py >= H && py < H + TY && q >= 1 && q <= TX / 4;
+        const bool tile = act && py >= HR && py < HR + TY && q >= 1 && q <= TX / 4;
         const int xq = wrapm(tl.y - 4 + 4 * q, nx);  // first column of the quad (nx % 4 == 0: contiguous)
-        const int gy = tl.z - H + py;
+        const int gy = tl.z - HR + py;
         // source rows y - c_y for c_y = -1, 0, +1
         const float* const rowp[3] = {fb + wrapm(gy + 1, ny) * nx + xq, fb + wrapm(gy, ny) * nx + xq,
                                       fb + wrapm(gy - 1, ny) * nx + xq};
         const int dst = py * SXP + 4 * q;
-        const int jdst = LY_::O_J + (py - H) * JRP + (q - 1) * 12;   // pairs 2(q - 1), 2(q - 1) + 1
+        const int jdst = LY_::O_J + (py - HR) * JRP + (q - 1) * 12;   // pairs 2(q - 1), 2(q - 1) + 1
         const int pl = nx * ny;
         const bool sm = S.small != 0;
         // the loads of plane zz + 1 are issued as soon as plane zz has been
@@ -354,8 +357,8 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
                         lpx = 2 * (lq % LX2);
                         lpy = lq / LX2;
                     }
-                    // Laplacian column lpx <-> footprint column lpx + 3, row lpy <-> lpy + 1
-                    rv.c = (lpy + 1) * SXP + lpx + 2;
+                    // Laplacian column lpx <-> footprint column lpx + 3, row lpy <-> lpy + HR - 1
+                    rv.c = (lpy + HR - 1) * SXP + lpx + 2;
                     const float2 lap = lap_d3q19<float2>(rv);
                     *reinterpret_cast<float2*>(lo + lpy * LXP + lpx) = lap;
                     le[lpy * LXP + lpx + 1] = lap.x;
@@ -385,7 +388,7 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
         }
         const int x = tl.y + 2 * pk, y = tl.z + ty;
         const bool valid = x < nx && y < ny;
-        const int rho_off = (ty + H) * SXP + 2 * pk + 4;
+        const int rho_off = (ty + HR) * SXP + 2 * pk + 4;
         const int j_off = LY_::O_J + ty * JRP + pk * 6;
         const int lap_c = (ty + 1) * LXP + 2 * pk;
         for (int zc = z0; zc < z1; ++zc) {
