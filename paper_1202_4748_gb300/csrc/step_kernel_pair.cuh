@@ -35,11 +35,16 @@
 // word, and every thread keeps the same control flow.
 //
 // CP = MODEQ runs the modified equilibrium carried to D3Q19
-// (collide_d3q19_modeq_tau1): no Laplacian planes are formed (full[...] of
-// plane zl completes once density plane zl + 1 is written), the consumers
-// read the density of the planes zc - 1 .. zc + 1 around their pair, and so
-// the producers reuse the slots of plane zz - R + 1 (whose collision no
-// longer reads them) instead of zz - R.
+// (collide_d3q19_modeq_tau1), which reads the density within radius 1: the
+// footprint has one halo row and a chunk one halo plane on each side
+// (density planes z0 - 1 .. z1, ring slot (z - z0 + 1) mod R), no Laplacian
+// planes are formed, full[(zc - z0) mod R] completes once density plane
+// zc + 1 is written, the consumers read the density of the planes
+// zc - 1 .. zc + 1 around their pair, and so the producers reuse the slots of
+// plane zz - R + 1 (whose collision no longer reads them) instead of zz - R.
+// A producer then writes plane zz only after the collision of zz - R + 1, and
+// a consumer collides zc only after density plane zc + 1 is written, so again
+// no phase of a barrier completes twice before its waiter looks.
 #pragma once
 
 #include "collide_d3q19.cuh"
@@ -177,7 +182,7 @@ template <int TX, int TY, int ZC, int PW, int MINB, int R, int STG, int CP = GUO
 __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(const StepArgs<float> A) {
     using RG = PairRegs<TX, TY, PW, MINB, STG>;
     using L = D3Q19;
-    constexpr int H = 2;                              // halo planes of a chunk
+    constexpr int HZ = CP == MODEQ ? 1 : 2;           // halo planes of a chunk
     constexpr int HR = CP == MODEQ ? 1 : 2;           // halo rows of the density footprint
     using LY_ = PairLayout<TX, TY, R, HR>;
     constexpr int NPR = LY_::NPR;
@@ -205,7 +210,7 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
         abort_flag = 0;
     }
     __syncthreads();
-    auto slot = [&](int z) { return (z - z0 + H) & (R - 1); };
+    auto slot = [&](int z) { return (z - z0 + HZ) & (R - 1); };
 
     if (tid >= NC) {
         // ---------------- producers ----------------
@@ -262,8 +267,8 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
             if constexpr (CPA) return stage[decltype(I)::value * NP];
             else return g[decltype(I)::value];
         };
-        pull(z0 - H);
-        for (int zz = z0 - H; zz < z1 + H; ++zz) {
+        pull(z0 - HZ);
+        for (int zz = z0 - HZ; zz < z1 + HZ; ++zz) {
             // plane whose slots this iteration reuses: the modified equilibrium's
             // consumers read the density of the planes on both sides of the one
             // they collide, so its producers also wait for the plane after it
@@ -275,7 +280,7 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
             // the neighbouring lane.  Density and momentum are summed in the
             // order of the one-site kernels (from 0, direction by direction).
             if constexpr (CPA) cp_async_wait_all();      // this lane's copies of plane zz have landed
-            const bool more = zz + 1 < z1 + H;
+            const bool more = zz + 1 < z1 + HZ;
             int zn[3];
             planes_of(zz + 1, zn);
             float2 r01 = make_float2(0.0f, 0.0f), r23 = r01;
@@ -334,12 +339,12 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
                 if (more) pull(zz + 1);
             }
             named_barrier(1, NP);                        // density plane zz complete (producers)
-            const int zl = zz - 1;                       // Laplacian plane (needs density zl-1 .. zl+1)
-            if (zl >= z0 - 1 && CP == MODEQ) {
-                // the modified equilibrium needs no Laplacian planes: density
-                // planes up to zl + 1 are complete (same hand-off as below)
-                mbar_arrive(&full[(zl - z0 + 1) & (R - 1)]);
-            } else if (zl >= z0 - 1) {
+            if constexpr (CP == MODEQ) {
+                // no Laplacian planes: density planes up to zz are complete, all
+                // that the collision of zz - 1 reads
+                if (zz >= z0 + 1) mbar_arrive(&full[(zz - z0 - 1) & (R - 1)]);
+            } else if (zz >= z0) {
+                const int zl = zz - 1;                   // Laplacian plane (needs density zl-1 .. zl+1)
                 PairRhoView<SXP> rv{{ring + slot(zl - 1) * PLANE, ring + slot(zl) * PLANE, ring + slot(zl + 1) * PLANE},
                                     0};
                 float* lo = ring + slot(zl) * PLANE + LY_::O_LO;
@@ -392,8 +397,10 @@ __global__ void __launch_bounds__(TX* TY / 2 + 32 * PW, MINB) step_kernel_pair(c
         const int j_off = LY_::O_J + ty * JRP + pk * 6;
         const int lap_c = (ty + 1) * LXP + 2 * pk;
         for (int zc = z0; zc < z1; ++zc) {
-            const int zl = zc + 1;                       // the last Laplacian plane the collision reads
-            const bool ok = mbar_wait(&full[(zl - z0 + 1) & (R - 1)], unsigned(((zl - z0 + 1) / R) & 1),
+            // the hand-off of the last plane the collision reads: Laplacian plane
+            // zc + 1 (full[zc - z0 + 2]), or density plane zc + 1 (full[zc - z0])
+            const int kf = zc - z0 + (CP == MODEQ ? 0 : 2);
+            const bool ok = mbar_wait(&full[kf & (R - 1)], unsigned((kf / R) & 1),
                                       &abort_flag, A.status);
             if (valid && ok) {
                 const float* cp = ring + slot(zc) * PLANE;
