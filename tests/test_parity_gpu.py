@@ -188,14 +188,16 @@ def test_single_16_thousand_step_trajectory(lb, lattice):
     ens.close()
 
 
-@pytest.mark.parametrize("workload,lattice", [("fss_160", "D3Q19"), ("fss_60", "D3Q19"), ("fss_160", "D2Q9")])
-def test_full_size_ensembles_sampled_parity(lb, workload, lattice):
+@pytest.mark.parametrize("workload,lattice,coupling", [("fss_160", "D3Q19", None), ("fss_60", "D3Q19", None),
+                                                       ("fss_160", "D2Q9", None), ("fss_160", "D3Q19", "modeq")])
+def test_full_size_ensembles_sampled_parity(lb, workload, lattice, coupling):
     """The batched FP32 ensembles in the launch configuration the benchmark times
-    (160 systems of 16^3..64^3, the uneven 60 systems of 32^3..128^3, and the
-    paper's D2Q9 lattice at 64^2..512^2): after one step, three systems
-    (smallest, a middle one, largest) are compared with the oracle stepping each
-    from the same state."""
-    systems = synth.ensemble(workload, lattice)
+    (160 systems of 16^3..64^3, the uneven 60 systems of 32^3..128^3, the
+    paper's D2Q9 lattice at 64^2..512^2, and the 160 systems with the modified
+    equilibrium carried to D3Q19): after one step, three systems (smallest, a
+    middle one, largest) are compared with the oracle stepping each from the
+    same state."""
+    systems = synth.ensemble(workload, lattice, coupling)
     ens = lb.Ensemble(systems, precision="fp32", obs_every=100, graph_chunk=100)
     ens.init(amplitude=0.01)
     picks = [0, len(systems) // 2, len(systems) - 1]
