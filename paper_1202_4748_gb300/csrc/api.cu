@@ -190,7 +190,8 @@ int64_t tiles_of(const lb_system_desc* s, int n, const int tdim[3]) {
 // the z-chunk, the longest chunk whose CTAs still fill the GPU at least twice
 // over (resident CTAs per SM x SMs of the current device; 152 SMs when no
 // device is visible), else the default row.  Longer chunks re-read fewer
-// halo planes (4 per chunk), but too few CTAs leave SMs idle in the last
+// halo planes (4 per chunk; 2 for the modified equilibrium on D3Q19), but
+// too few CTAs leave SMs idle in the last
 // wave: on GB300 the 64-plane chunks win on the 160-system ensemble (1,184
 // CTAs) and on 256^3 (1,024), the 32-plane ones on 32 systems of 64^3 (512).
 void prefer_longer_chunk(const lb_system_desc* s, int n, int& tile_id, int tdim[3]) {
